@@ -1,0 +1,720 @@
+// ob_oracle.cpp -- TEST INFRASTRUCTURE, not part of the product path.
+//
+// A plain, slow, obviously-correct CPU implementation of what the GPU library
+// computes, written from the paper (N. Zhang, A. Roux, T. Zastawniak,
+// "Parallel Binomial American Option Pricing with (and without) Transaction
+// Costs", 2011).  Only the tests, the package smoke check and the benchmark's
+// CPU-baseline leg may load it.  It shares no code, header or table with the
+// CUDA library.
+//
+// What it computes
+//  * Section 4.1: the binomial model u = exp(sigma*sqrt(T/N)), d = 1/u,
+//    r = exp(R*T/N), an extra time instant N+1 whose N+2 nodes carry the
+//    payoff (0,0), and no transaction costs at t = 0.
+//  * Section 3: bid/ask stock prices S^a = (1+k)S, S^b = (1-k)S; the seller's
+//    expense function u_t (Eq. 1) and the buyer's (Eq. 6); and the backward
+//    induction that builds, at every node, w_t = max of the two successor z's,
+//    the discounted w_t/r, its slope restriction v_t to [-S^a_t, -S^b_t], and
+//    z_t = max(u_t, v_t) for the seller (ask = z_0(0)) or z_t = min(u_t, v_t)
+//    for the buyer (bid = -z'_0(0)).  These are Roux & Zastawniak's
+//    Algorithms 3.1 and 3.5 as the paper sketches them.
+//  * Section 3 (first paragraph) and the Appendix: the plain CRR recursion
+//    pi_t = max(P_t, (p pi^u + (1-p) pi^d)/r) without costs, with no extra
+//    level, and its European counterpart (no early exercise).
+//  * Forward-mode dual numbers through the same induction give the
+//    derivatives of ask and bid with respect to (S0, K, sigma, R, T, k).
+//
+// Readings of the paper taken here (each is also listed in the design doc):
+//  * "restricting the slopes" of w_t/r to [-S^a_t, -S^b_t] is the
+//    inf-convolution v(y) = inf_{y'} [ w(y')/r + theta(y'-y) ], with
+//    theta(x) = S^a x for x >= 0 and S^b x for x < 0: the cheapest way to
+//    rebalance from stock holding y to y' and then hold a covering position.
+//    It is the largest function below w/r whose slopes lie in the window; for
+//    the convex seller functions it is a clip of the slopes, for the
+//    (non-convex) buyer functions it is computed by two monotone sweeps.
+//  * node (t, j) has stock price S_{t,j} = S0 u^(2j-t); its successors are
+//    (t+1, j+1) (up) and (t+1, j) (down).
+//  * payoffs (xi, zeta): put (K, -1) and call (-K, +1), both physically
+//    settled; bull spread cash-settled, xi = (S-K)^+ - (S-K2)^+, zeta = 0.
+//
+// Representation: a piecewise-linear (PL) function is a strictly increasing
+// list of breakpoints y_i with values f_i, plus the slopes of the two tails.
+// Every breakpoint kept is a genuine kink: results are simplified
+// structurally (a point is dropped when the same input piece continues
+// through it), never by a floating-point collinearity test.
+//
+// Build: g++ -O2 -ffp-contract=off -std=c++17 -shared -fPIC -pthread
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+extern "C" {
+// 64-byte option record (same layout as the workload tables).
+typedef struct {
+  double S0, K, K2, sigma, R, T, k;
+  int32_t N, payoff;
+} or_option_t;
+}
+
+namespace {
+
+enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_ARBITRAGE = -2, OR_ERR_UNBOUNDED = -3,
+       OR_ERR_CAPACITY = -4 };
+enum { PAY_PUT = 0, PAY_CALL = 1, PAY_SPREAD = 2 };
+
+// ---------------------------------------------------------------- dual numbers
+// Value plus its gradient with respect to (S0, K, sigma, R, T, k).
+constexpr int NG = 6;
+struct Dual {
+  double v;
+  double g[NG];
+  Dual() : v(0) { for (int i = 0; i < NG; ++i) g[i] = 0; }
+  Dual(double x) : v(x) { for (int i = 0; i < NG; ++i) g[i] = 0; }
+};
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual c; c.v = a.v + b.v; for (int i = 0; i < NG; ++i) c.g[i] = a.g[i] + b.g[i]; return c;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual c; c.v = a.v - b.v; for (int i = 0; i < NG; ++i) c.g[i] = a.g[i] - b.g[i]; return c;
+}
+inline Dual operator-(const Dual& a) {
+  Dual c; c.v = -a.v; for (int i = 0; i < NG; ++i) c.g[i] = -a.g[i]; return c;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual c; c.v = a.v * b.v;
+  for (int i = 0; i < NG; ++i) c.g[i] = a.g[i] * b.v + a.v * b.g[i];
+  return c;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual c; c.v = a.v / b.v;
+  for (int i = 0; i < NG; ++i) c.g[i] = (a.g[i] - c.v * b.g[i]) / b.v;
+  return c;
+}
+inline Dual dexp(const Dual& a) {
+  Dual c; c.v = std::exp(a.v); for (int i = 0; i < NG; ++i) c.g[i] = c.v * a.g[i]; return c;
+}
+inline Dual dsqrt(const Dual& a) {
+  Dual c; c.v = std::sqrt(a.v);
+  for (int i = 0; i < NG; ++i) c.g[i] = a.g[i] / (2.0 * c.v);
+  return c;
+}
+inline Dual dpowi(const Dual& a, int e) {
+  Dual c; c.v = std::pow(a.v, e);
+  double dv = (e == 0) ? 0.0 : e * std::pow(a.v, e - 1);
+  for (int i = 0; i < NG; ++i) c.g[i] = dv * a.g[i];
+  return c;
+}
+inline double dexp(double a) { return std::exp(a); }
+inline double dsqrt(double a) { return std::sqrt(a); }
+inline double dpowi(double a, int e) { return std::pow(a, e); }
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+// ---------------------------------------------------------------- PL functions
+template <class T>
+struct PL {
+  std::vector<T> y, f;  // strictly increasing breakpoints and values
+  T sL, sR;             // slopes for y < y.front() and y > y.back()
+};
+
+template <class T>
+T pl_eval(const PL<T>& F, const T& x) {
+  const size_t m = F.y.size();
+  const double xv = val(x);
+  if (xv <= val(F.y[0])) return F.f[0] + F.sL * (x - F.y[0]);
+  if (xv >= val(F.y[m - 1])) return F.f[m - 1] + F.sR * (x - F.y[m - 1]);
+  size_t lo = 0, hi = m - 1;  // y[lo] <= x < y[hi]
+  while (hi - lo > 1) {
+    size_t mid = (lo + hi) / 2;
+    if (val(F.y[mid]) <= xv) lo = mid; else hi = mid;
+  }
+  if (xv == val(F.y[lo])) return F.f[lo];
+  T t = (x - F.y[lo]) / (F.y[hi] - F.y[lo]);
+  return F.f[lo] + (F.f[hi] - F.f[lo]) * t;
+}
+
+// Pointwise max (take_max) or min of F and G.  The union of both breakpoint
+// sets is evaluated on both functions; wherever F - G changes sign strictly
+// between neighbouring union points (or in a tail) the crossing is inserted.
+template <class T>
+PL<T> pl_envelope(const PL<T>& F, const PL<T>& G, bool take_max) {
+  enum { OF = 1, OG = 2 };
+  struct UP { T y; int iF, iG; };
+  std::vector<UP> U;
+  size_t i = 0, j = 0;
+  const size_t mF = F.y.size(), mG = G.y.size();
+  while (i < mF || j < mG) {
+    if (j == mG || (i < mF && val(F.y[i]) < val(G.y[j]))) { U.push_back({F.y[i], (int)i, -1}); ++i; }
+    else if (i == mF || val(G.y[j]) < val(F.y[i])) { U.push_back({G.y[j], -1, (int)j}); ++j; }
+    else { U.push_back({F.y[i], (int)i, (int)j}); ++i; ++j; }
+  }
+  const size_t n = U.size();
+  std::vector<T> a(n), b(n);
+  std::vector<int> s(n);  // +1: F wins strictly, -1: G wins strictly, 0: tie
+  for (size_t q = 0; q < n; ++q) {
+    a[q] = U[q].iF >= 0 ? F.f[U[q].iF] : pl_eval(F, U[q].y);
+    b[q] = U[q].iG >= 0 ? G.f[U[q].iG] : pl_eval(G, U[q].y);
+    const double av = val(a[q]), bv = val(b[q]);
+    s[q] = (av == bv) ? 0 : (((av > bv) == take_max) ? 1 : -1);
+  }
+  auto owner = [](int sg) { return sg > 0 ? OF : OG; };
+
+  struct OP { T y, f; int iF, iG; };
+  std::vector<OP> P;      // candidate output points, in order
+  std::vector<int> own;   // own[q]: owner of the segment left of P[q]; own.back(): right tail
+
+  // Left tail: the function with the smaller slope is larger far to the left.
+  int farL;
+  {
+    const double dl = val(F.sL) - val(G.sL);
+    if (dl != 0) farL = ((dl < 0) == take_max) ? OF : OG;
+    else farL = (s[0] >= 0) ? OF : OG;
+  }
+  own.push_back(farL);
+  if (s[0] != 0 && owner(s[0]) != farL) {
+    T h0 = a[0] - b[0];
+    T dL = F.sL - G.sL;
+    T ys = U[0].y - h0 / dL;
+    if (val(ys) < val(U[0].y)) {
+      T fs = a[0] + F.sL * (ys - U[0].y);
+      P.push_back({ys, fs, -1, -1});
+      own.push_back(owner(s[0]));
+    }
+  }
+  for (size_t q = 0; q < n; ++q) {
+    P.push_back({U[q].y, (s[q] >= 0 ? a[q] : b[q]), U[q].iF, U[q].iG});
+    if (q + 1 == n) break;
+    const int sl = s[q], sr = s[q + 1];
+    if (sl * sr < 0) {
+      T h0 = a[q] - b[q], h1 = a[q + 1] - b[q + 1];
+      T t = h0 / (h0 - h1);
+      T ys = U[q].y + (U[q + 1].y - U[q].y) * t;
+      if (val(ys) > val(U[q].y) && val(ys) < val(U[q + 1].y)) {
+        T fs = a[q] + (a[q + 1] - a[q]) * t;
+        own.push_back(owner(sl));
+        P.push_back({ys, fs, -1, -1});
+        own.push_back(owner(sr));
+      } else if (val(ys) <= val(U[q].y)) {
+        own.push_back(owner(sr));
+      } else {
+        own.push_back(owner(sl));
+      }
+    } else {
+      const int ss = sl + sr;
+      own.push_back(ss > 0 ? OF : (ss < 0 ? OG : OF));
+    }
+  }
+  // Right tail: the function with the larger slope is larger far to the right.
+  int farR;
+  {
+    const double dr = val(F.sR) - val(G.sR);
+    if (dr != 0) farR = ((dr > 0) == take_max) ? OF : OG;
+    else farR = (s[n - 1] >= 0) ? OF : OG;
+  }
+  if (s[n - 1] != 0 && owner(s[n - 1]) != farR) {
+    T h0 = a[n - 1] - b[n - 1];
+    T dR = F.sR - G.sR;
+    T ys = U[n - 1].y - h0 / dR;
+    if (val(ys) > val(U[n - 1].y)) {
+      T fs = a[n - 1] + F.sR * (ys - U[n - 1].y);
+      own.push_back(owner(s[n - 1]));
+      P.push_back({ys, fs, -1, -1});
+    }
+  }
+  own.push_back(farR);
+
+  PL<T> out;
+  out.sL = own.front() == OF ? F.sL : G.sL;
+  out.sR = own.back() == OF ? F.sR : G.sR;
+  for (size_t q = 0; q < P.size(); ++q) {
+    const int ol = own[q], orr = own[q + 1];
+    const bool kink = (ol != orr) || (ol == OF ? P[q].iF >= 0 : P[q].iG >= 0);
+    if (kink) { out.y.push_back(P[q].y); out.f.push_back(P[q].f); }
+  }
+  if (out.y.empty()) { out.y.push_back(P[0].y); out.f.push_back(P[0].f); }
+  return out;
+}
+
+template <class T>
+PL<T> pl_div(const PL<T>& F, const T& r) {
+  PL<T> out = F;
+  for (auto& v : out.f) v = v / r;
+  out.sL = F.sL / r;
+  out.sR = F.sR / r;
+  return out;
+}
+
+// Slope restriction v(y) = inf_{y'} [ F(y') + theta(y' - y) ] = min(A(y), B(y)),
+//   A(y) = min_{y' >= y} [F(y') + Sa y'] - Sa y   (buy stock, swept from the right)
+//   B(y) = min_{y' <= y} [F(y') + Sb y'] - Sb y   (sell stock, swept from the left)
+// Each of A, B follows F ("active") or a line of slope -Sa / -Sb ("flat").
+template <class T>
+int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V) {
+  enum { ACT = 1, FLAT = 2 };
+  const size_t m = F.y.size();
+  if (val(F.sR) + val(Sa) < 0 || val(F.sL) + val(Sb) > 0) return OR_ERR_UNBOUNDED;
+  struct SP { T y, f; int iF; };
+
+  // ---- A: sweep from the right over g = F + Sa*y.
+  PL<T> A;
+  {
+    std::vector<SP> P;     // right-to-left
+    std::vector<int> own;  // own[q]: owner of the segment right of P[q] (own[0] = right tail)
+    own.push_back(ACT);
+    T cur = F.f[m - 1] + Sa * F.y[m - 1];
+    bool act_right = true;  // is M equal to g at the current right end point?
+    P.push_back({F.y[m - 1], F.f[m - 1], (int)(m - 1)});
+    for (size_t ii = m - 1; ii-- > 0;) {
+      T gi = F.f[ii] + Sa * F.y[ii];
+      T gr = F.f[ii + 1] + Sa * F.y[ii + 1];
+      if (val(gi) >= val(cur)) {
+        own.push_back(FLAT);
+        P.push_back({F.y[ii], cur - Sa * F.y[ii], (int)ii});
+        act_right = false;
+      } else if (act_right) {
+        own.push_back(ACT);
+        P.push_back({F.y[ii], F.f[ii], (int)ii});
+        cur = gi;
+      } else {
+        T t = (cur - gi) / (gr - gi);  // g(y*) = cur, measured from y_i
+        T ys = F.y[ii] + (F.y[ii + 1] - F.y[ii]) * t;
+        if (val(ys) > val(F.y[ii]) && val(ys) < val(F.y[ii + 1])) {
+          own.push_back(FLAT);
+          P.push_back({ys, cur - Sa * ys, -1});
+          own.push_back(ACT);
+        } else if (val(ys) >= val(F.y[ii + 1])) {
+          own.push_back(ACT);
+        } else {
+          own.push_back(FLAT);
+        }
+        P.push_back({F.y[ii], F.f[ii], (int)ii});
+        cur = gi;
+        act_right = true;
+      }
+    }
+    // left tail: g(y) = g_0 + (sL + Sa)(y - y_0)
+    const double slg = val(F.sL) + val(Sa);
+    T tailslope;
+    if (slg <= 0) {
+      own.push_back(FLAT);
+      tailslope = -Sa;
+    } else if (act_right) {
+      own.push_back(ACT);
+      tailslope = F.sL;
+    } else {
+      T g0 = F.f[0] + Sa * F.y[0];
+      T ys = F.y[0] - (g0 - cur) / (F.sL + Sa);
+      if (val(ys) < val(F.y[0])) {
+        own.push_back(FLAT);
+        P.push_back({ys, cur - Sa * ys, -1});
+      }
+      own.push_back(ACT);
+      tailslope = F.sL;
+    }
+    // P is right-to-left; own[q] is right of P[q], own[q+1] is left of P[q].
+    A.sR = F.sR;  // own[0] == ACT
+    A.sL = tailslope;
+    std::vector<T> yy, ff;
+    for (size_t q = 0; q < P.size(); ++q) {
+      const int orr = own[q], ol = own[q + 1];
+      const bool kink = (ol != orr) || (ol == ACT && P[q].iF >= 0);
+      if (kink) { yy.push_back(P[q].y); ff.push_back(P[q].f); }
+    }
+    if (yy.empty()) { yy.push_back(P[0].y); ff.push_back(P[0].f); }
+    A.y.assign(yy.rbegin(), yy.rend());
+    A.f.assign(ff.rbegin(), ff.rend());
+  }
+
+  // ---- B: sweep from the left over h = F + Sb*y.
+  PL<T> B;
+  {
+    std::vector<SP> P;     // left-to-right
+    std::vector<int> own;  // own[q]: owner of the segment left of P[q] (own[0] = left tail)
+    own.push_back(ACT);
+    T cur = F.f[0] + Sb * F.y[0];
+    bool act_left = true;
+    P.push_back({F.y[0], F.f[0], 0});
+    for (size_t ii = 1; ii < m; ++ii) {
+      T hi = F.f[ii] + Sb * F.y[ii];
+      T hl = F.f[ii - 1] + Sb * F.y[ii - 1];
+      if (val(hi) >= val(cur)) {
+        own.push_back(FLAT);
+        P.push_back({F.y[ii], cur - Sb * F.y[ii], (int)ii});
+        act_left = false;
+      } else if (act_left) {
+        own.push_back(ACT);
+        P.push_back({F.y[ii], F.f[ii], (int)ii});
+        cur = hi;
+      } else {
+        T t = (hl - cur) / (hl - hi);  // h(y*) = cur, measured from y_{i-1}
+        T ys = F.y[ii - 1] + (F.y[ii] - F.y[ii - 1]) * t;
+        if (val(ys) > val(F.y[ii - 1]) && val(ys) < val(F.y[ii])) {
+          own.push_back(FLAT);
+          P.push_back({ys, cur - Sb * ys, -1});
+          own.push_back(ACT);
+        } else if (val(ys) <= val(F.y[ii - 1])) {
+          own.push_back(ACT);
+        } else {
+          own.push_back(FLAT);
+        }
+        P.push_back({F.y[ii], F.f[ii], (int)ii});
+        cur = hi;
+        act_left = true;
+      }
+    }
+    const double srh = val(F.sR) + val(Sb);
+    T tailslope;
+    if (srh >= 0) {
+      own.push_back(FLAT);
+      tailslope = -Sb;
+    } else if (act_left) {
+      own.push_back(ACT);
+      tailslope = F.sR;
+    } else {
+      T hm = F.f[m - 1] + Sb * F.y[m - 1];
+      T ys = F.y[m - 1] + (cur - hm) / (F.sR + Sb);
+      if (val(ys) > val(F.y[m - 1])) {
+        own.push_back(FLAT);
+        P.push_back({ys, cur - Sb * ys, -1});
+      }
+      own.push_back(ACT);
+      tailslope = F.sR;
+    }
+    B.sL = F.sL;  // own[0] == ACT
+    B.sR = tailslope;
+    for (size_t q = 0; q < P.size(); ++q) {
+      const int ol = own[q], orr = own[q + 1];
+      const bool kink = (ol != orr) || (ol == ACT && P[q].iF >= 0);
+      if (kink) { B.y.push_back(P[q].y); B.f.push_back(P[q].f); }
+    }
+    if (B.y.empty()) { B.y.push_back(P[0].y); B.f.push_back(P[0].f); }
+  }
+
+  V = pl_envelope(A, B, false);
+  return OR_OK;
+}
+
+// Expense function of the seller (Eq. 1) or of the buyer (Eq. 6):
+//   seller: u(y) =  xi + (y - zeta)^- Sa - (y - zeta)^+ Sb
+//   buyer : u(y) = -xi + (y + zeta)^- Sa - (y + zeta)^+ Sb
+template <class T>
+PL<T> pl_expense(const T& xi, const T& zeta, const T& Sa, const T& Sb, bool buyer) {
+  PL<T> u;
+  u.y.push_back(buyer ? -zeta : zeta);
+  u.f.push_back(buyer ? -xi : xi);
+  u.sL = -Sa;
+  u.sR = -Sb;
+  return u;
+}
+
+// One node of the induction (Section 3): w = max(z_up, z_down); f = w / r;
+// v = restriction of f to slopes in [-Sa, -Sb]; z = max(u, v) (seller) or
+// z = min(u, v) (buyer).
+template <class T>
+int node_step(const PL<T>& zu, const PL<T>& zd, const T& r, const T& Sa, const T& Sb,
+              const T& xi, const T& zeta, bool buyer, PL<T>& z) {
+  PL<T> w = pl_envelope(zu, zd, true);
+  PL<T> f = pl_div(w, r);
+  PL<T> v;
+  int rc = pl_restrict(f, Sa, Sb, v);
+  if (rc) return rc;
+  PL<T> u = pl_expense(xi, zeta, Sa, Sb, buyer);
+  z = pl_envelope(u, v, !buyer);
+  return OR_OK;
+}
+
+// ---------------------------------------------------------------- tree model
+template <class T>
+struct Model {
+  int N, payoff;
+  T S0, K, K2, k, u, r;
+};
+
+int check_option(const or_option_t& o) {
+  if (!(o.N >= 1) || !(o.S0 > 0) || !(o.sigma > 0) || !(o.T > 0) || !(o.k >= 0) || !(o.k < 1) ||
+      !(o.K >= 0) || !std::isfinite(o.R) || o.payoff < 0 || o.payoff > 2)
+    return OR_ERR_ARG;
+  if (o.payoff == PAY_SPREAD && !(o.K2 >= o.K)) return OR_ERR_ARG;
+  const double dt = o.T / o.N;
+  const double u = std::exp(o.sigma * std::sqrt(dt));
+  const double d = 1.0 / u;
+  const double r = std::exp(o.R * dt);
+  if (!(d < r && r < u)) return OR_ERR_ARBITRAGE;
+  return OR_OK;
+}
+
+template <class T>
+Model<T> make_model(const or_option_t& o, const T& S0, const T& K, const T& sigma, const T& R,
+                    const T& Tm, const T& k) {
+  Model<T> m;
+  m.N = o.N;
+  m.payoff = o.payoff;
+  m.S0 = S0;
+  m.K = K;
+  m.K2 = T(o.K2) + (K - T(o.K));  // the spread's width is held fixed when K moves
+  m.k = k;
+  T dt = Tm / T((double)o.N);
+  m.u = dexp(sigma * dsqrt(dt));
+  m.r = dexp(R * dt);
+  return m;
+}
+
+template <class T>
+T stock(const Model<T>& m, int t, int j) { return m.S0 * dpowi(m.u, 2 * j - t); }
+
+template <class T>
+void payoff_at(const Model<T>& m, const T& S, T& xi, T& zeta) {
+  if (m.payoff == PAY_PUT) { xi = m.K; zeta = T(-1.0); }
+  else if (m.payoff == PAY_CALL) { xi = -m.K; zeta = T(1.0); }
+  else {
+    T a = (val(S) > val(m.K)) ? S - m.K : T(0.0);
+    T b = (val(S) > val(m.K2)) ? S - m.K2 : T(0.0);
+    xi = a - b;
+    zeta = T(0.0);
+  }
+}
+
+struct Stats {
+  int64_t nodes = 0;
+  int64_t bp_seller = 0, bp_buyer = 0;   // sum of breakpoints over all computed nodes
+  int max_seller = 0, max_buyer = 0;
+  std::vector<int64_t>* per_level = nullptr;  // optional: [2*(N+2)] sums by level
+};
+
+template <class T>
+int price_tc(const Model<T>& m, T& ask, T& bid, Stats* st) {
+  const int N = m.N;
+  std::vector<PL<T>> zs(N + 2), zb(N + 2);
+  // level N+1: payoff (0, 0) for both parties; costs apply there.
+  for (int j = 0; j <= N + 1; ++j) {
+    T S = stock(m, N + 1, j);
+    T Sa = (T(1.0) + m.k) * S, Sb = (T(1.0) - m.k) * S;
+    zs[j] = pl_expense(T(0.0), T(0.0), Sa, Sb, false);
+    zb[j] = pl_expense(T(0.0), T(0.0), Sa, Sb, true);
+  }
+  for (int t = N; t >= 0; --t) {
+    for (int j = 0; j <= t; ++j) {  // ascending j: slot j+1 still holds level t+1
+      T S = stock(m, t, j);
+      T kt = (t == 0) ? T(0.0) : m.k;
+      T Sa = (T(1.0) + kt) * S, Sb = (T(1.0) - kt) * S;
+      T xi, zeta;
+      payoff_at(m, S, xi, zeta);
+      PL<T> ns, nb;
+      int rc = node_step(zs[j + 1], zs[j], m.r, Sa, Sb, xi, zeta, false, ns);
+      if (rc) return rc;
+      rc = node_step(zb[j + 1], zb[j], m.r, Sa, Sb, xi, zeta, true, nb);
+      if (rc) return rc;
+      zs[j] = std::move(ns);
+      zb[j] = std::move(nb);
+      if (st) {
+        st->nodes += 1;
+        const int ms = (int)zs[j].y.size(), mb = (int)zb[j].y.size();
+        st->bp_seller += ms;
+        st->bp_buyer += mb;
+        st->max_seller = std::max(st->max_seller, ms);
+        st->max_buyer = std::max(st->max_buyer, mb);
+        if (st->per_level) {
+          (*st->per_level)[2 * t] += ms;
+          (*st->per_level)[2 * t + 1] += mb;
+        }
+      }
+    }
+  }
+  ask = pl_eval(zs[0], T(0.0));
+  bid = -pl_eval(zb[0], T(0.0));
+  return OR_OK;
+}
+
+// Plain CRR recursion without costs (Section 3, Appendix): N levels, no extra
+// level; exercise value P_t = K - S (put), S - K (call), spread payoff.
+double crr_payoff(int payoff, double S, double K, double K2) {
+  if (payoff == PAY_PUT) return K - S;
+  if (payoff == PAY_CALL) return S - K;
+  return std::max(S - K, 0.0) - std::max(S - K2, 0.0);
+}
+
+double price_crr(const or_option_t& o, bool american) {
+  const int N = o.N;
+  const double dt = o.T / N;
+  const double u = std::exp(o.sigma * std::sqrt(dt));
+  const double d = 1.0 / u;
+  const double r = std::exp(o.R * dt);
+  const double p = (r - d) / (u - d);
+  std::vector<double> c(N + 1);
+  for (int j = 0; j <= N; ++j)
+    c[j] = std::max(crr_payoff(o.payoff, o.S0 * std::pow(u, 2 * j - N), o.K, o.K2), 0.0);
+  for (int t = N - 1; t >= 0; --t) {
+    for (int j = 0; j <= t; ++j) {
+      const double cont = (p * c[j + 1] + (1.0 - p) * c[j]) / r;
+      c[j] = american ? std::max(crr_payoff(o.payoff, o.S0 * std::pow(u, 2 * j - t), o.K, o.K2), cont)
+                      : cont;
+    }
+  }
+  return c[0];
+}
+
+template <class F>
+void parallel_for(int64_t n, int nthreads, F fn) {
+  if (nthreads <= 1 || n <= 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nthreads; ++w)
+    pool.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+template <class T>
+PL<T> pl_from(const double* y, const double* f, int m, double sL, double sR) {
+  PL<T> F;
+  for (int i = 0; i < m; ++i) { F.y.push_back(T(y[i])); F.f.push_back(T(f[i])); }
+  F.sL = T(sL);
+  F.sR = T(sR);
+  return F;
+}
+
+int pl_to(const PL<double>& F, double* y, double* f, int cap, double* sL, double* sR) {
+  const int m = (int)F.y.size();
+  if (m > cap) return OR_ERR_CAPACITY;
+  for (int i = 0; i < m; ++i) { y[i] = F.y[i]; f[i] = F.f[i]; }
+  *sL = F.sL;
+  *sR = F.sR;
+  return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ask/bid of each option by the piecewise-linear induction; out[2i] = ask,
+// out[2i+1] = bid; status[i] = 0 or a negative error code.
+int or_price_tc(const or_option_t* opts, int64_t n, double* out, int32_t* status, int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    const or_option_t& o = opts[i];
+    int rc = check_option(o);
+    double ask = NAN, bid = NAN;
+    if (rc == OR_OK) {
+      Model<double> m = make_model<double>(o, o.S0, o.K, o.sigma, o.R, o.T, o.k);
+      rc = price_tc(m, ask, bid, nullptr);
+    }
+    out[2 * i] = ask;
+    out[2 * i + 1] = bid;
+    if (status) status[i] = rc;
+  });
+  return OR_OK;
+}
+
+// Breakpoint statistics of one option's induction: counts[0] = nodes,
+// [1] = sum of seller breakpoints, [2] = sum of buyer breakpoints,
+// [3] = max seller, [4] = max buyer.  per_level (may be NULL) receives
+// 2*(N+1) sums: [2t] seller, [2t+1] buyer, for t = 0..N.
+int or_tc_stats(const or_option_t* o, int64_t* counts, int64_t* per_level) {
+  int rc = check_option(*o);
+  if (rc) return rc;
+  Model<double> m = make_model<double>(*o, o->S0, o->K, o->sigma, o->R, o->T, o->k);
+  Stats st;
+  std::vector<int64_t> pl(2 * (o->N + 1), 0);
+  st.per_level = &pl;
+  double ask, bid;
+  rc = price_tc(m, ask, bid, &st);
+  if (rc) return rc;
+  counts[0] = st.nodes;
+  counts[1] = st.bp_seller;
+  counts[2] = st.bp_buyer;
+  counts[3] = st.max_seller;
+  counts[4] = st.max_buyer;
+  if (per_level) std::memcpy(per_level, pl.data(), pl.size() * sizeof(int64_t));
+  return OR_OK;
+}
+
+// Derivatives of ask and bid by forward-mode dual numbers:
+// grad[12i + 0..5] = d ask / d(S0, K, sigma, R, T, k), grad[12i + 6..11] = d bid / d(...).
+int or_greeks_tc(const or_option_t* opts, int64_t n, double* out, double* grad, int32_t* status,
+                 int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    const or_option_t& o = opts[i];
+    int rc = check_option(o);
+    Dual ask, bid;
+    if (rc == OR_OK) {
+      Dual in[NG];
+      const double base[NG] = {o.S0, o.K, o.sigma, o.R, o.T, o.k};
+      for (int a = 0; a < NG; ++a) { in[a] = Dual(base[a]); in[a].g[a] = 1.0; }
+      Model<Dual> m = make_model<Dual>(o, in[0], in[1], in[2], in[3], in[4], in[5]);
+      rc = price_tc(m, ask, bid, nullptr);
+    }
+    out[2 * i] = rc ? NAN : ask.v;
+    out[2 * i + 1] = rc ? NAN : bid.v;
+    for (int a = 0; a < NG; ++a) {
+      grad[12 * i + a] = rc ? NAN : ask.g[a];
+      grad[12 * i + 6 + a] = rc ? NAN : bid.g[a];
+    }
+    if (status) status[i] = rc;
+  });
+  return OR_OK;
+}
+
+// Plain CRR price without costs; american = 0 gives the European price.
+int or_price_crr(const or_option_t* opts, int64_t n, double* out, int32_t* status, int american,
+                 int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    int rc = check_option(opts[i]);
+    out[i] = rc ? NAN : price_crr(opts[i], american != 0);
+    if (status) status[i] = rc;
+  });
+  return OR_OK;
+}
+
+// ---- single primitives on explicit PL functions (for unit tests) ----
+int or_pl_envelope(const double* y1, const double* f1, int m1, double sL1, double sR1,
+                   const double* y2, const double* f2, int m2, double sL2, double sR2, int take_max,
+                   double* yo, double* fo, int cap, double* sLo, double* sRo) {
+  if (m1 < 1 || m2 < 1) return OR_ERR_ARG;
+  PL<double> F = pl_from<double>(y1, f1, m1, sL1, sR1), G = pl_from<double>(y2, f2, m2, sL2, sR2);
+  return pl_to(pl_envelope(F, G, take_max != 0), yo, fo, cap, sLo, sRo);
+}
+
+int or_pl_restrict(const double* y, const double* f, int m, double sL, double sR, double Sa,
+                   double Sb, double* yo, double* fo, int cap, double* sLo, double* sRo) {
+  if (m < 1) return OR_ERR_ARG;
+  PL<double> F = pl_from<double>(y, f, m, sL, sR), V;
+  int rc = pl_restrict(F, Sa, Sb, V);
+  if (rc) return rc;
+  return pl_to(V, yo, fo, cap, sLo, sRo);
+}
+
+int or_pl_eval(const double* y, const double* f, int m, double sL, double sR, const double* x,
+               int nx, double* out) {
+  if (m < 1) return OR_ERR_ARG;
+  PL<double> F = pl_from<double>(y, f, m, sL, sR);
+  for (int i = 0; i < nx; ++i) out[i] = pl_eval(F, x[i]);
+  return OR_OK;
+}
+
+// One node of the induction from explicit successor functions.
+int or_node_step(const double* yu, const double* fu, int mu, double sLu, double sRu,
+                 const double* yd, const double* fd, int md, double sLd, double sRd, double r,
+                 double Sa, double Sb, double xi, double zeta, int buyer, double* yo, double* fo,
+                 int cap, double* sLo, double* sRo) {
+  if (mu < 1 || md < 1) return OR_ERR_ARG;
+  PL<double> U = pl_from<double>(yu, fu, mu, sLu, sRu), D = pl_from<double>(yd, fd, md, sLd, sRd);
+  PL<double> z;
+  int rc = node_step(U, D, r, Sa, Sb, xi, zeta, buyer != 0, z);
+  if (rc) return rc;
+  return pl_to(z, yo, fo, cap, sLo, sRo);
+}
+
+}  // extern "C"
