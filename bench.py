@@ -1,0 +1,292 @@
+"""Benchmark: batched ask/bid pricing of 4096 uneven American options with
+proportional transaction costs, FP64, one persistent launch per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is tree node updates per second
+(ask and bid together; (N+1)(N+2)/2 updates per option), device-timed with
+CUDA events on the launching stream, inputs resident in HBM.  `e2e` is the
+same metric through the host-buffer C-ABI call (pinned host buffers, copies
+inside the timed region).  `--impl reference` times the CPU oracle on the
+host cores on a bounded sample of the same workload.
+
+Under torchrun each rank prices its own batch of the same distribution
+(weak scaling, no collective on the data path); the max over ranks of the
+timed region sets the job time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "tree node updates/s (ask+bid, FP64) batched; options/s with Greeks vs plain"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 dense FP64 (profiling recipe); see the design doc
+CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(table, seed=7):
+    """The CPU oracle, as it stands, on a bounded random sample of the batch, all host cores."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(table), CPU_SAMPLE, replace=False)
+    sample = table[idx]
+    cores = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.price_ask_bid(sample, nthreads=cores)
+    dt = time.perf_counter() - t0
+    nodes = int(np.sum(W.node_updates(sample)))
+    return {"value": nodes / dt, "unit": "node updates/s", "cores": cores, "kind": "oracle",
+            "sample": "%d random options of the 4096-option batch (seed %d), %d node updates, %.1f s"
+                      % (CPU_SAMPLE, seed, nodes, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    table = W.batched_uneven()
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    samples = [table[rng.choice(len(table), 16, replace=False)] for _ in range(args.warmup + args.steps)]
+    for s in samples[:args.warmup]:
+        oracle.price_ask_bid(s[:2], nthreads=cores)
+    nodes = 0
+    t0 = time.perf_counter()
+    for s in samples[args.warmup:]:
+        oracle.price_ask_bid(s, nthreads=cores)
+        nodes += int(np.sum(W.node_updates(s)))
+    dt = time.perf_counter() - t0
+    v = nodes / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "node updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched uneven 4096 (N~U{100..2000}, put/call/spread)",
+                       "sample_per_step": "16 random options of the batch"},
+            "cpu_baseline": {"value": v, "unit": "node updates/s", "cores": cores, "kind": "oracle",
+                             "sample": "16 random options per step of the 4096-option batch"},
+            "e2e": {"value": v, "unit": "node updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    from paper_1110_2477_gb300 import _build
+    _build.build()
+    ob.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    table = W.batched_uneven() if rank == 0 else W.random_table(4096, 3 + 1000 * rank)
+    n = len(table)
+    nodes_per_step = int(np.sum(W.node_updates(table)))
+    params = ob.to_device(table, dev)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB of L2
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        ob.ob_price_ask_bid(params, n, out, st, stream)
+    torch.cuda.synchronize(dev)
+    assert int((st != 0).sum().item()) == 0, "options failed: %s" % st[st != 0][:8].tolist()
+    stats = ob.ob_get_stats()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ob.ob_price_ask_bid(params, n, out, st, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    job_s = max_over_ranks(dev_s, world)
+    value = world * nodes_per_step * args.steps / job_s
+
+    # end to end through the host-buffer call: copies of inputs and results inside
+    pin_in = torch.from_numpy(table.view(np.uint8).reshape(-1).copy()).pin_memory()
+    pin_in_np = pin_in.numpy().view(W.OPTION_DTYPE)
+    pin_out = torch.empty((n, 2), dtype=torch.float64).pin_memory()
+    pin_st = torch.empty(n, dtype=torch.int32).pin_memory()
+    ob.ob_price_ask_bid_host(pin_in_np, pin_out.numpy(), pin_st.numpy())
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ob.ob_price_ask_bid_host(pin_in_np, pin_out.numpy(), pin_st.numpy())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * nodes_per_step * args.steps / e2e_s, "unit": "node updates/s",
+           "h2d_bytes_per_step": int(table.nbytes),
+           "d2h_bytes_per_step": int(pin_out.numel() * 8 + pin_st.numel() * 4)}
+
+    # plain single-option kernel on the same batch (one warp per option, no queue)
+    ob.ob_price_ask_bid_plain(params, n, out, st, stream)
+    torch.cuda.synchronize(dev)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(stream)
+    ob.ob_price_ask_bid_plain(params, n, out, st, stream)
+    pb.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_s = pa.elapsed_time(pb) / 1e3
+
+    if rank != 0:
+        return
+    avg_step = dev_s / args.steps
+    alg_flops = 2.0 * stats["u_points"] + 4.0 * stats["w_points"] + 2.0 * stats["z_points"]
+    achieved = alg_flops / avg_step / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "node updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "batched uneven 4096: N~U{100..2000}, S0,K~U[80,120], sigma~U[0.1,0.5], "
+                               "R~U[0,0.1], T~U[0.1,2], k~U[0,0.02], put/call/bull spread (width 10), seed 3",
+                   "options": n, "node_updates_per_step": nodes_per_step,
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": "replicas (one batch per GPU)"},
+        "options_per_s": world * n * args.steps / job_s,
+        "plain": {"value": nodes_per_step / plain_s, "unit": "node updates/s",
+                  "options_per_s": n / plain_s, "kernel": "one warp per option, index order"},
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "note": "algorithmic FP64 flops = 2U + 4W + 2Z per step (U successor points "
+                             "merged, W points of w, Z points of z), FP64 peak nominal"},
+        "breakpoints": {"u_points": stats["u_points"], "w_points": stats["w_points"],
+                        "z_points": stats["z_points"], "max_level_points": stats["max_level_points"],
+                        "retried": stats["retried"]},
+        "step_ms": step_ms, "wall_s": wall, "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(table)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,132 @@
+/* ob.h -- C ABI of the GB300 ask/bid pricer for American options under
+ * proportional transaction costs.
+ *
+ * What is computed (Zhang, Roux & Zastawniak, "Parallel Binomial American
+ * Option Pricing with (and without) Transaction Costs", 2011):
+ *   - Section 4.1: a recombining binomial tree with N steps,
+ *     u = exp(sigma*sqrt(T/N)), d = 1/u, r = exp(R*T/N), plus an extra time
+ *     instant N+1 whose N+2 nodes carry the payoff (0,0); no transaction costs
+ *     at t = 0.
+ *   - Section 3: stock bought at S^a = (1+k)S and sold at S^b = (1-k)S; the
+ *     seller's expense function (Eq. 1) and the buyer's (Eq. 6); the backward
+ *     induction w_t = max of the successors' functions, discount by r,
+ *     restriction of the slopes to [-S^a_t, -S^b_t], then z_t = max(u_t, v_t)
+ *     (seller, Roux & Zastawniak Algorithm 3.1) or z_t = min(u_t, v_t) (buyer,
+ *     Algorithm 3.5).  ask = z_0(0), bid = -z'_0(0).
+ *   - Section 3 (first paragraph) and the Appendix: without costs the same
+ *     numbers equal the plain CRR American price, computed by the scalar
+ *     recursion pi_t = max(P_t, (p pi^u + (1-p) pi^d)/r) over N levels.
+ * All arithmetic is IEEE binary64.
+ *
+ * Threading: calls may come from any host thread; a call that needs the
+ * library's scratch pool on a device serialises on an internal mutex only
+ * while the pool is (re)allocated.  Kernels run asynchronously on the given
+ * stream.
+ */
+#ifndef OB_H_
+#define OB_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One option, 64 bytes, host byte order, tightly packed.  Field meaning:
+ *   S0     stock price at t = 0 (> 0)
+ *   K      strike (>= 0); for the bull spread the long call's strike
+ *   K2     bull spread only: the short call's strike (>= K); ignored otherwise
+ *   sigma  volatility (> 0), R continuously compounded annual rate (finite),
+ *   T      expiry in years (> 0), k cost rate, 0 <= k < 1
+ *   N      time steps (>= 1)
+ *   payoff OB_PUT: payoff process (K, -1), physical delivery (Section 3);
+ *          OB_CALL: (-K, +1), physical delivery;
+ *          OB_SPREAD: cash-settled bull spread, xi = (S-K)^+ - (S-K2)^+,
+ *          zeta = 0 (Section 5). */
+typedef struct {
+  double S0, K, K2, sigma, R, T, k;
+  int32_t N, payoff;
+} ob_option_t;
+
+enum { OB_PUT = 0, OB_CALL = 1, OB_SPREAD = 2 };
+
+/* Status / return codes. */
+enum {
+  OB_OK = 0,
+  OB_ERR_ARG = -1,       /* a parameter outside the ranges above, or bad pointers/sizes */
+  OB_ERR_ARBITRAGE = -2, /* d < r < u fails, so the tree model admits arbitrage */
+  OB_ERR_CAPACITY = -3,  /* the option's piecewise-linear functions outgrew the scratch pool */
+  OB_ERR_TIMEOUT = -4,   /* a bounded device wait expired */
+  OB_ERR_CUDA = -5,      /* a CUDA runtime call failed (see ob_last_cuda_error) */
+  OB_ERR_NOMEM = -6      /* the scratch pool could not be allocated */
+};
+
+/* Ask and bid of n_options options (Section 3, Algorithms 3.1 / 3.5).
+ *   params  DEVICE pointer, n_options records, read only.
+ *   out     DEVICE pointer, 2*n_options doubles: out[2i] = ask, out[2i+1] = bid.
+ *   status  DEVICE pointer to n_options int32 (may be NULL): OB_OK or the
+ *           option's error code; an option that fails leaves NaN in out and
+ *           does not stop the others.
+ *   stream  cudaStream_t (NULL = legacy default stream).
+ * Batched form: one persistent launch whose warps take options from a device
+ * queue, costliest first (work stealing); options whose functions outgrow a
+ * warp's scratch are retried by follow-up launches with larger scratch, on
+ * the same stream, without returning to the host.  Asynchronous: returns
+ * OB_OK once the work is enqueued, or an error code (nothing enqueued) for
+ * bad arguments, allocation failure or a launch error.  The library's scratch
+ * pool is allocated on the first call on a device (cudaMalloc, so make that
+ * call before any stream capture) and kept until ob_release(). */
+int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                     void* stream);
+
+/* The plain form of the same computation: one warp per option, options taken
+ * in index order with a static assignment, no queue and no retry (an option
+ * that outgrows its warp's scratch gets OB_ERR_CAPACITY).  Arguments and
+ * results as for ob_price_ask_bid.  This is the single-option kernel the
+ * batched form is compared against. */
+int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double* out,
+                           int32_t* status, void* stream);
+
+/* Plain CRR American price without transaction costs (the Appendix): the
+ * scalar recursion over N levels, no extra level; k is ignored.
+ *   out  DEVICE pointer, n_options doubles.  Other arguments as above. */
+int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                    void* stream);
+
+/* Host-buffer convenience form of ob_price_ask_bid: params, out (2*n) and
+ * status (n, may be NULL) are HOST pointers; the call copies the inputs to
+ * the device, runs the batched form on an internal stream, copies the results
+ * back and returns after they have arrived.  Pinned host memory makes the
+ * copies faster but is not required. */
+int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* out,
+                          int32_t* status);
+
+/* Counters of the most recent ob_price_ask_bid / _plain call on the current
+ * device.  Call after that work has completed (synchronise its stream). */
+typedef struct {
+  int64_t options;        /* options processed (any status) */
+  int64_t node_updates;   /* (N+1)(N+2)/2 summed over successfully priced options */
+  int64_t u_points;       /* successor breakpoints merged into the maxima w, both parties */
+  int64_t w_points;       /* breakpoints of all successor maxima w, both parties */
+  int64_t z_points;       /* breakpoints of all node functions z, both parties */
+  int32_t max_level_points; /* largest number of breakpoints held by one tree level */
+  int32_t retried;        /* options that needed a follow-up launch with larger scratch */
+  int32_t failed;         /* options with a nonzero status */
+  int32_t tiers;          /* launches enqueued by the call */
+} ob_stats_t;
+int ob_get_stats(ob_stats_t* host_out);
+
+/* Release the current device's scratch pool (synchronises the device). */
+int ob_release(void);
+
+/* Human-readable text of a status code; never NULL. */
+const char* ob_strerror(int code);
+
+/* The CUDA error string of the last OB_ERR_CUDA returned on this thread. */
+const char* ob_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OB_H_ */

@@ -1,0 +1,512 @@
+// ob_lib.cu -- kernels and the C ABI declared in include/ob.h.
+//
+//  k_order  one CTA sorts the option indices by estimated cost (largest first)
+//  k_tc     persistent warps: each warp takes an option from a device queue and
+//           runs the piecewise-linear induction (ob_tc.cuh) in its own slice of
+//           the scratch pool; an option that outgrows the slice is appended to
+//           an overflow list that the next launch (fewer warps, larger slices)
+//           takes over, on the same stream
+//  k_crr    persistent warps: plain CRR recursion without costs, the level kept
+//           in shared memory and updated in place
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "ob.h"
+#include "ob_tc.cuh"
+
+namespace {
+
+constexpr int kBlock = 128;          // 4 warps per CTA
+constexpr int kTiers = 3;            // launches per ob_price_ask_bid call
+constexpr int kTier1Workers = 64;    // warps of the first follow-up launch
+constexpr int kSortMax = 8192;       // largest batch ordered by cost
+constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
+
+struct DevStats {
+  unsigned long long options, node_updates, upts, wpts, zpts;
+  int max_level, retried, failed, tiers;
+};
+
+static_assert(sizeof(ob_option_t) == 64, "ob_option_t must be 64 bytes");
+static_assert(sizeof(obk::Opt) == 64, "Opt must be 64 bytes");
+
+__device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+__device__ __forceinline__ int check_option(const obk::Opt& o, bool need_k) {
+  if (!(o.N >= 1) || o.N > (1 << 26) || !(o.S0 > 0.0) || !(o.sigma > 0.0) || !(o.T > 0.0) ||
+      !(o.K >= 0.0) || !isfinite(o.R) || !isfinite(o.S0) || !isfinite(o.K) || !isfinite(o.sigma) ||
+      !isfinite(o.T) || o.payoff < 0 || o.payoff > 2)
+    return obk::ST_ARG;
+  if (need_k && !(o.k >= 0.0 && o.k < 1.0)) return obk::ST_ARG;
+  if (o.payoff == obk::PAY_SPREAD && !(o.K2 >= o.K && isfinite(o.K2))) return obk::ST_ARG;
+  return obk::ST_OK;
+}
+
+// ------------------------------------------------------------------ ordering
+// Bitonic sort of (cost, index) keys, descending, in one CTA.
+__global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int* __restrict__ order) {
+  extern __shared__ unsigned long long keys[];
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+    unsigned long long key = 0;
+    if (i < n) {
+      const long long N = opts[i].N > 0 ? opts[i].N : 1;
+      const int w = opts[i].payoff == obk::PAY_PUT ? 1 : (opts[i].payoff == obk::PAY_CALL ? 2 : 3);
+      unsigned long long cost = (unsigned long long)((N + 1) * (N + 2) / 2) * w;
+      if (cost > (1ULL << 43)) cost = 1ULL << 43;
+      key = ((cost + 1) << 20) | (unsigned long long)i;
+    }
+    keys[i] = key;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npad; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool desc = (i & size) == 0;
+          const unsigned long long a = keys[i], b = keys[j];
+          if ((a < b) == desc) { keys[i] = b; keys[j] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(keys[i] & 0xFFFFF);
+}
+
+// ------------------------------------------------------------------ induction with costs
+__global__ void __launch_bounds__(kBlock) k_tc(const obk::Opt* __restrict__ opts, int n,
+                                               const int* __restrict__ order, double* out, int* status,
+                                               char* arena, size_t wbytes, int nworkers, int* ctl,
+                                               int tier, const int* in_list, int* out_list, int last,
+                                               int plain, DevStats* ds) {
+  obk::WarpTeam tm;
+  const int lane = tm.lane();
+  const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (wid >= nworkers) return;
+  char* my = arena + (size_t)wid * wbytes;
+  const int count = (tier == 0) ? n : *((volatile int*)&ctl[2 * (tier - 1) + 1]);
+  int next_static = wid;
+  for (;;) {
+    int idx;
+    if (plain) {
+      idx = next_static;
+      next_static += nworkers;
+    } else {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(&ctl[2 * tier], 1);
+      idx = tm.shfl(v, 0);
+    }
+    if (idx >= count) break;
+    const int oi = (tier == 0) ? (order ? order[idx] : idx) : in_list[idx];
+    const obk::Opt o = opts[oi];
+    int rc = check_option(o, true);
+    double ask = dnan(), bid = dnan();
+    obk::Stats st;
+    st.upts = st.wpts = st.zpts = 0;
+    st.zmax_level = 0;
+    if (rc == obk::ST_OK) {
+      obk::Lay L;
+      if (!obk::carve(my, wbytes, o.N, 2 * (o.N + 2), L)) {
+        rc = obk::ST_CAPACITY;
+      } else {
+        obk::TcRun<obk::WarpTeam> R(tm, o, L);
+        rc = R.run(ask, bid);
+        st = R.st;
+      }
+    }
+    if (lane == 0) {
+      if (rc == obk::ST_CAPACITY && !last) {
+        const int pos = atomicAdd(&ctl[2 * tier + 1], 1);
+        out_list[pos] = oi;
+        atomicAdd(&ds->retried, 1);
+      } else {
+        out[2 * oi] = rc ? dnan() : ask;
+        out[2 * oi + 1] = rc ? dnan() : bid;
+        if (status) status[oi] = rc;
+        atomicAdd(&ds->options, 1ULL);
+        if (rc == obk::ST_OK) {
+          const unsigned long long N = (unsigned long long)o.N;
+          atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
+          atomicAdd(&ds->upts, (unsigned long long)st.upts);
+          atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
+          atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
+          atomicMax(&ds->max_level, st.zmax_level);
+        } else {
+          atomicAdd(&ds->failed, 1);
+        }
+      }
+    }
+    tm.sync();  // the next option reuses the slice
+  }
+}
+
+// ------------------------------------------------------------------ plain CRR
+// c_{t,j} = max(P_{t,j}, pu c_{t+1,j+1} + pd c_{t+1,j}), pu = p/r, pd = (1-p)/r;
+// P is tabulated per option by stock exponent e = 2j - t (max(payoff, 0)).
+// Lanes take interleaved nodes so that shared-memory and table accesses are
+// unit-stride; the up-successor value comes from the neighbour lane.
+__device__ __forceinline__ double crr_payoff(const obk::Opt& o, double S) {
+  double v;
+  if (o.payoff == obk::PAY_PUT) v = o.K - S;
+  else if (o.payoff == obk::PAY_CALL) v = S - o.K;
+  else v = fmax(S - o.K, 0.0) - fmax(S - o.K2, 0.0);
+  return fmax(v, 0.0);
+}
+
+__global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opts, int n, double* out,
+                                                int* status, char* arena, size_t wbytes, int nworkers,
+                                                int* ctl) {
+  extern __shared__ double crr_sm[];
+  obk::WarpTeam tm;
+  const int lane = tm.lane();
+  const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (wid >= nworkers) return;
+  double* mysm = crr_sm + (size_t)(threadIdx.x >> 5) * kCrrSmem;
+  char* my = arena + (size_t)wid * wbytes;
+  for (;;) {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(&ctl[0], 1);
+    const int oi = tm.shfl(v, 0);
+    if (oi >= n) break;
+    const obk::Opt o = opts[oi];
+    int rc = check_option(o, false);
+    double res = dnan();
+    if (rc == obk::ST_OK) {
+      const int N = o.N;
+      const double dt = o.T / N;
+      const double u = exp(o.sigma * sqrt(dt));
+      const double d = 1.0 / u;
+      const double r = exp(o.R * dt);
+      const size_t ptab_bytes = obk::al256(sizeof(double) * (2 * (size_t)N + 1));
+      const bool in_smem = (N + 2) <= kCrrSmem;
+      const size_t need = ptab_bytes + (in_smem ? 0 : sizeof(double) * ((size_t)N + 2));
+      if (!(d < r && r < u)) {
+        rc = obk::ST_ARBITRAGE;
+      } else if (need > wbytes) {
+        rc = obk::ST_CAPACITY;
+      } else {
+        const double p = (r - d) / (u - d);
+        const double pu = p / r, pd = (1.0 - p) / r;
+        double* P = (double*)my;  // P[e + N], e = -N..N
+        double* V = in_smem ? mysm : (double*)(my + ptab_bytes);
+        for (int e = lane; e <= 2 * N; e += 32) P[e] = crr_payoff(o, o.S0 * pow(u, (double)(e - N)));
+        tm.sync();
+        for (int j = lane; j <= N; j += 32) V[j] = P[2 * j];
+        tm.sync();
+        for (int t = N - 1; t >= 0; --t) {
+          const int width = t + 1;  // nodes of level t; level t+1 holds width+1 values
+          const double* Pt = P + (N - t);
+          for (int base = 0; base < width; base += 32) {
+            const int i = base + lane;
+            const double cur = (i <= width) ? V[i] : 0.0;
+            double up = tm.shfl_down(cur, 1);
+            const double extra = (base + 32 <= width) ? V[base + 32] : 0.0;
+            if (lane == 31) up = extra;
+            tm.sync();
+            if (i < width) {
+              const double cont = pu * up + pd * cur;
+              const double ex = Pt[2 * i];
+              V[i] = (__double_as_longlong(cont) > __double_as_longlong(ex)) ? cont : ex;
+            }
+            tm.sync();
+          }
+        }
+        res = V[0];
+        tm.sync();
+      }
+    }
+    if (lane == 0) {
+      out[oi] = res;
+      if (status) status[oi] = rc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", cudaGetErrorString(e));
+  return OB_ERR_CUDA;
+}
+
+struct DevPool {
+  bool init = false;
+  int sms = 0;
+  int warps_per_sm = 16;
+  size_t arena_per_warp = 8ull << 20;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
+  int* order = nullptr;    // kSortMax
+  int* lists = nullptr;    // 2 overflow lists of list_cap
+  size_t list_cap = 0;
+  DevStats* stats = nullptr;
+  // host-buffer entry point
+  cudaStream_t hstream = nullptr;
+  ob_option_t* hparams = nullptr;
+  double* hout = nullptr;
+  int* hstatus = nullptr;
+  size_t hcap = 0;
+  int last_tiers = 0;
+};
+
+std::mutex g_mu;
+DevPool g_pool[64];
+
+size_t env_size(const char* name, size_t dflt) {
+  const char* s = getenv(name);
+  if (!s || !*s) return dflt;
+  const long long v = atoll(s);
+  return v > 0 ? (size_t)v : dflt;
+}
+
+int pool_get(DevPool** out, size_t need_list) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= 64) return OB_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevPool& P = g_pool[dev];
+  if (!P.init) {
+    e = cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    P.warps_per_sm = (int)env_size("OB_WARPS_PER_SM", 16);
+    P.arena_per_warp = env_size("OB_ARENA_MB", 8) << 20;
+    const size_t workers = (size_t)P.sms * P.warps_per_sm;
+    P.arena_bytes = workers * P.arena_per_warp;
+    if (cudaMalloc(&P.arena, P.arena_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      P.arena = nullptr;
+      return OB_ERR_NOMEM;
+    }
+    if (cudaMalloc(&P.ctl, sizeof(int) * 2 * kTiers) != cudaSuccess ||
+        cudaMalloc(&P.order, sizeof(int) * kSortMax) != cudaSuccess ||
+        cudaMalloc(&P.stats, sizeof(DevStats)) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+    cudaMemset(P.stats, 0, sizeof(DevStats));
+    e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(unsigned long long) * kSortMax));
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaFuncSetAttribute(k_crr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * kCrrSmem * (kBlock / 32)));
+    if (e != cudaSuccess) return cuda_fail(e);
+    P.init = true;
+  }
+  if (need_list > P.list_cap) {
+    if (P.lists) cudaFree(P.lists);
+    P.lists = nullptr;
+    P.list_cap = 0;
+    if (cudaMalloc(&P.lists, sizeof(int) * 2 * need_list) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+    P.list_cap = need_list;
+  }
+  *out = &P;
+  return OB_OK;
+}
+
+int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* status, void* stream,
+              bool plain) {
+  if (n64 < 0 || n64 > (1 << 30)) return OB_ERR_ARG;
+  if (n64 == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  const int n = (int)n64;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, (size_t)n);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * 2 * kTiers, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
+  const obk::Opt* opts = (const obk::Opt*)params;
+  const int* order = nullptr;
+  if (!plain && n <= kSortMax && n > 1) {
+    int npad = 1;
+    while (npad < n) npad <<= 1;
+    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    order = P->order;
+  }
+  const int max_workers = P->sms * P->warps_per_sm;
+  const int w0 = n < max_workers ? n : max_workers;
+  int* list0 = P->lists;
+  int* list1 = P->lists + P->list_cap;
+  const int tiers = plain ? 1 : kTiers;
+  for (int tier = 0; tier < tiers; ++tier) {
+    int workers;
+    size_t wbytes;
+    const int* in_list = nullptr;
+    int* out_list = nullptr;
+    if (tier == 0) {
+      workers = w0;
+      wbytes = P->arena_per_warp;
+      out_list = list0;
+    } else if (tier == 1) {
+      workers = kTier1Workers;
+      wbytes = (P->arena_bytes / kTier1Workers) & ~(size_t)255;
+      in_list = list0;
+      out_list = list1;
+    } else {
+      workers = 1;
+      wbytes = P->arena_bytes & ~(size_t)255;
+      in_list = list1;
+    }
+    const int blocks = (workers * 32 + kBlock - 1) / kBlock;
+    k_tc<<<blocks, kBlock, 0, s>>>(opts, n, order, out, status, P->arena, wbytes, workers, P->ctl,
+                                   tier, in_list, out_list, tier == tiers - 1 ? 1 : 0, plain ? 1 : 0,
+                                   P->stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  }
+  P->last_tiers = tiers;
+  return OB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                     void* stream) {
+  return launch_tc(params, n_options, out, status, stream, false);
+}
+
+int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double* out,
+                           int32_t* status, void* stream) {
+  return launch_tc(params, n_options, out, status, stream, true);
+}
+
+int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                    void* stream) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  const int n = (int)n_options;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, 1);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * 2 * kTiers, s)) != cudaSuccess) return cuda_fail(e);
+  const int max_workers = P->sms * 12;  // 3 CTAs of 4 warps per SM fit the shared memory
+  const int workers = n < max_workers ? n : max_workers;
+  const size_t wbytes = (P->arena_bytes / (size_t)workers) & ~(size_t)255;
+  const int blocks = (workers * 32 + kBlock - 1) / kBlock;
+  k_crr<<<blocks, kBlock, sizeof(double) * kCrrSmem * (kBlock / 32), s>>>(
+      (const obk::Opt*)params, n, out, status, P->arena, wbytes, workers, P->ctl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  return OB_OK;
+}
+
+int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* out,
+                          int32_t* status) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, (size_t)n_options);
+  if (rc) return rc;
+  cudaError_t e;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!P->hstream) {
+      if ((e = cudaStreamCreateWithFlags(&P->hstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e);
+    }
+    if ((size_t)n_options > P->hcap) {
+      cudaFree(P->hparams);
+      cudaFree(P->hout);
+      cudaFree(P->hstatus);
+      P->hparams = nullptr; P->hout = nullptr; P->hstatus = nullptr; P->hcap = 0;
+      if (cudaMalloc(&P->hparams, sizeof(ob_option_t) * n_options) != cudaSuccess ||
+          cudaMalloc(&P->hout, sizeof(double) * 2 * n_options) != cudaSuccess ||
+          cudaMalloc(&P->hstatus, sizeof(int) * n_options) != cudaSuccess) {
+        cudaGetLastError();
+        return OB_ERR_NOMEM;
+      }
+      P->hcap = (size_t)n_options;
+    }
+  }
+  cudaStream_t s = P->hstream;
+  if ((e = cudaMemcpyAsync(P->hparams, params, sizeof(ob_option_t) * n_options,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e);
+  rc = launch_tc(P->hparams, n_options, P->hout, P->hstatus, s, false);
+  if (rc) return rc;
+  if ((e = cudaMemcpyAsync(out, P->hout, sizeof(double) * 2 * n_options, cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess)
+    return cuda_fail(e);
+  if (status && (e = cudaMemcpyAsync(status, P->hstatus, sizeof(int) * n_options,
+                                     cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+  return OB_OK;
+}
+
+int ob_get_stats(ob_stats_t* host_out) {
+  if (!host_out) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, 1);
+  if (rc) return rc;
+  DevStats d;
+  cudaError_t e = cudaMemcpy(&d, P->stats, sizeof(d), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  host_out->options = (int64_t)d.options;
+  host_out->node_updates = (int64_t)d.node_updates;
+  host_out->u_points = (int64_t)d.upts;
+  host_out->w_points = (int64_t)d.wpts;
+  host_out->z_points = (int64_t)d.zpts;
+  host_out->max_level_points = d.max_level;
+  host_out->retried = d.retried;
+  host_out->failed = d.failed;
+  host_out->tiers = P->last_tiers;
+  return OB_OK;
+}
+
+int ob_release(void) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevPool& P = g_pool[dev];
+  if (!P.init) return OB_OK;
+  cudaDeviceSynchronize();
+  cudaFree(P.arena);
+  cudaFree(P.ctl);
+  cudaFree(P.order);
+  cudaFree(P.lists);
+  cudaFree(P.stats);
+  cudaFree(P.hparams);
+  cudaFree(P.hout);
+  cudaFree(P.hstatus);
+  if (P.hstream) cudaStreamDestroy(P.hstream);
+  P = DevPool();
+  return OB_OK;
+}
+
+const char* ob_strerror(int code) {
+  switch (code) {
+    case OB_OK: return "ok";
+    case OB_ERR_ARG: return "invalid argument or option parameter";
+    case OB_ERR_ARBITRAGE: return "tree admits arbitrage (d < r < u fails)";
+    case OB_ERR_CAPACITY: return "piecewise-linear functions outgrew the scratch pool";
+    case OB_ERR_TIMEOUT: return "bounded device wait expired";
+    case OB_ERR_CUDA: return "CUDA runtime error";
+    case OB_ERR_NOMEM: return "scratch pool allocation failed";
+    default: return "unknown status code";
+  }
+}
+
+const char* ob_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

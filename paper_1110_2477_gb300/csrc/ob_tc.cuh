@@ -1,0 +1,749 @@
+// ob_tc.cuh -- the level-by-level backward induction of the seller's (ask) and
+// buyer's (bid) piecewise-linear functions on a recombining binomial tree
+// (Zhang, Roux & Zastawniak, Section 3 and Section 4.1; the sequential
+// procedures are Roux & Zastawniak's Algorithms 3.1 and 3.5), written as
+// element-parallel passes for one team of threads (a warp) working on one
+// option.
+//
+// Representation.  A node function is a list of breakpoints (y, value,
+// slope to the right of y).  Its left-tail slope is always -S^a_t and its
+// right-tail slope -S^b_t (both children's tails bracket the window whenever
+// d < r < u, so the restriction clips them), so tails are not stored.
+// Values are kept in "future-value" units: a value at level t is multiplied by
+// lambda_t = r^(N+1-t).  Discounting w_t by r then costs nothing, and a slope
+// is never rescaled once created, so two pieces with the same origin keep
+// bitwise-equal slopes and a breakpoint between them can be dropped exactly.
+//
+// One level t (from level t+1):
+//   pass 1  for each breakpoint of the two successors (a merge of their sorted
+//           lists): evaluate both successors there, keep w = max(z_up, z_down),
+//           insert the crossings between neighbouring points and in the tails.
+//   pass 2  g = w + S^a y and h = w + S^b y at every point of w, then the
+//           running minima cA (suffix, from the right) and cB (prefix, from the
+//           left) per node, as segmented scans on integer keys.
+//   pass 3  for every piece of w: the restriction
+//             v = min( w-line, cA_{i+1} - S^a y, cB_i - S^b y )
+//           (the inf-convolution v(y) = inf_y' [w(y') + theta(y' - y)] split into
+//           buying and selling; on the left tail v is the cA line, on the right
+//           tail the cB line), then z = max(u, v) for the seller or
+//           z = min(u, v) for the buyer, with u the expense function (Eq. 1,
+//           Eq. 6).  A point is emitted only where the slope changes.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "ob_team.cuh"
+
+namespace obk {
+
+enum { ST_OK = 0, ST_ARG = -1, ST_ARBITRAGE = -2, ST_CAPACITY = -3 };
+enum { PAY_PUT = 0, PAY_CALL = 1, PAY_SPREAD = 2 };
+
+struct Opt {
+  double S0, K, K2, sigma, R, T, k;
+  int32_t N, payoff;
+};
+
+struct Stats {
+  long long upts;        // successor breakpoints merged (union points) over all levels
+  long long wpts, zpts;  // points of w and of z summed over all levels (both parties)
+  int zmax_level;        // largest number of z points in one level
+  int zmax_node;         // not tracked per node (reserved)
+};
+
+// Per-option scratch carved from one worker's arena.
+struct Lay {
+  double* Stab;   // [2N+3]   S0 u^e, e = -(N+1)..N+1 at index e+N+1
+  double* lam;    // [N+2]    lambda_t = r^(N+1-t)
+  double* nt[2];  // [4(N+2)] per node of a level: S^a lambda, S^b lambda, xi lambda
+  int* off[2];    // [2(N+2)+1] first point of each node (seller nodes, then buyer nodes)
+  double *zY[2], *zF[2], *zS[2];
+  int* offw;      // [2(N+1)+1]
+  int* wN;        // node of each point of w
+  double *wY, *wF, *wS, *wG, *wH;
+  long long *wCA, *wCB;
+  int capZ, capW;
+};
+
+OB_HD size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bytes of the per-option node arrays for N steps.
+OB_HD size_t node_bytes(int N) {
+  size_t n = 0;
+  n += al256(sizeof(double) * (2 * (size_t)N + 3));
+  n += al256(sizeof(double) * ((size_t)N + 2));
+  n += 2 * al256(sizeof(double) * 4 * ((size_t)N + 2));
+  n += 2 * al256(sizeof(int) * (2 * ((size_t)N + 2) + 1));
+  n += al256(sizeof(int) * (2 * ((size_t)N + 1) + 1));
+  return n;
+}
+
+constexpr size_t ELEM_BYTES = 2 * 3 * sizeof(double) + 5 * sizeof(double) + 2 * sizeof(long long) +
+                              sizeof(int);
+
+// Carve an arena of `bytes` for an option with N steps.  Returns false when the
+// arena cannot hold the node arrays and at least min_cap points per array.
+OB_HD bool carve(char* base, size_t bytes, int N, int min_cap, Lay& L) {
+  size_t nb = node_bytes(N) + 16 * 256;
+  if (bytes < nb) return false;
+  size_t cap = (bytes - nb) / ELEM_BYTES;
+  if (cap > 0x3fffffff) cap = 0x3fffffff;
+  if ((long long)cap < (long long)min_cap) return false;
+  char* p = base;
+  auto take = [&](size_t sz) { char* r = p; p += al256(sz); return r; };
+  L.Stab = (double*)take(sizeof(double) * (2 * (size_t)N + 3));
+  L.lam = (double*)take(sizeof(double) * ((size_t)N + 2));
+  for (int b = 0; b < 2; ++b) L.nt[b] = (double*)take(sizeof(double) * 4 * ((size_t)N + 2));
+  for (int b = 0; b < 2; ++b) L.off[b] = (int*)take(sizeof(int) * (2 * ((size_t)N + 2) + 1));
+  L.offw = (int*)take(sizeof(int) * (2 * ((size_t)N + 1) + 1));
+  for (int b = 0; b < 2; ++b) {
+    L.zY[b] = (double*)take(sizeof(double) * cap);
+    L.zF[b] = (double*)take(sizeof(double) * cap);
+    L.zS[b] = (double*)take(sizeof(double) * cap);
+  }
+  L.wY = (double*)take(sizeof(double) * cap);
+  L.wF = (double*)take(sizeof(double) * cap);
+  L.wS = (double*)take(sizeof(double) * cap);
+  L.wG = (double*)take(sizeof(double) * cap);
+  L.wH = (double*)take(sizeof(double) * cap);
+  L.wCA = (long long*)take(sizeof(long long) * cap);
+  L.wCB = (long long*)take(sizeof(long long) * cap);
+  L.wN = (int*)take(sizeof(int) * cap);
+  L.capZ = (int)cap;
+  L.capW = (int)cap;
+  return (size_t)(p - base) <= bytes;
+}
+
+OB_HD double ob_inf() { return bitsd(0x7FF0000000000000LL); }
+
+struct Em {
+  double y, f, s;
+};
+
+// Value at x of the successor function piece anchored at its breakpoint k
+// (k = -1: the left tail, anchored at the first breakpoint).
+OB_HD double seg_eval(const double* Y, const double* F, const double* S, int k, double tailL,
+                      double x) {
+  return (k >= 0) ? F[k] + S[k] * (x - Y[k]) : F[0] + tailL * (x - Y[0]);
+}
+
+// ------------------------------------------------------------------ pass 1
+// One union point of w = max(A, B) (A = up successor, B = down successor).
+// The owner of every segment between two neighbouring union points is decided
+// once, by the point at its left end (own), and handed to the point at its right
+// end, which needs it as the owner just left of itself; so the two ends never
+// disagree about a crossing that rounds onto a breakpoint.
+struct P1 {
+  double y, a, b, aL, aR, bL, bR;
+  double xr, vr, sr;  // crossing before the next union point
+  double xl, vl, sl;  // crossing in the left tail (first union point of a node)
+  int wr;             // owner just right of y
+  int own;            // owner just left of the next union point
+  int wl_first;       // owner just left of y, first union point only
+  bool dup, rc, lc;
+};
+
+// q is the index in the merged breakpoint order (ties: A first).
+OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int ma, double aTL,
+                      const double* By, const double* Bf, const double* Bs, int mb, double bTL,
+                      int q, P1& e) {
+  e.dup = e.rc = e.lc = false;
+  e.own = e.wr = e.wl_first = 0;
+  int lo = q - mb > 0 ? q - mb : 0, hi = q < ma ? q : ma;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (kle(Ay[mid], By[q - 1 - mid])) lo = mid + 1; else hi = mid;
+  }
+  const int iu = lo, id = q - lo;
+  const bool fromA = iu < ma && (id >= mb || kle(Ay[iu], By[id]));
+  double y;
+  bool aBp, bBp;
+  int ia = -1, ib = -1;
+  if (fromA) {
+    ia = iu;
+    y = Ay[ia];
+    aBp = true;
+    bBp = id < mb && keq(By[id], y);
+    if (bBp) ib = id;
+  } else {
+    ib = id;
+    y = By[ib];
+    bBp = true;
+    if (iu > 0 && keq(Ay[iu - 1], y)) {  // already represented by A's point
+      e.dup = true;
+      return;
+    }
+    aBp = false;
+  }
+  const int ka = aBp ? ia : iu - 1;  // last breakpoint of A at or before y
+  const int kb = bBp ? ib : id - 1;
+  double a, aL, aR, b, bL, bR;
+  if (aBp) {
+    a = Af[ia];
+    aL = ia > 0 ? As[ia - 1] : aTL;
+    aR = As[ia];
+  } else {
+    a = seg_eval(Ay, Af, As, ka, aTL, y);
+    aL = aR = (ka >= 0 ? As[ka] : aTL);
+  }
+  if (bBp) {
+    b = Bf[ib];
+    bL = ib > 0 ? Bs[ib - 1] : bTL;
+    bR = Bs[ib];
+  } else {
+    b = seg_eval(By, Bf, Bs, kb, bTL, y);
+    bL = bR = (kb >= 0 ? Bs[kb] : bTL);
+  }
+  e.y = y; e.a = a; e.b = b; e.aL = aL; e.aR = aR; e.bL = bL; e.bR = bR;
+  // next union point
+  const int na = aBp ? ia + 1 : iu;
+  const int nb = bBp ? ib + 1 : id;
+  const bool hasA = na < ma, hasB = nb < mb;
+  bool nA = false, nB = false;
+  double yn = 0.0;
+  if (hasA && hasB) {
+    const long long ka2 = okey(Ay[na]), kb2 = okey(By[nb]);
+    if (ka2 <= kb2) { yn = Ay[na]; nA = true; }
+    if (kb2 <= ka2) { yn = By[nb]; nB = true; }
+  } else if (hasA) {
+    yn = Ay[na];
+    nA = true;
+  } else if (hasB) {
+    yn = By[nb];
+    nB = true;
+  }
+  const bool hasNext = nA || nB;
+  const long long kA = okey(a), kB = okey(b);
+  int wr = (kA != kB) ? (kA > kB ? 0 : 1) : (klt(bR, aR) ? 0 : (klt(aR, bR) ? 1 : 0));
+  if (q == 0) {  // the far left belongs to the successor with the smaller left slope
+    int wl = (kA != kB) ? (kA > kB ? 0 : 1) : (klt(aL, bL) ? 0 : (klt(bL, aL) ? 1 : 0));
+    const int farL = klt(aL, bL) ? 0 : (klt(bL, aL) ? 1 : wl);
+    if (farL != wl) {
+      const double vW = wl ? b : a, vO = wl ? a : b, sW = wl ? bL : aL, sO = wl ? aL : bL;
+      const double x = y + (vW - vO) / (sO - sW);
+      if (klt(x, y)) {
+        e.lc = true;
+        e.xl = x;
+        e.vl = vW + sW * (x - y);
+        e.sl = sW;
+      } else {
+        wl = farL;
+      }
+    }
+    e.wl_first = wl;
+  }
+  // Does the loser overtake before the next union point?  Cheap test: who is larger
+  // there; only then the crossing itself is computed.
+  int wn;
+  if (hasNext) {
+    const double an = nA ? Af[na] : seg_eval(Ay, Af, As, ka, aTL, yn);
+    const double bn = nB ? Bf[nb] : seg_eval(By, Bf, Bs, kb, bTL, yn);
+    const long long kAn = okey(an), kBn = okey(bn);
+    wn = (kAn != kBn) ? (kAn > kBn ? 0 : 1) : wr;
+  } else {  // the far right belongs to the larger right slope
+    wn = klt(bR, aR) ? 0 : (klt(aR, bR) ? 1 : wr);
+  }
+  int own = wr;
+  if (wn != wr) {
+    const double vW = wr ? b : a, vO = wr ? a : b, sW = wr ? bR : aR, sO = wr ? aR : bR;
+    if (klt(sW, sO)) {  // the loser climbs faster: it overtakes at x
+      const double x = y + (vW - vO) / (sO - sW);
+      if (!klt(y, x)) {
+        wr = own = 1 - wr;  // the crossing rounds onto y
+      } else if (!hasNext || klt(x, yn)) {
+        e.rc = true;
+        e.xr = x;
+        e.vr = vW + sW * (x - y);
+        e.sr = sO;
+        own = 1 - wr;
+      }  // else: it rounds onto the next point, the whole segment stays with wr
+    }
+  }
+  e.wr = wr;
+  e.own = own;
+}
+
+// Emissions of an analysed union point, given the owner just left of it.
+OB_HD int p1_emit(const P1& e, int wl, Em* em) {
+  int n = 0;
+  if (e.dup) return 0;
+  if (e.lc) em[n++] = Em{e.xl, e.vl, e.sl};
+  const double sLw = wl ? e.bL : e.aL, sRw = e.wr ? e.bR : e.aR;
+  if (!same_bits(sLw, sRw)) em[n++] = Em{e.y, (okey(e.a) >= okey(e.b)) ? e.a : e.b, sRw};
+  if (e.rc) em[n++] = Em{e.xr, e.vr, e.sr};
+  return n;
+}
+
+// ------------------------------------------------------------------ pass 3 helpers
+// A line of the restriction/exercise step.  Point-slope form anchored at x0
+// (exact there); an F line (a piece of w) is also exact at its right end x1.
+struct Ln {
+  double x0, v0, s, x1, v1;
+  int icpt;  // 1: intercept form, value = v0 + s*x
+};
+
+OB_HD double ln_eval(const Ln& l, double x) {
+  if (l.icpt) return l.v0 + l.s * x;
+  if (same_bits(x, l.x0)) return l.v0;
+  if (same_bits(x, l.x1)) return l.v1;
+  return l.v0 + l.s * (x - l.x0);
+}
+
+constexpr int MAXSUB = 10;
+
+struct Subs {
+  double xs[MAXSUB];  // start of each sub-piece (xs[0] may be -inf)
+  int li[MAXSUB];     // line of each sub-piece
+  int ns;
+  double hi;          // end of the last sub-piece (may be +inf)
+};
+
+// Split the sub-piece containing x (strictly inside) at x.
+OB_HD void subs_split(Subs& S, double x) {
+  for (int k = 0; k < S.ns; ++k) {
+    const double e = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
+    if (klt(S.xs[k], x) && klt(x, e)) {
+      for (int m = S.ns; m > k + 1; --m) {
+        S.xs[m] = S.xs[m - 1];
+        S.li[m] = S.li[m - 1];
+      }
+      S.xs[k + 1] = x;
+      S.li[k + 1] = S.li[k];
+      S.ns += 1;
+      return;
+    }
+  }
+}
+
+// Replace every sub-piece line P by max(P, Q) (take_max) or min(P, Q), Q = lines[qi(k)],
+// where qi(k) = q_left if the sub-piece lies left of xq, else q_right.
+OB_HD void subs_combine(Subs& S, const Ln* lines, int q_left, int q_right, double xq,
+                        bool take_max) {
+  Subs O;
+  O.ns = 0;
+  O.hi = S.hi;
+  const double INF = ob_inf();
+  for (int k = 0; k < S.ns; ++k) {
+    const double x0 = S.xs[k];
+    const double x1 = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
+    const int pi = S.li[k];
+    const int qi = klt(x0, xq) ? q_left : q_right;
+    if (pi == qi) {
+      O.xs[O.ns] = x0; O.li[O.ns] = pi; ++O.ns;
+      continue;
+    }
+    const Ln& P = lines[pi];
+    const Ln& Q = lines[qi];
+    const bool finite0 = !same_bits(x0, -INF), finite1 = !same_bits(x1, INF);
+    double p0 = 0, q0 = 0, p1 = 0, q1 = 0;
+    if (finite0) { p0 = ln_eval(P, x0); q0 = ln_eval(Q, x0); }
+    if (finite1) { p1 = ln_eval(P, x1); q1 = ln_eval(Q, x1); }
+    const long long kps = okey(P.s), kqs = okey(Q.s);
+    int wl, wr;  // 0 = P, 1 = Q
+    if (finite0) {
+      const long long a = okey(p0), b = okey(q0);
+      if (a != b) wl = ((a > b) == take_max) ? 0 : 1;
+      else wl = (kps == kqs) ? 0 : (((kps > kqs) == take_max) ? 0 : 1);  // right-side tie-break
+    } else {
+      if (kps != kqs) wl = ((kps < kqs) == take_max) ? 0 : 1;
+      else { const long long a = okey(p1), b = okey(q1); wl = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+    }
+    if (finite1) {
+      const long long a = okey(p1), b = okey(q1);
+      if (a != b) wr = ((a > b) == take_max) ? 0 : 1;
+      else wr = (kps == kqs) ? 0 : (((kps < kqs) == take_max) ? 0 : 1);  // left-side tie-break
+    } else {
+      if (kps != kqs) wr = ((kps > kqs) == take_max) ? 0 : 1;
+      else { const long long a = okey(p0), b = okey(q0); wr = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+    }
+    const int lw = wl ? qi : pi;
+    if (wl == wr || kps == kqs) {
+      O.xs[O.ns] = x0; O.li[O.ns] = lw; ++O.ns;
+      continue;
+    }
+    // The end values disagree, so the lines cross; which line owns each side of the
+    // crossing follows from the slopes (left of it the smaller slope is larger), so a
+    // tie at one end that rounding tipped the wrong way cannot misplace the piece.
+    double x;
+    if (finite0) x = x0 + (p0 - q0) / (Q.s - P.s);
+    else x = x1 + (p1 - q1) / (Q.s - P.s);
+    const int left_line = ((kps < kqs) == take_max) ? pi : qi;
+    const int right_line = (left_line == pi) ? qi : pi;
+    if (!klt(x0, x)) {
+      O.xs[O.ns] = x0; O.li[O.ns] = right_line; ++O.ns;
+    } else if (!klt(x, x1)) {
+      O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
+    } else {
+      O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
+      O.xs[O.ns] = x; O.li[O.ns] = right_line; ++O.ns;
+    }
+  }
+  S = O;
+}
+
+// ------------------------------------------------------------------ the option
+template <class Team>
+struct TcRun {
+  const Team& tm;
+  const Opt& o;
+  const Lay& L;
+  int N;
+  int zeta;  // -1 put, +1 call, 0 spread
+  Stats st;
+
+  OB_HD TcRun(const Team& tm_, const Opt& o_, const Lay& L_) : tm(tm_), o(o_), L(L_), N(o_.N) {
+    zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
+    st.upts = st.wpts = st.zpts = 0;
+    st.zmax_level = 0;
+    st.zmax_node = 0;
+  }
+
+  // exclusive prefix sum over the team; returns the prefix, sets the total
+  OB_HD int excl_sum(int v, int& total) const {
+    const int lane = tm.lane();
+    int x = v;
+    for (int d = 1; d < Team::W; d <<= 1) {
+      const int y = tm.shfl_up(x, d);
+      if (lane >= d) x += y;
+    }
+    total = tm.shfl(x, Team::W - 1);
+    return x - v;
+  }
+
+  // segmented inclusive min-scan of keys across the team, lane order; heads start segments
+  OB_HD long long seg_min(long long v, bool head, long long& carry) const {
+    const int lane = tm.lane();
+    int fl = head ? 1 : 0;
+    for (int d = 1; d < Team::W; d <<= 1) {
+      const long long vu = tm.shfl_up(v, d);
+      const int fu = tm.shfl_up(fl, d);
+      if (lane >= d) {
+        if (!fl) v = kmin(v, vu);
+        fl |= fu;
+      }
+    }
+    if (!fl) v = kmin(v, carry);
+    carry = tm.shfl(v, Team::W - 1);
+    return v;
+  }
+
+  OB_HD void node_table(int t) {
+    const int lane = tm.lane();
+    double* nt = L.nt[t & 1];
+    const double lam = L.lam[t];
+    const double kt = (t == 0) ? 0.0 : o.k;
+    for (int j = lane; j <= t; j += Team::W) {
+      const double S = L.Stab[2 * j - t + N + 1];
+      const double Sl = S * lam;
+      nt[4 * j] = Sl * (1.0 + kt);
+      nt[4 * j + 1] = Sl * (1.0 - kt);
+      double xi;
+      if (o.payoff == PAY_PUT) xi = o.K;
+      else if (o.payoff == PAY_CALL) xi = -o.K;
+      else xi = fmax(S - o.K, 0.0) - fmax(S - o.K2, 0.0);
+      nt[4 * j + 2] = xi * lam;
+    }
+  }
+
+  // union start of node (p, j) of level t; j in [0, t+1]
+  OB_HD int ustart(const int* o1, int W1, int UB1, int p, int j) const {
+    const int* op = o1 + p * W1;
+    return (p ? UB1 : 0) + (op[j] - op[0]) + (op[j + 1] - op[1]);
+  }
+
+  // pass 1: w = max(z_up, z_down) for every node of level t; returns false on overflow
+  OB_HD bool pass1(int t, int& wtot, int& utot) {
+    const int lane = tm.lane();
+    const int b1 = (t + 1) & 1;
+    const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
+    const int* o1 = L.off[b1];
+    const double *Y1 = L.zY[b1], *F1 = L.zF[b1], *S1 = L.zS[b1];
+    const double* nt1 = L.nt[b1];
+    const int UB1 = ustart(o1, W1, 0, 0, W0);
+    const int Utot = ustart(o1, W1, UB1, 1, W0);
+    utot = Utot;
+    int ncur = 0, wpos = 0, carry_own = 0;
+    bool ovf = false;
+    for (int base = 0; base < Utot; base += Team::W) {
+      const int q = base + lane;
+      const int nl = ncur + lane;
+      int nend = 0x7fffffff;
+      if (nl < nNodes) {
+        const int p = nl >= W0 ? 1 : 0;
+        nend = ustart(o1, W1, UB1, p, nl - p * W0 + 1);
+      }
+      // node of q: number of node ends <= q among the 32 loaded (ends are increasing)
+      int pos = 0;
+      for (int step = Team::W / 2; step >= 1; step >>= 1) {
+        const int v = tm.shfl(nend, pos + step - 1);
+        if (v <= q) pos += step;
+      }
+      {
+        const int v = tm.shfl(nend, Team::W - 1);
+        if (pos == Team::W - 1 && v <= q) pos = Team::W;
+      }
+      const int ncur_next = ncur + popc32(tm.ballot(nend <= base + Team::W));
+      Em em[3];
+      P1 e;
+      e.dup = true;
+      int cnt = 0, node = ncur + pos, ql = -1;
+      if (q < Utot) {
+        const int p = node >= W0 ? 1 : 0;
+        const int j = node - p * W0;
+        ql = q - ustart(o1, W1, UB1, p, j);
+        const int* op = o1 + p * W1;
+        const int aoff = op[j + 1], ma = op[j + 2] - aoff;
+        const int boff = op[j], mb = aoff - boff;
+        p1_analyze(Y1 + aoff, F1 + aoff, S1 + aoff, ma, -nt1[4 * (j + 1)], Y1 + boff, F1 + boff,
+                   S1 + boff, mb, -nt1[4 * j], ql, e);
+      }
+      // owner of the segment ending at this point: that of the previous union point,
+      // forwarded across a duplicate (duplicates are never adjacent)
+      int own = e.own;
+      int v1 = tm.shfl_up(own, 1);
+      if (lane == 0) v1 = carry_own;
+      if (q < Utot && e.dup) own = v1;
+      int v2 = tm.shfl_up(own, 1);
+      if (lane == 0) v2 = carry_own;
+      carry_own = tm.shfl(own, Team::W - 1);
+      if (q < Utot) cnt = p1_emit(e, ql == 0 ? e.wl_first : v2, em);
+      int total;
+      const int pre = excl_sum(cnt, total);
+      const int p0 = wpos + pre;
+      if (q < Utot && ql == 0) L.offw[node] = p0;
+      if (p0 + cnt <= L.capW) {
+        for (int c = 0; c < cnt; ++c) {
+          L.wY[p0 + c] = em[c].y;
+          L.wF[p0 + c] = em[c].f;
+          L.wS[p0 + c] = em[c].s;
+          L.wN[p0 + c] = node;
+        }
+      } else if (cnt > 0) {
+        ovf = true;
+      }
+      wpos += total;
+      ncur = ncur_next;
+    }
+    if (lane == 0) L.offw[nNodes] = wpos;
+    wtot = wpos;
+    tm.sync();
+    return !(tm.ballot(ovf) != 0u || wpos > L.capW);
+  }
+
+  // pass 2: g, h and the per-node running minima of their keys
+  OB_HD void pass2(int t, int wtot) {
+    const int lane = tm.lane();
+    const int W0 = t + 1;
+    const double* nt = L.nt[t & 1];
+    const long long KMAX = 0x7fffffffffffffffLL;
+    long long carry = KMAX;
+    for (int base = 0; base < wtot; base += Team::W) {
+      const int i = base + lane;
+      const bool ok = i < wtot;
+      const int n = ok ? L.wN[i] : -1;
+      const bool head = ok && (i == 0 || L.wN[i - 1] != n);
+      long long hk = KMAX;
+      if (ok) {
+        const int j = n >= W0 ? n - W0 : n;
+        const double y = L.wY[i], f = L.wF[i];
+        const double g = f + nt[4 * j] * y, h = f + nt[4 * j + 1] * y;
+        L.wG[i] = g;
+        L.wH[i] = h;
+        hk = okey(h);
+      }
+      const long long v = seg_min(hk, head, carry);
+      if (ok) L.wCB[i] = v;
+    }
+    tm.sync();
+    carry = KMAX;
+    const int ntiles = (wtot + Team::W - 1) / Team::W;
+    for (int tile = ntiles - 1; tile >= 0; --tile) {
+      const int i = tile * Team::W + (Team::W - 1 - lane);
+      const bool ok = i < wtot;
+      const int n = ok ? L.wN[i] : -1;
+      const bool head = ok && (i + 1 == wtot || L.wN[i + 1] != n);
+      const long long gk = ok ? okey(L.wG[i]) : KMAX;
+      const long long v = seg_min(gk, head, carry);
+      if (ok) L.wCA[i] = v;
+    }
+    tm.sync();
+  }
+
+  // pass 3: restriction and exercise for every piece of w; writes level t
+  OB_HD bool pass3(int t, int wtot, int& ztot) {
+    const int lane = tm.lane();
+    const int bt = t & 1, W0 = t + 1, nNodes = 2 * W0;
+    const double* nt = L.nt[bt];
+    const double INF = ob_inf();
+    int* off = L.off[bt];
+    double* Yz = L.zY[bt];
+    double* Fz = L.zF[bt];
+    double* Sz = L.zS[bt];
+    int zpos = 0;
+    bool ovf = false;
+    double carry_slope = 0.0;
+    for (int base = 0; base < wtot; base += Team::W) {
+      const int i = base + lane;
+      const bool ok = i < wtot;
+      Em em[2 * MAXSUB + 1];
+      int ntl = 0, nm = 0;  // internal emissions of the left tail and of the main piece
+      Em first{0.0, 0.0, 0.0};
+      double last_slope = 0.0, tail_slope = 0.0;
+      bool head = false, anchor = false;
+      int node = -1;
+      if (ok) {
+        node = L.wN[i];
+        head = (i == 0 || L.wN[i - 1] != node);
+        const bool tail = (i + 1 == wtot || L.wN[i + 1] != node);
+        const int p = node >= W0 ? 1 : 0;
+        const int j = node - p * W0;
+        const double Sa = nt[4 * j], Sb = nt[4 * j + 1], xi = nt[4 * j + 2];
+        const bool seller = (p == 0);
+        const double yu = seller ? (double)zeta : -(double)zeta;
+        const double vu = seller ? xi : -xi;
+        anchor = head && same_bits(Sa, Sb);
+        const double y0 = L.wY[i], f0 = L.wF[i], s0 = L.wS[i];
+        const long long cB = L.wCB[i];
+        // line table: 0 piece of w, 1 cA line (slope -S^a), 2 cB line (slope -S^b),
+        //             3 left branch of u (slope -S^a), 4 right branch of u (slope -S^b)
+        Ln lines[5];
+        lines[2] = Ln{0.0, unkey(cB), -Sb, 0.0, 0.0, 1};
+        lines[3] = Ln{yu, vu, -Sa, INF, 0.0, 0};
+        lines[4] = Ln{yu, vu, -Sb, INF, 0.0, 0};
+        if (head) {  // left tail: v is the cA_0 line
+          lines[1] = Ln{0.0, unkey(L.wCA[i]), -Sa, 0.0, 0.0, 1};
+          Subs S;
+          S.ns = 1;
+          S.xs[0] = -INF;
+          S.li[0] = 1;
+          S.hi = y0;
+          if (klt(yu, y0)) subs_split(S, yu);
+          subs_combine(S, lines, 3, 4, yu, seller);
+          for (int k = 1; k < S.ns; ++k) {
+            const Ln& l = lines[S.li[k]];
+            if (!same_bits(l.s, lines[S.li[k - 1]].s)) em[ntl++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+          }
+          tail_slope = lines[S.li[S.ns - 1]].s;
+        }
+        Subs S;
+        S.ns = 1;
+        S.xs[0] = y0;
+        if (tail) {  // right tail: v is the cB line
+          S.li[0] = 2;
+          S.hi = INF;
+        } else {
+          const double y1 = L.wY[i + 1], f1 = L.wF[i + 1];
+          const long long cA1 = L.wCA[i + 1];
+          const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
+          const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
+          lines[0] = Ln{y0, f0, s0, y1, f1, 0};
+          lines[1] = Ln{0.0, unkey(cA1), -Sa, 0.0, 0.0, 1};
+          S.li[0] = 0;
+          S.hi = y1;
+          // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
+          // the cB line iff h <= cB_i at both ends (then that side of v equals w)
+          const bool Arel = !(g1 == cA1 && g0 <= cA1);
+          const bool Brel = !(h0 == cB && h1 <= cB);
+          if (Brel) subs_combine(S, lines, 2, 2, INF, false);
+          if (Arel) subs_combine(S, lines, 1, 1, INF, false);
+        }
+        if (klt(y0, yu) && klt(yu, S.hi)) subs_split(S, yu);
+        subs_combine(S, lines, 3, 4, yu, seller);
+        first = Em{y0, ln_eval(lines[S.li[0]], y0), lines[S.li[0]].s};
+        for (int k = 1; k < S.ns; ++k) {
+          const Ln& l = lines[S.li[k]];
+          if (!same_bits(l.s, lines[S.li[k - 1]].s))
+            em[ntl + 1 + nm++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+        }
+        last_slope = lines[S.li[S.ns - 1]].s;
+      }
+      // slope of z just left of this piece's first point
+      double prev = tm.shfl_up(last_slope, 1);
+      if (lane == 0) prev = carry_slope;
+      if (head) prev = tail_slope;
+      const int emit_first = (ok && (anchor || !same_bits(prev, first.s))) ? 1 : 0;
+      const int nout = ok ? ntl + emit_first + nm : 0;
+      int total;
+      const int pre = excl_sum(nout, total);
+      const int p0 = zpos + pre;
+      if (ok && head) off[node] = p0;
+      if (ok) {
+        if (p0 + nout <= L.capZ) {
+          int w = p0;
+          for (int c = 0; c < ntl; ++c, ++w) { Yz[w] = em[c].y; Fz[w] = em[c].f; Sz[w] = em[c].s; }
+          if (emit_first) { Yz[w] = first.y; Fz[w] = first.f; Sz[w] = first.s; ++w; }
+          for (int c = 0; c < nm; ++c, ++w) {
+            Yz[w] = em[ntl + 1 + c].y; Fz[w] = em[ntl + 1 + c].f; Sz[w] = em[ntl + 1 + c].s;
+          }
+        } else if (nout > 0) {
+          ovf = true;
+        }
+      }
+      carry_slope = tm.shfl(last_slope, Team::W - 1);
+      zpos += total;
+    }
+    if (lane == 0) off[nNodes] = zpos;
+    ztot = zpos;
+    tm.sync();
+    return !(tm.ballot(ovf) != 0u || zpos > L.capZ);
+  }
+
+  // value at y = 0 of node n of level 0 (bank 0)
+  OB_HD double root_value(int n) const {
+    const int b = L.off[0][n], e = L.off[0][n + 1];
+    const double tailL = -L.nt[0][0];
+    if (e <= b) return 0.0;
+    if (!klt(L.zY[0][b], 0.0)) return L.zF[0][b] + tailL * (0.0 - L.zY[0][b]);
+    int k = b;
+    while (k + 1 < e && kle(L.zY[0][k + 1], 0.0)) ++k;
+    return L.zF[0][k] + L.zS[0][k] * (0.0 - L.zY[0][k]);
+  }
+
+  // Full induction for one option; returns a status code, writes ask and bid.
+  OB_HD int run(double& ask, double& bid) {
+    const int lane = tm.lane();
+    ask = bid = 0.0;
+    const double dt = o.T / N;
+    const double u = exp(o.sigma * sqrt(dt));
+    const double r = exp(o.R * dt);
+    const double d = 1.0 / u;
+    if (!(d < r && r < u)) return ST_ARBITRAGE;
+    for (int e = lane; e < 2 * N + 3; e += Team::W) L.Stab[e] = o.S0 * pow(u, (double)(e - (N + 1)));
+    for (int t = lane; t <= N + 1; t += Team::W) L.lam[t] = pow(r, (double)(N + 1 - t));
+    tm.sync();
+    // level N+1: payoff (0,0) for both parties: one point (0, 0, -S^b)
+    {
+      const int b = (N + 1) & 1, W = N + 2;
+      node_table(N + 1);
+      tm.sync();
+      for (int n = lane; n < 2 * W; n += Team::W) {
+        const int j = n >= W ? n - W : n;
+        L.off[b][n] = n;
+        L.zY[b][n] = 0.0;
+        L.zF[b][n] = 0.0;
+        L.zS[b][n] = -L.nt[b][4 * j + 1];
+      }
+      if (lane == 0) L.off[b][2 * W] = 2 * W;
+      tm.sync();
+    }
+    if (2 * (N + 2) > L.capZ) return ST_CAPACITY;
+    for (int t = N; t >= 0; --t) {
+      node_table(t);
+      tm.sync();
+      int wtot = 0, ztot = 0, utot = 0;
+      if (!pass1(t, wtot, utot)) return ST_CAPACITY;
+      st.upts += utot;
+      pass2(t, wtot);
+      if (!pass3(t, wtot, ztot)) return ST_CAPACITY;
+      st.wpts += wtot;
+      st.zpts += ztot;
+      if (ztot > st.zmax_level) st.zmax_level = ztot;
+    }
+    const double lam0 = L.lam[0];
+    ask = root_value(0) / lam0;
+    bid = -root_value(1) / lam0;
+    return ST_OK;
+  }
+};
+
+}  // namespace obk

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerance (prices): |gpu - oracle| <= 1e-10 * max(|oracle|, 1e-2 K).  The
+absolute floor keeps deep out-of-the-money bids (~0) meaningful.  The oracle
+agrees with exact rational arithmetic to ~1e-15, the GPU keeps values in
+future-value units and evaluates pieces by fused multiply-add, so both sit
+within a few hundred ulps of the exact recursion; 1e-10 leaves room for the
+ill-conditioned crossings of nearly parallel pieces.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def _ob():
+    import paper_1110_2477_gb300 as ob
+    return ob
+
+
+def _close(got, ref, K):
+    scale = np.maximum(np.abs(ref), 1e-2 * np.asarray(K)[..., None] if ref.ndim == 2 else 1e-2 * np.asarray(K))
+    return np.abs(got - ref) <= RTOL * scale
+
+
+def _gpu(table, plain=False):
+    import torch
+    ob = _ob()
+    out, st = ob.price(table, plain=plain)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), st.cpu().numpy()
+
+
+def _assert_parity(table, out, st, ref, rst):
+    assert np.array_equal(st, rst), (st, rst)
+    ok = _close(out, ref, table["K"])
+    ok |= (np.isnan(out) & np.isnan(ref))
+    bad = np.argwhere(~ok)
+    assert bad.size == 0, [(int(i), out[i].tolist(), ref[i].tolist(), table[i]) for i, _ in bad[:5]]
+
+
+def test_config1_put_n250():
+    t = W.single_put_n250()
+    out, st = _gpu(t)
+    ref, rst = oracle.price_ask_bid(t)
+    _assert_parity(t, out, st, ref, rst)
+    crr, _ = oracle.crr_price(t[1:])
+    assert abs(out[1, 0] - crr[0]) <= RTOL * crr[0] and abs(out[1, 1] - crr[0]) <= RTOL * crr[0]
+    assert out[0, 1] <= crr[0] <= out[0, 0]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small_tables(seed):
+    # sizes span several warp tiles per level and end in ragged tails
+    t = W.random_table(48, 20000 + seed, N_lo=1, N_hi=140, k_hi=0.05 if seed % 2 else 0.02)
+    out, st = _gpu(t)
+    ref, rst = oracle.price_ask_bid(t, nthreads=8)
+    _assert_parity(t, out, st, ref, rst)
+
+
+def test_heavy_small_cases():
+    # low volatility and high costs: hundreds of breakpoints per node
+    t = W.concat(W.make(S0=100, K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=150, payoff=W.SPREAD),
+                 W.make(S0=100, K=100, sigma=0.1, T=0.1, k=0.02, N=150, payoff=W.CALL),
+                 W.make(K=95, K2=105, k=0.01, N=300, payoff=W.SPREAD),
+                 W.make(S0=110, K=100, k=0.03, N=200, payoff=W.CALL))
+    out, st = _gpu(t)
+    ref, rst = oracle.price_ask_bid(t, nthreads=4)
+    _assert_parity(t, out, st, ref, rst)
+
+
+def test_k0_all_payoffs_equal_crr():
+    t = W.random_table(30, 31337, N_lo=1, N_hi=200, k_zero=True)
+    out, st = _gpu(t)
+    ref, _ = oracle.crr_price(t)
+    assert np.all(st == 0)
+    for col in (0, 1):
+        assert np.all(_close(out[:, col], ref, t["K"])), (out[:, col], ref)
+
+
+def test_edge_cases_status():
+    good = W.make(k=0.01, N=5)
+    bad_N = W.make(N=0)
+    bad_k = W.make(k=1.0)
+    bad_sigma = W.make(sigma=0.0)
+    bad_payoff = W.make()
+    bad_payoff["payoff"] = 7
+    bad_spread = W.make(K=100.0, K2=90.0, payoff=W.SPREAD)
+    arb = W.make(R=5.0, N=2, T=1.0)  # r > u
+    n1 = W.make(k=0.02, N=1)
+    t = W.concat(good, bad_N, bad_k, bad_sigma, bad_payoff, bad_spread, arb, n1)
+    out, st = _gpu(t)
+    ref, rst = oracle.price_ask_bid(t)
+    # the oracle's codes: -1 argument, -2 arbitrage; the library's are the same numbers
+    assert st.tolist() == rst.tolist() == [0, -1, -1, -1, -1, -1, -2, 0]
+    assert np.all(np.isnan(out[1:7]))
+    _assert_parity(t[[0, 7]], out[[0, 7]], st[[0, 7]], ref[[0, 7]], rst[[0, 7]])
+
+
+def test_empty_batch_is_noop():
+    import torch
+    ob = _ob()
+    params = torch.empty(0, dtype=torch.uint8, device="cuda")
+    out = torch.empty(0, dtype=torch.float64, device="cuda")
+    ob.ob_price_ask_bid(params, 0, out)
+    ob.ob_crr_american(params, 0, out)
+
+
+def test_batched_equals_plain_bitwise():
+    t = W.random_table(64, 555, N_lo=20, N_hi=300)
+    a, sa = _gpu(t, plain=False)
+    b, sb = _gpu(t, plain=True)
+    assert np.array_equal(sa, sb)
+    assert np.array_equal(a.view(np.int64), b.view(np.int64))
+
+
+def test_host_buffer_entry_matches_device():
+    ob = _ob()
+    t = W.random_table(40, 99, N_lo=10, N_hi=200)
+    d, ds = _gpu(t)
+    out = np.empty((len(t), 2), np.float64)
+    st = np.empty(len(t), np.int32)
+    ob.ob_price_ask_bid_host(t, out, st)
+    assert np.array_equal(st, ds)
+    assert np.array_equal(out.view(np.int64), d.view(np.int64))
+
+
+def test_stats_count_node_updates():
+    ob = _ob()
+    t = W.random_table(50, 4242, N_lo=5, N_hi=100)
+    _gpu(t)
+    s = ob.ob_get_stats()
+    assert s["options"] == len(t) and s["failed"] == 0
+    assert s["node_updates"] == int(np.sum(W.node_updates(t)))
+    assert s["z_points"] >= s["node_updates"]  # every node keeps >= 1 breakpoint per party... at least one
+
+
+# ---------------------------------------------------------------- full-size configurations
+def test_batched_4096_sampled():
+    """The batched uneven workload at full size; the oracle checks a stratified sample."""
+    t = W.batched_uneven()
+    out, st = _gpu(t)
+    assert np.all(st == 0)
+    assert np.all(np.isfinite(out))
+    rng = np.random.default_rng(0)
+    order = np.argsort(t["N"])
+    idx = np.unique(np.concatenate([order[:8], rng.choice(len(t), 10, replace=False)]))
+    ref, rst = oracle.price_ask_bid(t[idx], nthreads=16)
+    _assert_parity(t[idx], out[idx], st[idx], ref, rst)
+    # properties at every option: bid <= CRR <= ask
+    t0 = t.copy()
+    t0["k"] = 0.0
+    crr, _ = _ob().crr(t0)
+    crr = crr.cpu().numpy()
+    assert np.all(out[:, 1] <= crr * (1 + 1e-12) + 1e-12)
+    assert np.all(out[:, 0] >= crr * (1 - 1e-12) - 1e-12)
+
+
+def test_paper_scale_n1500_single_launches():
+    t = W.paper_scale(Ns=(1500,), ks=(0.005, 0.01))
+    outs = []
+    for i in range(len(t)):
+        o, s = _gpu(t[i:i + 1])
+        assert s[0] == 0
+        outs.append(o[0])
+    out = np.array(outs)
+    ref, rst = oracle.price_ask_bid(t, nthreads=4)
+    _assert_parity(t, out, np.zeros(len(t), np.int32), ref, rst)
+
+
+def test_paper_scale_large_n_properties():
+    t = W.paper_scale(Ns=(3000, 6000))
+    out, st = _gpu(t)
+    assert np.all(st == 0)
+    puts, spreads = out[0::2], out[1::2]
+    for grp in (puts, spreads):
+        for N_blk in range(2):
+            blk = grp[3 * N_blk:3 * N_blk + 3]  # k increasing
+            assert np.all(np.diff(blk[:, 0]) > 0) and np.all(np.diff(blk[:, 1]) <= 1e-12)
+    ref, rst = oracle.price_ask_bid(t[:1], nthreads=1)  # N = 3000 put, k = 0.0025
+    _assert_parity(t[:1], out[:1], st[:1], ref, rst)
+
+
+def test_greeks_config_puts_sampled():
+    t = W.greeks_puts()
+    out, st = _gpu(t)
+    assert np.all(st == 0)
+    idx = np.arange(0, len(t), 128)
+    ref, rst = oracle.price_ask_bid(t[idx], nthreads=8)
+    _assert_parity(t[idx], out[idx], st[idx], ref, rst)
+
+
+# ---------------------------------------------------------------- plain CRR kernel
+@pytest.mark.parametrize("seed", range(3))
+def test_crr_kernel_random(seed):
+    t = W.random_table(200, 600 + seed, N_lo=1, N_hi=2500, k_zero=True)
+    got, st = _ob().crr(t)
+    got, st = got.cpu().numpy(), st.cpu().numpy()
+    ref, rst = oracle.crr_price(t, nthreads=8)
+    assert np.array_equal(st, rst)
+    assert np.all(_close(got, ref, t["K"])), np.max(np.abs(got - ref) / np.maximum(ref, 1))
+
+
+def test_crr_65536_sampled_and_appendix_put():
+    t = W.crr_puts()
+    got, st = _ob().crr(t)
+    got, st = got.cpu().numpy(), st.cpu().numpy()
+    assert np.all(st == 0)
+    idx = np.arange(0, len(t), 4096)
+    ref, _ = oracle.crr_price(t[idx], nthreads=8)
+    assert np.all(_close(got[idx], ref, t["K"][idx]))
+    big = W.appendix_put(20000)
+    g, s = _ob().crr(big)
+    g = g.cpu().numpy()
+    r, _ = oracle.crr_price(big)
+    assert s.cpu().numpy()[0] == 0 and abs(g[0] - r[0]) <= RTOL * r[0]
+    assert round(float(g[0]), 3) == 13.906
