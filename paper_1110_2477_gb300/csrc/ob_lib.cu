@@ -22,11 +22,17 @@
 
 namespace {
 
-constexpr int kBlock = 128;          // 4 warps per CTA
+constexpr int kBlock = 128;          // CTA of the plain kernel and of the CRR kernel (4 warps)
+constexpr int kNW = 8;               // warps of a CTA of the batched kernel
+constexpr int kTeamBlock = 32 * kNW;
 constexpr int kTiers = 3;            // launches per ob_price_ask_bid call
-constexpr int kTier1Workers = 64;    // warps of the first follow-up launch
+constexpr int kTier1Ctas = 16;       // CTAs of the first follow-up launch
 constexpr int kSortMax = 8192;       // largest batch ordered by cost
 constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
+constexpr double kHeavyFactor = 2.0; // heavy: predicted cost > factor x (total / warps)
+// control words
+enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
+       C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
 
 struct DevStats {
   unsigned long long options, node_updates, upts, wpts, zpts;
@@ -49,20 +55,44 @@ __device__ __forceinline__ int check_option(const obk::Opt& o, bool need_k) {
 }
 
 // ------------------------------------------------------------------ ordering
-// Bitonic sort of (cost, index) keys, descending, in one CTA.
-__global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int* __restrict__ order) {
+// Predicted work of an option: node updates times an estimate of the
+// breakpoints per node (both parties).  Puts keep about one breakpoint per
+// node and party; calls and cash-settled spreads gather many once
+// x = k / (sigma sqrt(T/N)) exceeds ~1 (pieces whose slopes stay inside the
+// bid/ask window survive more levels).  Fitted to the oracle's counts on the
+// batched workload; only the ordering and the warp/CTA split depend on it.
+__device__ __forceinline__ double predicted_cost(const obk::Opt& o) {
+  const double N = o.N > 0 ? (double)o.N : 1.0;
+  const double nodes = (N + 1.0) * (N + 2.0) * 0.5;
+  const double sd = (o.sigma > 0.0 && o.T > 0.0) ? o.sigma * sqrt(o.T / N) : 1.0;
+  const double x = (o.k > 0.0) ? o.k / sd : 0.0;
+  double m = 2.0;
+  if (x > 1.0) {
+    if (o.payoff == obk::PAY_CALL) m += 1.5 * x;
+    else if (o.payoff == obk::PAY_SPREAD) m += x * x;
+  }
+  double c = nodes * m;
+  return c < 1e12 ? c : 1e12;
+}
+
+// Bitonic sort of (cost, index) keys, descending, in one CTA; also decides how
+// many of the costliest options go to whole-CTA teams (ctl[C_NHEAVY]).
+__global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int* __restrict__ order,
+                        int* ctl, int nwarps, int nctas) {
   extern __shared__ unsigned long long keys[];
+  __shared__ double part[32];
+  double mysum = 0.0;
   for (int i = threadIdx.x; i < npad; i += blockDim.x) {
     unsigned long long key = 0;
     if (i < n) {
-      const long long N = opts[i].N > 0 ? opts[i].N : 1;
-      const int w = opts[i].payoff == obk::PAY_PUT ? 1 : (opts[i].payoff == obk::PAY_CALL ? 2 : 3);
-      unsigned long long cost = (unsigned long long)((N + 1) * (N + 2) / 2) * w;
-      if (cost > (1ULL << 43)) cost = 1ULL << 43;
-      key = ((cost + 1) << 20) | (unsigned long long)i;
+      const double c = predicted_cost(opts[i]);
+      mysum += c;
+      key = ((unsigned long long)c + 1ULL) << 20 | (unsigned long long)i;
     }
     keys[i] = key;
   }
+  for (int d = 16; d >= 1; d >>= 1) mysum += __shfl_down_sync(0xffffffffu, mysum, d);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = mysum;
   __syncthreads();
   for (int size = 2; size <= npad; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -78,72 +108,152 @@ __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int*
     }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(keys[i] & 0xFFFFF);
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += part[w];
+    int nh = 0;
+    if (n <= nctas) {
+      nh = n;  // few options: every option gets a whole CTA
+    } else {
+      const double thr = kHeavyFactor * total / (double)nwarps;
+      while (nh < n && (double)(keys[nh] >> 20) > thr) ++nh;
+    }
+    ctl[C_NHEAVY] = nh;
+  }
 }
 
 // ------------------------------------------------------------------ induction with costs
-__global__ void __launch_bounds__(kBlock) k_tc(const obk::Opt* __restrict__ opts, int n,
-                                               const int* __restrict__ order, double* out, int* status,
-                                               char* arena, size_t wbytes, int nworkers, int* ctl,
-                                               int tier, const int* in_list, int* out_list, int last,
-                                               int plain, DevStats* ds) {
+template <class Team>
+__device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
+                                          int& rc, double& ask, double& bid, obk::Stats& st) {
+  rc = check_option(o, true);
+  ask = dnan();
+  bid = dnan();
+  st.upts = st.wpts = st.zpts = 0;
+  st.zmax_level = 0;
+  if (rc != obk::ST_OK) return;
+  obk::Lay L;
+  if (!obk::carve(slice, bytes, o.N, 2 * (o.N + 2), L)) {
+    rc = obk::ST_CAPACITY;
+    return;
+  }
+  obk::TcRun<Team> R(tm, o, L);
+  rc = R.run(ask, bid);
+  st = R.st;
+}
+
+// Record an option's result (one thread); a capacity failure goes to the retry
+// list when a follow-up launch exists.
+__device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, const obk::Stats& st,
+                                       const obk::Opt& o, double* out, int* status, int* ovf_count,
+                                       int* ovf_list, bool retry, DevStats* ds) {
+  if (rc == obk::ST_CAPACITY && retry) {
+    const int pos = atomicAdd(ovf_count, 1);
+    ovf_list[pos] = oi;
+    atomicAdd(&ds->retried, 1);
+    return;
+  }
+  out[2 * oi] = rc ? dnan() : ask;
+  out[2 * oi + 1] = rc ? dnan() : bid;
+  if (status) status[oi] = rc;
+  atomicAdd(&ds->options, 1ULL);
+  if (rc == obk::ST_OK) {
+    const unsigned long long N = (unsigned long long)o.N;
+    atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
+    atomicAdd(&ds->upts, (unsigned long long)st.upts);
+    atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
+    atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
+    atomicMax(&ds->max_level, st.zmax_level);
+  } else {
+    atomicAdd(&ds->failed, 1);
+  }
+}
+
+// Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
+// one at a time as a whole-CTA team, then each of its warps takes the remaining
+// options one at a time from a second queue.  Both queues are device counters.
+__global__ void __launch_bounds__(kTeamBlock, 2) k_tc_batched(
+    const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
+    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds) {
+  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
+  obk::BlockTeam<kNW> bt{tbuf};
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  const int nh = order ? *((volatile int*)&ctl[C_NHEAVY]) : 0;
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_HEAVY_HEAD], 1);
+    const int idx = bt.bcast0(v);
+    if (idx >= nh) break;
+    const int oi = order[idx];
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
+    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    bt.sync();
+  }
+  obk::WarpTeam wt;
+  const size_t wbytes = (cta_bytes / kNW) & ~(size_t)255;
+  char* wmy = my + (size_t)(threadIdx.x >> 5) * wbytes;
+  for (;;) {
+    int v = 0;
+    if (wt.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int idx = wt.bcast0(v) + nh;
+    if (idx >= n) break;
+    const int oi = order ? order[idx] : idx;
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one(wt, o, wmy, wbytes, rc, ask, bid, st);
+    if (wt.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    wt.sync();
+  }
+}
+
+// Follow-up launch: the options of in_list (count at *in_count), one per CTA,
+// with larger slices.
+__global__ void __launch_bounds__(kTeamBlock, 2) k_tc_retry(
+    const obk::Opt* __restrict__ opts, double* out, int* status, char* arena, size_t cta_bytes,
+    const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list, int last,
+    DevStats* ds) {
+  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
+  obk::BlockTeam<kNW> bt{tbuf};
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  const int cnt = *((volatile const int*)in_count);
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(head, 1);
+    const int idx = bt.bcast0(v);
+    if (idx >= cnt) break;
+    const int oi = in_list[idx];
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
+    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, ovf_count, ovf_list, !last, ds);
+    bt.sync();
+  }
+}
+
+// Plain form: one warp per option, static assignment in index order, no retry.
+__global__ void __launch_bounds__(kBlock) k_tc_plain(const obk::Opt* __restrict__ opts, int n,
+                                                     double* out, int* status, char* arena,
+                                                     size_t wbytes, int nworkers, DevStats* ds) {
   obk::WarpTeam tm;
-  const int lane = tm.lane();
   const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   if (wid >= nworkers) return;
   char* my = arena + (size_t)wid * wbytes;
-  const int count = (tier == 0) ? n : *((volatile int*)&ctl[2 * (tier - 1) + 1]);
-  int next_static = wid;
-  for (;;) {
-    int idx;
-    if (plain) {
-      idx = next_static;
-      next_static += nworkers;
-    } else {
-      int v = 0;
-      if (lane == 0) v = atomicAdd(&ctl[2 * tier], 1);
-      idx = tm.shfl(v, 0);
-    }
-    if (idx >= count) break;
-    const int oi = (tier == 0) ? (order ? order[idx] : idx) : in_list[idx];
+  for (int oi = wid; oi < n; oi += nworkers) {
     const obk::Opt o = opts[oi];
-    int rc = check_option(o, true);
-    double ask = dnan(), bid = dnan();
+    int rc;
+    double ask, bid;
     obk::Stats st;
-    st.upts = st.wpts = st.zpts = 0;
-    st.zmax_level = 0;
-    if (rc == obk::ST_OK) {
-      obk::Lay L;
-      if (!obk::carve(my, wbytes, o.N, 2 * (o.N + 2), L)) {
-        rc = obk::ST_CAPACITY;
-      } else {
-        obk::TcRun<obk::WarpTeam> R(tm, o, L);
-        rc = R.run(ask, bid);
-        st = R.st;
-      }
-    }
-    if (lane == 0) {
-      if (rc == obk::ST_CAPACITY && !last) {
-        const int pos = atomicAdd(&ctl[2 * tier + 1], 1);
-        out_list[pos] = oi;
-        atomicAdd(&ds->retried, 1);
-      } else {
-        out[2 * oi] = rc ? dnan() : ask;
-        out[2 * oi + 1] = rc ? dnan() : bid;
-        if (status) status[oi] = rc;
-        atomicAdd(&ds->options, 1ULL);
-        if (rc == obk::ST_OK) {
-          const unsigned long long N = (unsigned long long)o.N;
-          atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
-          atomicAdd(&ds->upts, (unsigned long long)st.upts);
-          atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
-          atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
-          atomicMax(&ds->max_level, st.zmax_level);
-        } else {
-          atomicAdd(&ds->failed, 1);
-        }
-      }
-    }
-    tm.sync();  // the next option reuses the slice
+    price_one(tm, o, my, wbytes, rc, ask, bid, st);
+    if (tm.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, nullptr, nullptr, false, ds);
+    tm.sync();
   }
 }
 
@@ -173,7 +283,7 @@ __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opt
   for (;;) {
     int v = 0;
     if (lane == 0) v = atomicAdd(&ctl[0], 1);
-    const int oi = tm.shfl(v, 0);
+    const int oi = tm.bcast0(v);
     if (oi >= n) break;
     const obk::Opt o = opts[oi];
     int rc = check_option(o, false);
@@ -206,7 +316,7 @@ __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opt
           for (int base = 0; base < width; base += 32) {
             const int i = base + lane;
             const double cur = (i <= width) ? V[i] : 0.0;
-            double up = tm.shfl_down(cur, 1);
+            double up = __shfl_down_sync(0xffffffffu, cur, 1);
             const double extra = (base + 32 <= width) ? V[base + 32] : 0.0;
             if (lane == 31) up = extra;
             tm.sync();
@@ -282,12 +392,14 @@ int pool_get(DevPool** out, size_t need_list) {
     P.arena_per_warp = env_size("OB_ARENA_MB", 8) << 20;
     const size_t workers = (size_t)P.sms * P.warps_per_sm;
     P.arena_bytes = workers * P.arena_per_warp;
+    const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
+    if (pool_mb) P.arena_bytes = pool_mb << 20;
     if (cudaMalloc(&P.arena, P.arena_bytes) != cudaSuccess) {
       cudaGetLastError();
       P.arena = nullptr;
       return OB_ERR_NOMEM;
     }
-    if (cudaMalloc(&P.ctl, sizeof(int) * 2 * kTiers) != cudaSuccess ||
+    if (cudaMalloc(&P.ctl, sizeof(int) * C_WORDS) != cudaSuccess ||
         cudaMalloc(&P.order, sizeof(int) * kSortMax) != cudaSuccess ||
         cudaMalloc(&P.stats, sizeof(DevStats)) != cudaSuccess) {
       cudaGetLastError();
@@ -327,48 +439,45 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * 2 * kTiers, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
   const obk::Opt* opts = (const obk::Opt*)params;
+  if (plain) {
+    const int max_workers = P->sms * P->warps_per_sm;
+    const int workers = n < max_workers ? n : max_workers;
+    const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
+    const int blocks = (workers * 32 + kBlock - 1) / kBlock;
+    k_tc_plain<<<blocks, kBlock, 0, s>>>(opts, n, out, status, P->arena, wbytes, workers, P->stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    P->last_tiers = 1;
+    return OB_OK;
+  }
+  const int nctas = P->sms * 2;
   const int* order = nullptr;
-  if (!plain && n <= kSortMax && n > 1) {
+  if (n <= kSortMax) {
     int npad = 1;
     while (npad < n) npad <<= 1;
-    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order);
+    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order, P->ctl,
+                                                               nctas * kNW, nctas);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
-  const int max_workers = P->sms * P->warps_per_sm;
-  const int w0 = n < max_workers ? n : max_workers;
+  const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
-  const int tiers = plain ? 1 : kTiers;
-  for (int tier = 0; tier < tiers; ++tier) {
-    int workers;
-    size_t wbytes;
-    const int* in_list = nullptr;
-    int* out_list = nullptr;
-    if (tier == 0) {
-      workers = w0;
-      wbytes = P->arena_per_warp;
-      out_list = list0;
-    } else if (tier == 1) {
-      workers = kTier1Workers;
-      wbytes = (P->arena_bytes / kTier1Workers) & ~(size_t)255;
-      in_list = list0;
-      out_list = list1;
-    } else {
-      workers = 1;
-      wbytes = P->arena_bytes & ~(size_t)255;
-      in_list = list1;
-    }
-    const int blocks = (workers * 32 + kBlock - 1) / kBlock;
-    k_tc<<<blocks, kBlock, 0, s>>>(opts, n, order, out, status, P->arena, wbytes, workers, P->ctl,
-                                   tier, in_list, out_list, tier == tiers - 1 ? 1 : 0, plain ? 1 : 0,
-                                   P->stats);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  }
-  P->last_tiers = tiers;
+  k_tc_batched<<<nctas, kTeamBlock, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
+                                            list0, P->stats);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
+  k_tc_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF],
+                                               list0, &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0,
+                                               P->stats);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, P->arena, P->arena_bytes & ~(size_t)255,
+                                      &P->ctl[C_T1_OVF], list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF],
+                                      nullptr, 1, P->stats);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  P->last_tiers = kTiers + (order ? 1 : 0);
   return OB_OK;
 }
 
@@ -397,7 +506,7 @@ int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, i
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * 2 * kTiers, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   const int max_workers = P->sms * 12;  // 3 CTAs of 4 warps per SM fit the shared memory
   const int workers = n < max_workers ? n : max_workers;
   const size_t wbytes = (P->arena_bytes / (size_t)workers) & ~(size_t)255;

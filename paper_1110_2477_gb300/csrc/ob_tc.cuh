@@ -398,35 +398,6 @@ struct TcRun {
     st.zmax_node = 0;
   }
 
-  // exclusive prefix sum over the team; returns the prefix, sets the total
-  OB_HD int excl_sum(int v, int& total) const {
-    const int lane = tm.lane();
-    int x = v;
-    for (int d = 1; d < Team::W; d <<= 1) {
-      const int y = tm.shfl_up(x, d);
-      if (lane >= d) x += y;
-    }
-    total = tm.shfl(x, Team::W - 1);
-    return x - v;
-  }
-
-  // segmented inclusive min-scan of keys across the team, lane order; heads start segments
-  OB_HD long long seg_min(long long v, bool head, long long& carry) const {
-    const int lane = tm.lane();
-    int fl = head ? 1 : 0;
-    for (int d = 1; d < Team::W; d <<= 1) {
-      const long long vu = tm.shfl_up(v, d);
-      const int fu = tm.shfl_up(fl, d);
-      if (lane >= d) {
-        if (!fl) v = kmin(v, vu);
-        fl |= fu;
-      }
-    }
-    if (!fl) v = kmin(v, carry);
-    carry = tm.shfl(v, Team::W - 1);
-    return v;
-  }
-
   OB_HD void node_table(int t) {
     const int lane = tm.lane();
     double* nt = L.nt[t & 1];
@@ -472,17 +443,9 @@ struct TcRun {
         const int p = nl >= W0 ? 1 : 0;
         nend = ustart(o1, W1, UB1, p, nl - p * W0 + 1);
       }
-      // node of q: number of node ends <= q among the 32 loaded (ends are increasing)
-      int pos = 0;
-      for (int step = Team::W / 2; step >= 1; step >>= 1) {
-        const int v = tm.shfl(nend, pos + step - 1);
-        if (v <= q) pos += step;
-      }
-      {
-        const int v = tm.shfl(nend, Team::W - 1);
-        if (pos == Team::W - 1 && v <= q) pos = Team::W;
-      }
-      const int ncur_next = ncur + popc32(tm.ballot(nend <= base + Team::W));
+      // node of q: number of node ends <= q among those loaded (ends are increasing)
+      const int pos = tm.count_le(nend, q);
+      const int ncur_next = ncur + tm.count(nend <= base + Team::W);
       Em em[3];
       P1 e;
       e.dup = true;
@@ -500,15 +463,14 @@ struct TcRun {
       // owner of the segment ending at this point: that of the previous union point,
       // forwarded across a duplicate (duplicates are never adjacent)
       int own = e.own;
-      int v1 = tm.shfl_up(own, 1);
-      if (lane == 0) v1 = carry_own;
+      const int v1 = tm.prev(own, carry_own);
       if (q < Utot && e.dup) own = v1;
-      int v2 = tm.shfl_up(own, 1);
-      if (lane == 0) v2 = carry_own;
-      carry_own = tm.shfl(own, Team::W - 1);
+      int last_own;
+      const int v2 = tm.prev_last(own, carry_own, last_own);
+      carry_own = last_own;
       if (q < Utot) cnt = p1_emit(e, ql == 0 ? e.wl_first : v2, em);
       int total;
-      const int pre = excl_sum(cnt, total);
+      const int pre = tm.excl_sum(cnt, total);
       const int p0 = wpos + pre;
       if (q < Utot && ql == 0) L.offw[node] = p0;
       if (p0 + cnt <= L.capW) {
@@ -526,8 +488,7 @@ struct TcRun {
     }
     if (lane == 0) L.offw[nNodes] = wpos;
     wtot = wpos;
-    tm.sync();
-    return !(tm.ballot(ovf) != 0u || wpos > L.capW);
+    return !(tm.any(ovf) || wpos > L.capW);
   }
 
   // pass 2: g, h and the per-node running minima of their keys
@@ -551,7 +512,7 @@ struct TcRun {
         L.wH[i] = h;
         hk = okey(h);
       }
-      const long long v = seg_min(hk, head, carry);
+      const long long v = tm.seg_min(hk, head, carry);
       if (ok) L.wCB[i] = v;
     }
     tm.sync();
@@ -563,7 +524,7 @@ struct TcRun {
       const int n = ok ? L.wN[i] : -1;
       const bool head = ok && (i + 1 == wtot || L.wN[i + 1] != n);
       const long long gk = ok ? okey(L.wG[i]) : KMAX;
-      const long long v = seg_min(gk, head, carry);
+      const long long v = tm.seg_min(gk, head, carry);
       if (ok) L.wCA[i] = v;
     }
     tm.sync();
@@ -625,46 +586,92 @@ struct TcRun {
           }
           tail_slope = lines[S.li[S.ns - 1]].s;
         }
-        Subs S;
-        S.ns = 1;
-        S.xs[0] = y0;
-        if (tail) {  // right tail: v is the cB line
-          S.li[0] = 2;
-          S.hi = INF;
-        } else {
+        bool done = false;
+        if (!tail) {
           const double y1 = L.wY[i + 1], f1 = L.wF[i + 1];
           const long long cA1 = L.wCA[i + 1];
           const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
           const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
-          lines[0] = Ln{y0, f0, s0, y1, f1, 0};
-          lines[1] = Ln{0.0, unkey(cA1), -Sa, 0.0, 0.0, 1};
-          S.li[0] = 0;
-          S.hi = y1;
           // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
           // the cB line iff h <= cB_i at both ends (then that side of v equals w)
           const bool Arel = !(g1 == cA1 && g0 <= cA1);
           const bool Brel = !(h0 == cB && h1 <= cB);
-          if (Brel) subs_combine(S, lines, 2, 2, INF, false);
-          if (Arel) subs_combine(S, lines, 1, 1, INF, false);
+          if (!Arel && !Brel && !(klt(y0, yu) && klt(yu, y1))) {
+            // common case: v = w on the piece and one branch of u covers it
+            done = true;
+            const bool leftside = klt(y0, yu);
+            const double sQ = leftside ? -Sa : -Sb;
+            const double q0 = vu + sQ * (y0 - yu), q1 = vu + sQ * (y1 - yu);
+            const long long kf0 = okey(f0), kq0 = okey(q0), kf1 = okey(f1), kq1 = okey(q1);
+            const long long ks0 = okey(s0), ksQ = okey(sQ);
+            // winner at the left end (0 = w, 1 = u); ties go to the line that wins just right
+            int wl, wr;
+            if (kf0 != kq0) wl = ((kf0 > kq0) == seller) ? 0 : 1;
+            else wl = (ks0 == ksQ) ? 0 : (((ks0 > ksQ) == seller) ? 0 : 1);
+            if (kf1 != kq1) wr = ((kf1 > kq1) == seller) ? 0 : 1;
+            else wr = (ks0 == ksQ) ? 0 : (((ks0 < ksQ) == seller) ? 0 : 1);
+            if (wl == wr || ks0 == ksQ) {
+              first = (wl == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
+              last_slope = (wl == 0) ? s0 : sQ;
+            } else {
+              const double x = y0 + (f0 - q0) / (sQ - s0);
+              const int left_line = ((ks0 < ksQ) == seller) ? 0 : 1;
+              if (!klt(y0, x)) {
+                first = (left_line == 0) ? Em{y0, q0, sQ} : Em{y0, f0, s0};
+                last_slope = first.s;
+              } else if (!klt(x, y1)) {
+                first = (left_line == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
+                last_slope = first.s;
+              } else {
+                first = (left_line == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
+                const double sr = (left_line == 0) ? sQ : s0;
+                const double vr = (left_line == 0) ? vu + sQ * (x - yu) : f0 + s0 * (x - y0);
+                em[ntl + 1 + nm++] = Em{x, vr, sr};
+                last_slope = sr;
+              }
+            }
+          }
         }
-        if (klt(y0, yu) && klt(yu, S.hi)) subs_split(S, yu);
-        subs_combine(S, lines, 3, 4, yu, seller);
-        first = Em{y0, ln_eval(lines[S.li[0]], y0), lines[S.li[0]].s};
-        for (int k = 1; k < S.ns; ++k) {
-          const Ln& l = lines[S.li[k]];
-          if (!same_bits(l.s, lines[S.li[k - 1]].s))
-            em[ntl + 1 + nm++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+        if (!done) {
+          Subs S;
+          S.ns = 1;
+          S.xs[0] = y0;
+          if (tail) {  // right tail: v is the cB line
+            S.li[0] = 2;
+            S.hi = INF;
+          } else {
+            const double y1 = L.wY[i + 1], f1 = L.wF[i + 1];
+            const long long cA1 = L.wCA[i + 1];
+            const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
+            const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
+            lines[0] = Ln{y0, f0, s0, y1, f1, 0};
+            lines[1] = Ln{0.0, unkey(cA1), -Sa, 0.0, 0.0, 1};
+            S.li[0] = 0;
+            S.hi = y1;
+            const bool Arel = !(g1 == cA1 && g0 <= cA1);
+            const bool Brel = !(h0 == cB && h1 <= cB);
+            if (Brel) subs_combine(S, lines, 2, 2, INF, false);
+            if (Arel) subs_combine(S, lines, 1, 1, INF, false);
+          }
+          if (klt(y0, yu) && klt(yu, S.hi)) subs_split(S, yu);
+          subs_combine(S, lines, 3, 4, yu, seller);
+          first = Em{y0, ln_eval(lines[S.li[0]], y0), lines[S.li[0]].s};
+          for (int k = 1; k < S.ns; ++k) {
+            const Ln& l = lines[S.li[k]];
+            if (!same_bits(l.s, lines[S.li[k - 1]].s))
+              em[ntl + 1 + nm++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+          }
+          last_slope = lines[S.li[S.ns - 1]].s;
         }
-        last_slope = lines[S.li[S.ns - 1]].s;
       }
       // slope of z just left of this piece's first point
-      double prev = tm.shfl_up(last_slope, 1);
-      if (lane == 0) prev = carry_slope;
+      double tile_last_slope;
+      double prev = tm.prev_last(last_slope, carry_slope, tile_last_slope);
       if (head) prev = tail_slope;
       const int emit_first = (ok && (anchor || !same_bits(prev, first.s))) ? 1 : 0;
       const int nout = ok ? ntl + emit_first + nm : 0;
       int total;
-      const int pre = excl_sum(nout, total);
+      const int pre = tm.excl_sum(nout, total);
       const int p0 = zpos + pre;
       if (ok && head) off[node] = p0;
       if (ok) {
@@ -679,13 +686,12 @@ struct TcRun {
           ovf = true;
         }
       }
-      carry_slope = tm.shfl(last_slope, Team::W - 1);
+      carry_slope = tile_last_slope;
       zpos += total;
     }
     if (lane == 0) off[nNodes] = zpos;
     ztot = zpos;
-    tm.sync();
-    return !(tm.ballot(ovf) != 0u || zpos > L.capZ);
+    return !(tm.any(ovf) || zpos > L.capZ);
   }
 
   // value at y = 0 of node n of level 0 (bank 0)

@@ -220,3 +220,46 @@ def test_crr_65536_sampled_and_appendix_put():
     r, _ = oracle.crr_price(big)
     assert s.cpu().numpy()[0] == 0 and abs(g[0] - r[0]) <= RTOL * r[0]
     assert round(float(g[0]), 3) == 13.906
+
+
+# ---------------------------------------------------------------- scratch limits (subprocess: the pool is per process)
+_CHILD = r"""
+import sys, json, numpy as np, torch
+sys.path.insert(0, %(root)r)
+import workloads as W, paper_1110_2477_gb300 as ob
+t = W.concat(W.make(K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=1000, payoff=W.SPREAD),
+             W.random_table(40, 77, N_lo=50, N_hi=600))
+out, st = ob.price(t)
+torch.cuda.synchronize()
+print(json.dumps({"out": out.cpu().numpy().tolist(), "st": st.cpu().numpy().tolist(),
+                  "stats": ob.ob_get_stats()}))
+"""
+
+
+def _child(env_extra):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, "-c", _CHILD % {"root": root}], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_capacity_retry_and_exhaustion():
+    """Small per-warp slices force follow-up launches with larger slices (same results);
+    a pool too small for an option yields OB_ERR_CAPACITY for it, the others complete."""
+    base = _child({})
+    small = _child({"OB_ARENA_MB": "1", "OB_WARPS_PER_SM": "2"})
+    assert small["stats"]["retried"] > 0
+    assert small["st"] == base["st"] == [0] * len(base["st"])
+    assert np.array_equal(np.array(small["out"]).view(np.int64), np.array(base["out"]).view(np.int64))
+    tiny = _child({"OB_POOL_MB": "3"})
+    st = np.array(tiny["st"])
+    assert st[0] == -3 and np.isnan(tiny["out"][0][0])
+    ok = st == 0
+    assert ok.sum() >= 1
+    np.testing.assert_array_equal(np.array(tiny["out"])[ok], np.array(base["out"])[ok])
