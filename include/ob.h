@@ -87,6 +87,34 @@ int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, 
 int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double* out,
                            int32_t* status, void* stream);
 
+/* Fixed-scratch form of ob_price_ask_bid, for callers that cannot allocate
+ * device memory at call time: code running inside a memory budget that is
+ * already fully handed out, callers that must not touch the allocator while
+ * other work is in flight, or hosts whose process-wide allocation policy
+ * forbids cudaMalloc after start-up.  (The paper has no counterpart; this is an
+ * interface convenience.)
+ *
+ * It prices with the same kernels as ob_price_ask_bid, but all of its scratch
+ * lives in one file-scope device array of OB_NOALLOC_SCRATCH_BYTES that every
+ * device holds from the moment the library is loaded until the process exits;
+ * the call itself allocates and frees nothing.  The caller passes params, out
+ * and status (device pointers, as for ob_price_ask_bid).
+ *   - n_options must not exceed OB_NOALLOC_MAX_OPTIONS; larger batches are
+ *     rejected with OB_ERR_ARG and nothing is enqueued.
+ *   - An option whose functions outgrow the fixed scratch gets
+ *     OB_ERR_CAPACITY in status (NaN in out); the others complete.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress), so make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the array and resets its counters on the
+ *     given stream; calls whose work overlaps on the GPU (different streams,
+ *     or different host threads without ordering) race on it and must be
+ *     serialised by the caller. */
+#define OB_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define OB_NOALLOC_MAX_OPTIONS 4096
+int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, double* out,
+                             int32_t* status, void* stream);
+
 /* Plain CRR American price without transaction costs (the Appendix): the
  * scalar recursion over N levels, no extra level; k is ignored.
  *   out  DEVICE pointer, n_options doubles.  Other arguments as above. */

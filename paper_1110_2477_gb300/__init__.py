@@ -27,7 +27,8 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
     0, -1, -2, -3, -4, -5, -6)
 
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
-           "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error")
+           "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
+           "ob_price_ask_bid_noalloc")
 
 
 class ObStats(ctypes.Structure):
@@ -50,7 +51,8 @@ def load():
             raise ObError("libob.so not built: run __graft_entry__.build() (no CPU fallback exists)")
         lib = ctypes.CDLL(LIB_PATH)
         P, i64 = ctypes.c_void_p, ctypes.c_int64
-        for name in ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american"):
+        for name in ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american",
+                     "ob_price_ask_bid_noalloc"):
             f = getattr(lib, name)
             f.argtypes = [P, i64, P, P, P]
             f.restype = ctypes.c_int
@@ -111,6 +113,14 @@ def ob_price_ask_bid_plain(params, n, out, status=None, stream=None):
 
 def ob_crr_american(params, n, out, status=None, stream=None):
     _check(load().ob_crr_american(_ptr(params), int(n), _ptr(out), _ptr(status), _stream(stream)))
+
+
+def ob_price_ask_bid_noalloc(params, n, out, status=None, stream=None):
+    """Fixed-scratch form: for callers that cannot allocate device memory when they price
+    (the library's pool is never touched; scratch is a device array held since load time).
+    At most 4096 options per call; calls that overlap on the GPU must be serialised."""
+    _check(load().ob_price_ask_bid_noalloc(_ptr(params), int(n), _ptr(out), _ptr(status),
+                                           _stream(stream)))
 
 
 def ob_price_ask_bid_host(params, out, status=None):

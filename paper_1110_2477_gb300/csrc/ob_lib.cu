@@ -481,6 +481,42 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   return OB_OK;
 }
 
+// ------------------------------------------------------------------ fixed-scratch form
+// Scratch of ob_price_ask_bid_noalloc: one file-scope device array, so that the
+// call needs no allocation at all.  Every device that loads the library holds
+// it until the process exits.  Layout: control words and counters, the cost
+// order, the retry list, then the workers' slices.
+constexpr size_t kNoAllocBytes = OB_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoAllocMaxOptions = OB_NOALLOC_MAX_OPTIONS;
+constexpr int kNoAllocCtas = 16;
+constexpr size_t kNoAllocHead = 4096;  // control words + DevStats
+constexpr size_t kNoAllocLists = 2 * sizeof(int) * (size_t)kNoAllocMaxOptions;
+static __device__ __align__(256) char ob_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDev {
+  bool ready = false;
+  char* base = nullptr;  // device address of ob_noalloc_scratch on this device
+};
+NoAllocDev g_noalloc[64];
+
+int noalloc_base(char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= 64) return OB_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  NoAllocDev& D = g_noalloc[dev];
+  if (!D.ready) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, ob_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    D.base = (char*)p;
+    D.ready = true;
+  }
+  *out = D.base;
+  return OB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -617,5 +653,47 @@ const char* ob_strerror(int code) {
 }
 
 const char* ob_last_cuda_error(void) { return g_cuda_err; }
+
+int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, double* out,
+                             int32_t* status, void* stream) {
+  if (n_options < 0 || n_options > kNoAllocMaxOptions) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  const int n = (int)n_options;
+  char* base = nullptr;
+  int rc = noalloc_base(&base);
+  if (rc) return rc;
+  int sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail(e);
+  int* ctl = (int*)base;
+  DevStats* ds = (DevStats*)(base + 256);
+  int* order = (int*)(base + kNoAllocHead);
+  int* list0 = (int*)(base + kNoAllocHead + sizeof(int) * (size_t)kNoAllocMaxOptions);
+  int* list1 = list0 + kNoAllocMaxOptions;
+  char* arena = base + kNoAllocHead + sizeof(int) * (size_t)kNoAllocMaxOptions + kNoAllocLists;
+  const size_t arena_bytes = (kNoAllocBytes - (size_t)(arena - base)) & ~(size_t)255;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: reset the queues and counters
+  if ((e = cudaMemsetAsync(base, 0, kNoAllocHead, s)) != cudaSuccess) return cuda_fail(e);
+  const obk::Opt* opts = (const obk::Opt*)params;
+  int npad = 1;
+  while (npad < n) npad <<= 1;
+  k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, order, ctl,
+                                                             kNoAllocCtas * kNW, kNoAllocCtas);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
+  k_tc_batched<<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
+                                                   list0, ds);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0,
+                                      &ctl[C_T1_HEAD], &ctl[C_T1_OVF], list1, 1, ds);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  (void)sms;
+  return OB_OK;
+}
+
 
 }  // extern "C"
