@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="batched", choices=["batched", "small"],
+                    help="batched: the 4096-option batch (the reported metric); small: 48 options "
+                         "with N in [200, 600] (seed 321), for profiler captures")
     return ap.parse_args()
 
 
@@ -193,7 +196,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    table = W.batched_uneven() if rank == 0 else W.random_table(4096, 3 + 1000 * rank)
+    if args.workload == "small":
+        table = W.random_table(48, 321 + rank, N_lo=200, N_hi=600)
+    else:
+        table = W.batched_uneven() if rank == 0 else W.random_table(4096, 3 + 1000 * rank)
     n = len(table)
     nodes_per_step = int(np.sum(W.node_updates(table)))
     params = ob.to_device(table, dev)
@@ -264,8 +270,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "batched uneven 4096: N~U{100..2000}, S0,K~U[80,120], sigma~U[0.1,0.5], "
-                               "R~U[0,0.1], T~U[0.1,2], k~U[0,0.02], put/call/bull spread (width 10), seed 3",
+        "config": {"workload": ("batched uneven 4096: N~U{100..2000}, S0,K~U[80,120], sigma~U[0.1,0.5], "
+                                "R~U[0,0.1], T~U[0.1,2], k~U[0,0.02], put/call/bull spread (width 10), seed 3")
+                   if args.workload == "batched" else "small: 48 options, N in [200, 600], seed 321",
                    "options": n, "node_updates_per_step": nodes_per_step,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas (one batch per GPU)"},
