@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-greeks", action="store_true", help="skip the Greeks-vs-plain comparison")
     ap.add_argument("--workload", default="batched", choices=["batched", "small"],
                     help="batched: the 4096-option batch (the reported metric); small: 48 options "
                          "with N in [200, 600] (seed 321), for profiler captures")
@@ -260,6 +261,32 @@ def main():
     torch.cuda.synchronize(dev)
     plain_s = pa.elapsed_time(pb) / 1e3
 
+    # options/s with Greeks vs plain pricing: 1024 puts, N = 1000 (seed 4)
+    greeks_line = None
+    if args.workload == "batched" and not args.no_greeks:
+        gt = W.greeks_puts()
+        gn = len(gt)
+        gp = ob.to_device(gt, dev)
+        gout = torch.empty((gn, 2), dtype=torch.float64, device=dev)
+        ggrad = torch.empty((gn, 2, 6), dtype=torch.float64, device=dev)
+        gst = torch.empty(gn, dtype=torch.int32, device=dev)
+        ob.ob_greeks(gp, gn, gout, ggrad, gst, stream)
+        ob.ob_price_ask_bid(gp, gn, gout, gst, stream)
+        torch.cuda.synchronize(dev)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ob.ob_greeks(gp, gn, gout, ggrad, gst, stream)
+        e1.record(stream)
+        ob.ob_price_ask_bid(gp, gn, gout, gst, stream)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        tg, tp = e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3
+        assert int((gst != 0).sum().item()) == 0
+        gnodes = int(np.sum(W.node_updates(gt)))
+        greeks_line = {"workload": "1024 American puts, N=1000, batched-table distributions (seed 4)",
+                       "greeks_options_per_s": gn / tg, "plain_options_per_s": gn / tp,
+                       "greeks_node_updates_per_s": gnodes / tg, "greeks_over_plain_time": tg / tp}
+
     if rank != 0:
         return
     avg_step = dev_s / args.steps
@@ -290,6 +317,8 @@ def main():
                         "retried": stats["retried"]},
         "step_ms": step_ms, "wall_s": wall, "clocks": clocks,
     }
+    if greeks_line is not None:
+        line["greeks"] = greeks_line
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(table)
     print(json.dumps(line), flush=True)

@@ -115,6 +115,24 @@ int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double*
 int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, double* out,
                              int32_t* status, void* stream);
 
+/* Derivatives of ask and bid (the adjoint of the induction), with the prices.
+ *   params  DEVICE pointer, n_options records.
+ *   out     DEVICE pointer, 2*n_options doubles (ask, bid), as ob_price_ask_bid.
+ *   grad    DEVICE pointer, 12*n_options doubles: grad[12i + 0..5] = d ask / d(S0, K,
+ *           sigma, R, T, k), grad[12i + 6..11] = d bid / d(the same).
+ *   status  DEVICE pointer to n_options int32, or NULL.
+ * Meaning: the derivative of the piecewise-linear recursion along the branch the
+ * prices take (breakpoint structure held fixed); at a kink of the price in a
+ * parameter (an exercise boundary, a breakpoint appearing) it is one of the
+ * one-sided derivatives.  d/dK of the bull spread moves both strikes (fixed
+ * width); d/dT changes the step T/N with N fixed; at k = 0, d/dk is the
+ * right-hand derivative.  Method: reverse mode over the levels, root to leaves,
+ * with the level functions kept at checkpoints every ceil(sqrt(N+2)) levels and
+ * each segment recomputed once.  One warp per option (CTA teams for options that
+ * outgrow a warp's scratch); asynchronous on stream. */
+int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad,
+              int32_t* status, void* stream);
+
 /* Plain CRR American price without transaction costs (the Appendix): the
  * scalar recursion over N levels, no extra level; k is ignored.
  *   out  DEVICE pointer, n_options doubles.  Other arguments as above. */

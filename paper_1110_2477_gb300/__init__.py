@@ -28,7 +28,7 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
-           "ob_price_ask_bid_noalloc")
+           "ob_price_ask_bid_noalloc", "ob_greeks")
 
 
 class ObStats(ctypes.Structure):
@@ -52,10 +52,12 @@ def load():
         lib = ctypes.CDLL(LIB_PATH)
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         for name in ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american",
-                     "ob_price_ask_bid_noalloc"):
+                     "ob_price_ask_bid_noalloc", "ob_greeks"):
             f = getattr(lib, name)
             f.argtypes = [P, i64, P, P, P]
             f.restype = ctypes.c_int
+        lib.ob_greeks.argtypes = [P, i64, P, P, P, P]
+        lib.ob_greeks.restype = ctypes.c_int
         lib.ob_price_ask_bid_host.argtypes = [P, i64, P, P]
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
         lib.ob_get_stats.argtypes = [ctypes.POINTER(ObStats)]
@@ -123,6 +125,12 @@ def ob_price_ask_bid_noalloc(params, n, out, status=None, stream=None):
                                            _stream(stream)))
 
 
+def ob_greeks(params, n, out, grad, status=None, stream=None):
+    """Prices and d(ask, bid)/d(S0, K, sigma, R, T, k): out (n x 2), grad (n x 2 x 6), device tensors."""
+    _check(load().ob_greeks(_ptr(params), int(n), _ptr(out), _ptr(grad), _ptr(status),
+                            _stream(stream)))
+
+
 def ob_price_ask_bid_host(params, out, status=None):
     """Host buffers: params (numpy records), out (n x 2 float64), status (n int32) or None."""
     a = np.ascontiguousarray(params)
@@ -162,3 +170,70 @@ def crr(table, stream=None):
     st = torch.empty(n, dtype=torch.int32, device=dev.device)
     ob_crr_american(dev, n, out, st, stream)
     return out, st
+
+
+def greeks(table, stream=None):
+    """Prices and gradients of a workloads table: (out[n,2], grad[n,2,6], status[n]) tensors."""
+    import torch
+    n = int(np.asarray(table).shape[0])
+    dev = to_device(table)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev.device)
+    grad = torch.empty((n, 2, 6), dtype=torch.float64, device=dev.device)
+    st = torch.empty(n, dtype=torch.int32, device=dev.device)
+    ob_greeks(dev, n, out, grad, st, stream)
+    return out, grad, st
+
+
+def pack_params(theta, width, N, payoff):
+    """64-byte option records from tensors: theta (n, 6) float64 = (S0, K, sigma, R, T, k),
+    width (n,) = K2 - K, N and payoff (n,) int32.  Plain tensor marshalling."""
+    import torch
+    S0, K, sig, R, T, k = theta.unbind(1)
+    d = torch.stack([S0, K, K + width, sig, R, T, k], dim=1)
+    ints = torch.stack([N.to(torch.int32), payoff.to(torch.int32)], dim=1).contiguous()
+    rec = torch.cat([d, ints.view(torch.float64)], dim=1).contiguous()
+    return rec.view(torch.uint8).reshape(-1)
+
+
+def _autograd_class():
+    import torch
+
+    class AskBid(torch.autograd.Function):
+        """(ask, bid) of American options with proportional costs as a differentiable function
+        of theta = (S0, K, sigma, R, T, k).  The forward calls ob_greeks (prices and the adjoint
+        in one launch); the backward contracts the stored gradient with the incoming ones."""
+
+        @staticmethod
+        def forward(ctx, theta, width, N, payoff):
+            n = theta.shape[0]
+            params = pack_params(theta.detach(), width, N, payoff)
+            out = torch.empty((n, 2), dtype=torch.float64, device=theta.device)
+            grad = torch.empty((n, 2, 6), dtype=torch.float64, device=theta.device)
+            st = torch.empty(n, dtype=torch.int32, device=theta.device)
+            ob_greeks(params, n, out, grad, st)
+            ctx.save_for_backward(grad)
+            ctx.mark_non_differentiable(st)
+            return out[:, 0].clone(), out[:, 1].clone(), st
+
+        @staticmethod
+        def backward(ctx, g_ask, g_bid, g_st):
+            (grad,) = ctx.saved_tensors
+            g = torch.zeros_like(grad[:, 0, :])
+            if g_ask is not None:
+                g = g + g_ask[:, None] * grad[:, 0, :]
+            if g_bid is not None:
+                g = g + g_bid[:, None] * grad[:, 1, :]
+            return g, None, None, None
+
+    return AskBid
+
+
+_AskBid = None
+
+
+def ask_bid(theta, width, N, payoff):
+    """Differentiable (ask, bid, status): see AskBid."""
+    global _AskBid
+    if _AskBid is None:
+        _AskBid = _autograd_class()
+    return _AskBid.apply(theta, width, N, payoff)

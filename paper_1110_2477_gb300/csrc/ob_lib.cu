@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "ob.h"
+#include "ob_adj.cuh"
 #include "ob_tc.cuh"
 
 namespace {
@@ -78,7 +79,7 @@ __device__ __forceinline__ double predicted_cost(const obk::Opt& o) {
 // Bitonic sort of (cost, index) keys, descending, in one CTA; also decides how
 // many of the costliest options go to whole-CTA teams (ctl[C_NHEAVY]).
 __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int* __restrict__ order,
-                        int* ctl, int nwarps, int nctas) {
+                        int* ctl, int nwarps, int nctas, double heavy_factor) {
   extern __shared__ unsigned long long keys[];
   __shared__ double part[32];
   double mysum = 0.0;
@@ -115,7 +116,7 @@ __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int*
     if (n <= nctas) {
       nh = n;  // few options: every option gets a whole CTA
     } else {
-      const double thr = kHeavyFactor * total / (double)nwarps;
+      const double thr = heavy_factor * total / (double)nwarps;
       while (nh < n && (double)(keys[nh] >> 20) > thr) ++nh;
     }
     ctl[C_NHEAVY] = nh;
@@ -257,6 +258,88 @@ __global__ void __launch_bounds__(kBlock) k_tc_plain(const obk::Opt* __restrict_
   }
 }
 
+// ------------------------------------------------------------------ adjoint (Greeks)
+template <class Team>
+__device__ __forceinline__ void greeks_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
+                                           int& rc, double& ask, double& bid, double* gA, double* gB) {
+  rc = check_option(o, true);
+  ask = dnan();
+  bid = dnan();
+  if (rc != obk::ST_OK) return;
+  obk::Lay L;
+  obk::AdjLay A;
+  if (!obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A)) {
+    rc = obk::ST_CAPACITY;
+    return;
+  }
+  obk::TcRun<Team> R(tm, o, L);
+  obk::TcAdj<Team> G(R, A);
+  rc = G.run(ask, bid, gA, gB);
+}
+
+__device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double bid, const double* gA,
+                                              const double* gB, double* out, double* grad, int* status,
+                                              int* ovf_count, int* ovf_list, bool retry) {
+  if (rc == obk::ST_CAPACITY && retry) {
+    const int pos = atomicAdd(ovf_count, 1);
+    ovf_list[pos] = oi;
+    return;
+  }
+  out[2 * oi] = rc ? dnan() : ask;
+  out[2 * oi + 1] = rc ? dnan() : bid;
+  for (int k = 0; k < obk::NPAR; ++k) {
+    grad[12 * (size_t)oi + k] = rc ? dnan() : gA[k];
+    grad[12 * (size_t)oi + 6 + k] = rc ? dnan() : gB[k];
+  }
+  if (status) status[oi] = rc;
+}
+
+// One warp per option from a device queue; an option that outgrows its slice is
+// handed to the CTA-team launch that follows.
+__global__ void __launch_bounds__(kBlock) k_greeks(const obk::Opt* __restrict__ opts, int n, double* out,
+                                                   double* grad, int* status, char* arena, size_t wbytes,
+                                                   int nworkers, int* ctl, int* ovf_list) {
+  obk::WarpTeam tm;
+  const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  if (wid >= nworkers) return;
+  char* my = arena + (size_t)wid * wbytes;
+  for (;;) {
+    int v = 0;
+    if (tm.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int oi = tm.bcast0(v);
+    if (oi >= n) break;
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
+    greeks_one(tm, o, my, wbytes, rc, ask, bid, gA, gB);
+    if (tm.lane() == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
+    tm.sync();
+  }
+}
+
+__global__ void __launch_bounds__(kTeamBlock, 1) k_greeks_retry(
+    const obk::Opt* __restrict__ opts, double* out, double* grad, int* status, char* arena,
+    size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list,
+    int last) {
+  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
+  obk::BlockTeam<kNW> bt{tbuf};
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  const int cnt = *((volatile const int*)in_count);
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(head, 1);
+    const int idx = bt.bcast0(v);
+    if (idx >= cnt) break;
+    const int oi = in_list[idx];
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
+    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
+    if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, ovf_count, ovf_list, !last);
+    bt.sync();
+  }
+}
+
 // ------------------------------------------------------------------ plain CRR
 // c_{t,j} = max(P_{t,j}, pu c_{t+1,j+1} + pd c_{t+1,j}), pu = p/r, pd = (1-p)/r;
 // P is tabulated per option by stock exponent e = 2j - t (max(payoff, 0)).
@@ -352,6 +435,7 @@ struct DevPool {
   int sms = 0;
   int warps_per_sm = 16;
   size_t arena_per_warp = 8ull << 20;
+  double heavy_factor = kHeavyFactor;
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -390,6 +474,7 @@ int pool_get(DevPool** out, size_t need_list) {
     if (e != cudaSuccess) return cuda_fail(e);
     P.warps_per_sm = (int)env_size("OB_WARPS_PER_SM", 16);
     P.arena_per_warp = env_size("OB_ARENA_MB", 8) << 20;
+    if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
     const size_t workers = (size_t)P.sms * P.warps_per_sm;
     P.arena_bytes = workers * P.arena_per_warp;
     const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
@@ -458,7 +543,7 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
     int npad = 1;
     while (npad < n) npad <<= 1;
     k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order, P->ctl,
-                                                               nctas * kNW, nctas);
+                                                               nctas * kNW, nctas, P->heavy_factor);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
@@ -549,6 +634,39 @@ int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, i
   const int blocks = (workers * 32 + kBlock - 1) / kBlock;
   k_crr<<<blocks, kBlock, sizeof(double) * kCrrSmem * (kBlock / 32), s>>>(
       (const obk::Opt*)params, n, out, status, P->arena, wbytes, workers, P->ctl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  return OB_OK;
+}
+
+int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad, int32_t* status,
+              void* stream) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out || !grad) return OB_ERR_ARG;
+  const int n = (int)n_options;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, (size_t)n);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
+  const obk::Opt* opts = (const obk::Opt*)params;
+  const int max_workers = P->sms * 8;
+  const int workers = n < max_workers ? n : max_workers;
+  const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
+  int* list0 = P->lists;
+  int* list1 = P->lists + P->list_cap;
+  k_greeks<<<(workers * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(opts, n, out, grad, status, P->arena,
+                                                                   wbytes, workers, P->ctl, list0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
+  k_greeks_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, t1_bytes,
+                                                   &P->ctl[C_T0_OVF], list0, &P->ctl[C_T1_HEAD],
+                                                   &P->ctl[C_T1_OVF], list1, 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  k_greeks_retry<<<1, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, P->arena_bytes & ~(size_t)255,
+                                          &P->ctl[C_T1_OVF], list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF],
+                                          nullptr, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   return OB_OK;
 }
@@ -682,7 +800,8 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
   int npad = 1;
   while (npad < n) npad <<= 1;
   k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, order, ctl,
-                                                             kNoAllocCtas * kNW, kNoAllocCtas);
+                                                             kNoAllocCtas * kNW, kNoAllocCtas,
+                                                             kHeavyFactor);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
   k_tc_batched<<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,

@@ -81,14 +81,9 @@ OB_HD size_t node_bytes(int N) {
 constexpr size_t ELEM_BYTES = 2 * 3 * sizeof(double) + 5 * sizeof(double) + 2 * sizeof(long long) +
                               sizeof(int);
 
-// Carve an arena of `bytes` for an option with N steps.  Returns false when the
-// arena cannot hold the node arrays and at least min_cap points per array.
-OB_HD bool carve(char* base, size_t bytes, int N, int min_cap, Lay& L) {
-  size_t nb = node_bytes(N) + 16 * 256;
-  if (bytes < nb) return false;
-  size_t cap = (bytes - nb) / ELEM_BYTES;
-  if (cap > 0x3fffffff) cap = 0x3fffffff;
-  if ((long long)cap < (long long)min_cap) return false;
+// Carve the arrays for N steps and `cap` points per array starting at base;
+// returns the first byte after them.
+OB_HD char* carve_cap(char* base, int N, size_t cap, Lay& L) {
   char* p = base;
   auto take = [&](size_t sz) { char* r = p; p += al256(sz); return r; };
   L.Stab = (double*)take(sizeof(double) * (2 * (size_t)N + 3));
@@ -111,6 +106,18 @@ OB_HD bool carve(char* base, size_t bytes, int N, int min_cap, Lay& L) {
   L.wN = (int*)take(sizeof(int) * cap);
   L.capZ = (int)cap;
   L.capW = (int)cap;
+  return p;
+}
+
+// Carve an arena of `bytes` for an option with N steps.  Returns false when the
+// arena cannot hold the node arrays and at least min_cap points per array.
+OB_HD bool carve(char* base, size_t bytes, int N, int min_cap, Lay& L) {
+  size_t nb = node_bytes(N) + 16 * 256;
+  if (bytes < nb) return false;
+  size_t cap = (bytes - nb) / ELEM_BYTES;
+  if (cap > 0x3fffffff) cap = 0x3fffffff;
+  if ((long long)cap < (long long)min_cap) return false;
+  char* p = carve_cap(base, N, cap, L);
   return (size_t)(p - base) <= bytes;
 }
 
@@ -141,6 +148,10 @@ struct P1 {
   int own;            // owner just left of the next union point
   int wl_first;       // owner just left of y, first union point only
   bool dup, rc, lc;
+  // provenance, for the adjoint: breakpoint indices used, the successors whose lines
+  // meet at the crossings
+  int ia, ka, ib, kb, lc_w, rc_w;
+  bool fromA, aBp, bBp;
 };
 
 // q is the index in the merged breakpoint order (ties: A first).
@@ -177,6 +188,7 @@ OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int 
   }
   const int ka = aBp ? ia : iu - 1;  // last breakpoint of A at or before y
   const int kb = bBp ? ib : id - 1;
+  e.ia = ia; e.ka = ka; e.ib = ib; e.kb = kb; e.fromA = fromA; e.aBp = aBp; e.bBp = bBp;
   double a, aL, aR, b, bL, bR;
   if (aBp) {
     a = Af[ia];
@@ -223,6 +235,7 @@ OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int 
       const double x = y + (vW - vO) / (sO - sW);
       if (klt(x, y)) {
         e.lc = true;
+        e.lc_w = wl;
         e.xl = x;
         e.vl = vW + sW * (x - y);
         e.sl = sW;
@@ -252,6 +265,7 @@ OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int 
         wr = own = 1 - wr;  // the crossing rounds onto y
       } else if (!hasNext || klt(x, yn)) {
         e.rc = true;
+        e.rc_w = wr;
         e.xr = x;
         e.vr = vW + sW * (x - y);
         e.sr = sO;
@@ -274,111 +288,330 @@ OB_HD int p1_emit(const P1& e, int wl, Em* em) {
   return n;
 }
 
+// ------------------------------------------------------------------ scalars
+// The per-piece logic below is written once for two scalar types: double (the
+// pricing passes) and LD, a value with a few local derivatives used by the
+// adjoint passes.  All branch decisions are taken on values; in the adjoint they
+// are replayed from a recording made by the double run, so both runs follow the
+// same path even where rounding of the two differs.
+constexpr int LDN = 11;
+struct LD {
+  double v;
+  double d[LDN];
+};
+OB_HD double val(double x) { return x; }
+OB_HD double val(const LD& x) { return x.v; }
+template <class T>
+OB_HD T mk(double x);
+template <>
+OB_HD double mk<double>(double x) { return x; }
+template <>
+OB_HD LD mk<LD>(double x) {
+  LD r;
+  r.v = x;
+  for (int i = 0; i < LDN; ++i) r.d[i] = 0.0;
+  return r;
+}
+OB_HD LD operator+(const LD& a, const LD& b) {
+  LD r; r.v = a.v + b.v;
+  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+OB_HD LD operator-(const LD& a, const LD& b) {
+  LD r; r.v = a.v - b.v;
+  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+OB_HD LD operator-(const LD& a) {
+  LD r; r.v = -a.v;
+  for (int i = 0; i < LDN; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+OB_HD LD operator*(const LD& a, const LD& b) {
+  LD r; r.v = a.v * b.v;
+  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+OB_HD LD operator/(const LD& a, const LD& b) {
+  LD r; r.v = a.v / b.v;
+  for (int i = 0; i < LDN; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+OB_HD LD operator+(const LD& a, double b) { return a + mk<LD>(b); }
+OB_HD LD operator-(const LD& a, double b) { return a - mk<LD>(b); }
+OB_HD LD operator-(double a, const LD& b) { return mk<LD>(a) - b; }
+OB_HD LD operator*(double a, const LD& b) { return mk<LD>(a) * b; }
+
+// Decisions: the pricing run computes them (NoDec); the adjoint records them with
+// a double run (RecDec) and replays them with an LD run (PlayDec).
+struct NoDec {
+  OB_HD int take(int c) { return c; }
+};
+struct RecDec {
+  unsigned char d[96];
+  int n = 0;
+  OB_HD int take(int c) {
+    if (n < 96) d[n] = (unsigned char)c;
+    ++n;
+    return c;
+  }
+};
+struct PlayDec {
+  const unsigned char* d;
+  int n = 0;
+  OB_HD int take(int) { return d[n++]; }
+};
+
 // ------------------------------------------------------------------ pass 3 helpers
 // A line of the restriction/exercise step.  Point-slope form anchored at x0
 // (exact there); an F line (a piece of w) is also exact at its right end x1.
-struct Ln {
-  double x0, v0, s, x1, v1;
+template <class T>
+struct LnT {
+  T x0, v0, s, x1, v1;
   int icpt;  // 1: intercept form, value = v0 + s*x
 };
 
-OB_HD double ln_eval(const Ln& l, double x) {
+template <class T>
+OB_HD T ln_eval(const LnT<T>& l, const T& x) {
   if (l.icpt) return l.v0 + l.s * x;
-  if (same_bits(x, l.x0)) return l.v0;
-  if (same_bits(x, l.x1)) return l.v1;
+  if (same_bits(val(x), val(l.x0))) return l.v0;
+  if (same_bits(val(x), val(l.x1))) return l.v1;
   return l.v0 + l.s * (x - l.x0);
 }
 
 constexpr int MAXSUB = 10;
 
-struct Subs {
-  double xs[MAXSUB];  // start of each sub-piece (xs[0] may be -inf)
-  int li[MAXSUB];     // line of each sub-piece
+template <class T>
+struct SubsT {
+  T xs[MAXSUB];  // start of each sub-piece (xs[0] may be -inf)
+  int li[MAXSUB];
   int ns;
-  double hi;          // end of the last sub-piece (may be +inf)
+  T hi;          // end of the last sub-piece (may be +inf)
 };
 
 // Split the sub-piece containing x (strictly inside) at x.
-OB_HD void subs_split(Subs& S, double x) {
+template <class T, class D>
+OB_HD void subs_split(SubsT<T>& S, const T& x, D& dec) {
+  int at = -1;
   for (int k = 0; k < S.ns; ++k) {
-    const double e = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
-    if (klt(S.xs[k], x) && klt(x, e)) {
-      for (int m = S.ns; m > k + 1; --m) {
-        S.xs[m] = S.xs[m - 1];
-        S.li[m] = S.li[m - 1];
-      }
-      S.xs[k + 1] = x;
-      S.li[k + 1] = S.li[k];
-      S.ns += 1;
-      return;
-    }
+    const double e = val((k + 1 < S.ns) ? S.xs[k + 1] : S.hi);
+    if (klt(val(S.xs[k]), val(x)) && klt(val(x), e)) { at = k; break; }
   }
+  at = dec.take(at + 1) - 1;
+  if (at < 0) return;
+  for (int m = S.ns; m > at + 1; --m) {
+    S.xs[m] = S.xs[m - 1];
+    S.li[m] = S.li[m - 1];
+  }
+  S.xs[at + 1] = x;
+  S.li[at + 1] = S.li[at];
+  S.ns += 1;
 }
 
 // Replace every sub-piece line P by max(P, Q) (take_max) or min(P, Q), Q = lines[qi(k)],
 // where qi(k) = q_left if the sub-piece lies left of xq, else q_right.
-OB_HD void subs_combine(Subs& S, const Ln* lines, int q_left, int q_right, double xq,
-                        bool take_max) {
-  Subs O;
+template <class T, class D>
+OB_HD void subs_combine(SubsT<T>& S, const LnT<T>* lines, int q_left, int q_right, double xq,
+                        bool take_max, D& dec) {
+  SubsT<T> O;
   O.ns = 0;
   O.hi = S.hi;
   const double INF = ob_inf();
   for (int k = 0; k < S.ns; ++k) {
-    const double x0 = S.xs[k];
-    const double x1 = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
+    const T x0 = S.xs[k];
+    const T x1 = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
     const int pi = S.li[k];
-    const int qi = klt(x0, xq) ? q_left : q_right;
+    const int qi = dec.take(klt(val(x0), xq) ? q_left : q_right);
     if (pi == qi) {
       O.xs[O.ns] = x0; O.li[O.ns] = pi; ++O.ns;
       continue;
     }
-    const Ln& P = lines[pi];
-    const Ln& Q = lines[qi];
-    const bool finite0 = !same_bits(x0, -INF), finite1 = !same_bits(x1, INF);
-    double p0 = 0, q0 = 0, p1 = 0, q1 = 0;
+    const LnT<T>& P = lines[pi];
+    const LnT<T>& Q = lines[qi];
+    const bool finite0 = !same_bits(val(x0), -INF), finite1 = !same_bits(val(x1), INF);
+    const long long kps = okey(val(P.s)), kqs = okey(val(Q.s));
+    // outcome: 0 left winner whole, 1 right line whole, 2 left line whole, 3 split
+    int outcome = 0, lw = pi;
+    T p0 = mk<T>(0.0), q0 = mk<T>(0.0), p1 = mk<T>(0.0), q1 = mk<T>(0.0);
     if (finite0) { p0 = ln_eval(P, x0); q0 = ln_eval(Q, x0); }
     if (finite1) { p1 = ln_eval(P, x1); q1 = ln_eval(Q, x1); }
-    const long long kps = okey(P.s), kqs = okey(Q.s);
-    int wl, wr;  // 0 = P, 1 = Q
-    if (finite0) {
-      const long long a = okey(p0), b = okey(q0);
-      if (a != b) wl = ((a > b) == take_max) ? 0 : 1;
-      else wl = (kps == kqs) ? 0 : (((kps > kqs) == take_max) ? 0 : 1);  // right-side tie-break
-    } else {
-      if (kps != kqs) wl = ((kps < kqs) == take_max) ? 0 : 1;
-      else { const long long a = okey(p1), b = okey(q1); wl = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
-    }
-    if (finite1) {
-      const long long a = okey(p1), b = okey(q1);
-      if (a != b) wr = ((a > b) == take_max) ? 0 : 1;
-      else wr = (kps == kqs) ? 0 : (((kps < kqs) == take_max) ? 0 : 1);  // left-side tie-break
-    } else {
-      if (kps != kqs) wr = ((kps > kqs) == take_max) ? 0 : 1;
-      else { const long long a = okey(p0), b = okey(q0); wr = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
-    }
-    const int lw = wl ? qi : pi;
-    if (wl == wr || kps == kqs) {
-      O.xs[O.ns] = x0; O.li[O.ns] = lw; ++O.ns;
-      continue;
-    }
-    // The end values disagree, so the lines cross; which line owns each side of the
-    // crossing follows from the slopes (left of it the smaller slope is larger), so a
-    // tie at one end that rounding tipped the wrong way cannot misplace the piece.
-    double x;
-    if (finite0) x = x0 + (p0 - q0) / (Q.s - P.s);
-    else x = x1 + (p1 - q1) / (Q.s - P.s);
     const int left_line = ((kps < kqs) == take_max) ? pi : qi;
     const int right_line = (left_line == pi) ? qi : pi;
-    if (!klt(x0, x)) {
+    {
+      int wl, wr;  // 0 = P, 1 = Q
+      if (finite0) {
+        const long long a = okey(val(p0)), b = okey(val(q0));
+        if (a != b) wl = ((a > b) == take_max) ? 0 : 1;
+        else wl = (kps == kqs) ? 0 : (((kps > kqs) == take_max) ? 0 : 1);
+      } else {
+        if (kps != kqs) wl = ((kps < kqs) == take_max) ? 0 : 1;
+        else { const long long a = okey(val(p1)), b = okey(val(q1)); wl = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+      }
+      if (finite1) {
+        const long long a = okey(val(p1)), b = okey(val(q1));
+        if (a != b) wr = ((a > b) == take_max) ? 0 : 1;
+        else wr = (kps == kqs) ? 0 : (((kps < kqs) == take_max) ? 0 : 1);
+      } else {
+        if (kps != kqs) wr = ((kps > kqs) == take_max) ? 0 : 1;
+        else { const long long a = okey(val(p0)), b = okey(val(q0)); wr = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+      }
+      lw = wl ? qi : pi;
+      if (wl == wr || kps == kqs) {
+        outcome = 0;
+      } else {
+        // The end values disagree, so the lines cross; which line owns each side of the
+        // crossing follows from the slopes (left of it the smaller slope is larger), so a
+        // tie at one end that rounding tipped the wrong way cannot misplace the piece.
+        const double xd = finite0 ? val(x0) + (val(p0) - val(q0)) / (val(Q.s) - val(P.s))
+                                  : val(x1) + (val(p1) - val(q1)) / (val(Q.s) - val(P.s));
+        if (!klt(val(x0), xd)) outcome = 1;
+        else if (!klt(xd, val(x1))) outcome = 2;
+        else outcome = 3;
+      }
+    }
+    outcome = dec.take(outcome);
+    lw = dec.take(lw);
+    if (outcome == 0) {
+      O.xs[O.ns] = x0; O.li[O.ns] = lw; ++O.ns;
+    } else if (outcome == 1) {
       O.xs[O.ns] = x0; O.li[O.ns] = right_line; ++O.ns;
-    } else if (!klt(x, x1)) {
+    } else if (outcome == 2) {
       O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
     } else {
+      const T x = finite0 ? x0 + (p0 - q0) / (Q.s - P.s) : x1 + (p1 - q1) / (Q.s - P.s);
       O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
       O.xs[O.ns] = x; O.li[O.ns] = right_line; ++O.ns;
     }
   }
   S = O;
+}
+
+template <class T>
+struct EmT {
+  T y, f, s;
+};
+
+// Inputs of one piece of w (point i to point i+1, or the right tail), in the
+// scalar type of the run.  Keys and flags come from the double data.
+template <class T>
+struct PieceIn {
+  T y0, f0, s0, y1, f1;  // w at points i and i+1 (i+1 unused on the right tail)
+  T cA0;                 // running minimum of g from point i (left tail line intercept)
+  T cA1, cB;             // cA_{i+1}, cB_i
+  T Sa, Sb, vu;          // node constants; vu = xi (seller) or -xi (buyer)
+  double yu;             // kink of u
+  bool head, tail, seller, anchor, Arel, Brel;
+};
+
+template <class T>
+struct PieceOut {
+  EmT<T> tl[3];          // emissions inside the left tail (head only)
+  int ntl;
+  EmT<T> first;          // candidate point at y_i
+  EmT<T> m[MAXSUB];      // emissions inside the piece
+  int nm;
+  double last_slope, tail_slope;
+};
+
+// The restriction and the exercise step on one piece (and, for the first point
+// of a node, on the left tail).
+template <class T, class D>
+OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
+  const double INF = ob_inf();
+  out.ntl = 0;
+  out.nm = 0;
+  LnT<T> lines[5];  // 0 piece of w, 1 cA line, 2 cB line, 3 u left branch, 4 u right branch
+  const T yu = mk<T>(in.yu);
+  lines[2] = LnT<T>{mk<T>(0.0), in.cB, -in.Sb, mk<T>(0.0), mk<T>(0.0), 1};
+  lines[3] = LnT<T>{yu, in.vu, -in.Sa, mk<T>(INF), mk<T>(0.0), 0};
+  lines[4] = LnT<T>{yu, in.vu, -in.Sb, mk<T>(INF), mk<T>(0.0), 0};
+  if (in.head) {  // left tail: v is the cA_0 line
+    lines[1] = LnT<T>{mk<T>(0.0), in.cA0, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
+    SubsT<T> S;
+    S.ns = 1;
+    S.xs[0] = mk<T>(-INF);
+    S.li[0] = 1;
+    S.hi = in.y0;
+    if (dec.take(klt(in.yu, val(in.y0)) ? 1 : 0)) subs_split(S, yu, dec);
+    subs_combine(S, lines, 3, 4, in.yu, in.seller, dec);
+    for (int k = 1; k < S.ns; ++k) {
+      const LnT<T>& l = lines[S.li[k]];
+      if (dec.take(same_bits(val(l.s), val(lines[S.li[k - 1]].s)) ? 0 : 1))
+        out.tl[out.ntl++] = EmT<T>{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+    }
+    out.tail_slope = val(lines[S.li[S.ns - 1]].s);
+  }
+  const bool fast = dec.take((!in.tail && !in.Arel && !in.Brel &&
+                              !(klt(val(in.y0), in.yu) && klt(in.yu, val(in.y1)))) ? 1 : 0);
+  if (fast) {
+    // common case: v = w on the piece and one branch of u covers it
+    const bool leftside = klt(val(in.y0), in.yu);
+    const T sQ = leftside ? -in.Sa : -in.Sb;
+    const T q0 = in.vu + sQ * (in.y0 - yu), q1 = in.vu + sQ * (in.y1 - yu);
+    const long long ks0 = okey(val(in.s0)), ksQ = okey(val(sQ));
+    int outcome;  // 0: w, 1: u, 2: w then u, 3: u then w
+    {
+      const long long kf0 = okey(val(in.f0)), kq0 = okey(val(q0)), kf1 = okey(val(in.f1)),
+                      kq1 = okey(val(q1));
+      int wl, wr;  // 0 = w, 1 = u; ties go to the line that wins just right (left)
+      if (kf0 != kq0) wl = ((kf0 > kq0) == in.seller) ? 0 : 1;
+      else wl = (ks0 == ksQ) ? 0 : (((ks0 > ksQ) == in.seller) ? 0 : 1);
+      if (kf1 != kq1) wr = ((kf1 > kq1) == in.seller) ? 0 : 1;
+      else wr = (ks0 == ksQ) ? 0 : (((ks0 < ksQ) == in.seller) ? 0 : 1);
+      if (wl == wr || ks0 == ksQ) {
+        outcome = wl;
+      } else {
+        const double x = val(in.y0) + (val(in.f0) - val(q0)) / (val(sQ) - val(in.s0));
+        const int left_line = ((ks0 < ksQ) == in.seller) ? 0 : 1;
+        if (!klt(val(in.y0), x)) outcome = 1 - left_line;
+        else if (!klt(x, val(in.y1))) outcome = left_line;
+        else outcome = 2 + left_line;
+      }
+    }
+    outcome = dec.take(outcome);
+    if (outcome == 0) {
+      out.first = EmT<T>{in.y0, in.f0, in.s0};
+      out.last_slope = val(in.s0);
+    } else if (outcome == 1) {
+      out.first = EmT<T>{in.y0, q0, sQ};
+      out.last_slope = val(sQ);
+    } else {
+      const T x = in.y0 + (in.f0 - q0) / (sQ - in.s0);
+      if (outcome == 2) {  // w, then u from x
+        out.first = EmT<T>{in.y0, in.f0, in.s0};
+        out.m[out.nm++] = EmT<T>{x, in.vu + sQ * (x - yu), sQ};
+        out.last_slope = val(sQ);
+      } else {  // u, then w from x
+        out.first = EmT<T>{in.y0, q0, sQ};
+        out.m[out.nm++] = EmT<T>{x, in.f0 + in.s0 * (x - in.y0), in.s0};
+        out.last_slope = val(in.s0);
+      }
+    }
+    return;
+  }
+  SubsT<T> S;
+  S.ns = 1;
+  S.xs[0] = in.y0;
+  if (in.tail) {  // right tail: v is the cB line
+    S.li[0] = 2;
+    S.hi = mk<T>(INF);
+  } else {
+    lines[0] = LnT<T>{in.y0, in.f0, in.s0, in.y1, in.f1, 0};
+    lines[1] = LnT<T>{mk<T>(0.0), in.cA1, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
+    S.li[0] = 0;
+    S.hi = in.y1;
+    if (in.Brel) subs_combine(S, lines, 2, 2, INF, false, dec);
+    if (in.Arel) subs_combine(S, lines, 1, 1, INF, false, dec);
+  }
+  if (dec.take((klt(val(in.y0), in.yu) && klt(in.yu, val(S.hi))) ? 1 : 0)) subs_split(S, yu, dec);
+  subs_combine(S, lines, 3, 4, in.yu, in.seller, dec);
+  out.first = EmT<T>{in.y0, ln_eval(lines[S.li[0]], in.y0), lines[S.li[0]].s};
+  for (int k = 1; k < S.ns; ++k) {
+    const LnT<T>& l = lines[S.li[k]];
+    if (dec.take(same_bits(val(l.s), val(lines[S.li[k - 1]].s)) ? 0 : 1))
+      out.m[out.nm++] = EmT<T>{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+  }
+  out.last_slope = val(lines[S.li[S.ns - 1]].s);
 }
 
 // ------------------------------------------------------------------ the option
@@ -390,12 +623,27 @@ struct TcRun {
   int N;
   int zeta;  // -1 put, +1 call, 0 spread
   Stats st;
+  // where pass 1 reads level t+1 and pass 3 writes level t (the two banks by default)
+  const double *inY, *inF, *inS;
+  const int* inOff;
+  double *outY, *outF, *outS;
+  int* outOff;
+  int outCap;
 
   OB_HD TcRun(const Team& tm_, const Opt& o_, const Lay& L_) : tm(tm_), o(o_), L(L_), N(o_.N) {
     zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
     st.upts = st.wpts = st.zpts = 0;
     st.zmax_level = 0;
     st.zmax_node = 0;
+    use_banks(N);
+  }
+
+  // level t reads the bank of t+1 and writes the bank of t
+  OB_HD void use_banks(int t) {
+    const int b1 = (t + 1) & 1, bt = t & 1;
+    inY = L.zY[b1]; inF = L.zF[b1]; inS = L.zS[b1]; inOff = L.off[b1];
+    outY = L.zY[bt]; outF = L.zF[bt]; outS = L.zS[bt]; outOff = L.off[bt];
+    outCap = L.capZ;
   }
 
   OB_HD void node_table(int t) {
@@ -427,8 +675,8 @@ struct TcRun {
     const int lane = tm.lane();
     const int b1 = (t + 1) & 1;
     const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
-    const int* o1 = L.off[b1];
-    const double *Y1 = L.zY[b1], *F1 = L.zF[b1], *S1 = L.zS[b1];
+    const int* o1 = inOff;
+    const double *Y1 = inY, *F1 = inF, *S1 = inS;
     const double* nt1 = L.nt[b1];
     const int UB1 = ustart(o1, W1, 0, 0, W0);
     const int Utot = ustart(o1, W1, UB1, 1, W0);
@@ -491,13 +739,16 @@ struct TcRun {
     return !(tm.any(ovf) || wpos > L.capW);
   }
 
-  // pass 2: g, h and the per-node running minima of their keys
-  OB_HD void pass2(int t, int wtot) {
+  // pass 2: g, h and the per-node running minima of their keys (and, for the
+  // adjoint, the index where each minimum is attained)
+  template <bool TRACK = false>
+  OB_HD void pass2(int t, int wtot, int* argA = nullptr, int* argB = nullptr) {
     const int lane = tm.lane();
     const int W0 = t + 1;
     const double* nt = L.nt[t & 1];
     const long long KMAX = 0x7fffffffffffffffLL;
     long long carry = KMAX;
+    int carry_i = 0;
     for (int base = 0; base < wtot; base += Team::W) {
       const int i = base + lane;
       const bool ok = i < wtot;
@@ -512,176 +763,120 @@ struct TcRun {
         L.wH[i] = h;
         hk = okey(h);
       }
-      const long long v = tm.seg_min(hk, head, carry);
-      if (ok) L.wCB[i] = v;
+      if (TRACK) {
+        int ix = i;
+        tm.seg_argmin(hk, ix, head, carry, carry_i);
+        if (ok) { L.wCB[i] = hk; argB[i] = ix; }
+      } else {
+        const long long v = tm.seg_min(hk, head, carry);
+        if (ok) L.wCB[i] = v;
+      }
     }
     tm.sync();
     carry = KMAX;
+    carry_i = 0;
     const int ntiles = (wtot + Team::W - 1) / Team::W;
     for (int tile = ntiles - 1; tile >= 0; --tile) {
       const int i = tile * Team::W + (Team::W - 1 - lane);
       const bool ok = i < wtot;
       const int n = ok ? L.wN[i] : -1;
       const bool head = ok && (i + 1 == wtot || L.wN[i + 1] != n);
-      const long long gk = ok ? okey(L.wG[i]) : KMAX;
-      const long long v = tm.seg_min(gk, head, carry);
-      if (ok) L.wCA[i] = v;
+      long long gk = ok ? okey(L.wG[i]) : KMAX;
+      if (TRACK) {
+        int ix = i;
+        tm.seg_argmin(gk, ix, head, carry, carry_i);
+        if (ok) { L.wCA[i] = gk; argA[i] = ix; }
+      } else {
+        const long long v = tm.seg_min(gk, head, carry);
+        if (ok) L.wCA[i] = v;
+      }
     }
     tm.sync();
+  }
+
+  // inputs of the piece starting at point i of w (level t)
+  OB_HD void load_piece(int t, int i, int wtot, PieceIn<double>& in, int& node) const {
+    const int W0 = t + 1;
+    const double* nt = L.nt[t & 1];
+    node = L.wN[i];
+    in.head = (i == 0 || L.wN[i - 1] != node);
+    in.tail = (i + 1 == wtot || L.wN[i + 1] != node);
+    const int p = node >= W0 ? 1 : 0;
+    const int j = node - p * W0;
+    in.Sa = nt[4 * j];
+    in.Sb = nt[4 * j + 1];
+    const double xi = nt[4 * j + 2];
+    in.seller = (p == 0);
+    in.yu = in.seller ? (double)zeta : -(double)zeta;
+    in.vu = in.seller ? xi : -xi;
+    in.anchor = in.head && same_bits(in.Sa, in.Sb);
+    in.y0 = L.wY[i];
+    in.f0 = L.wF[i];
+    in.s0 = L.wS[i];
+    const long long cB = L.wCB[i];
+    in.cB = unkey(cB);
+    in.cA0 = unkey(L.wCA[i]);
+    in.Arel = in.Brel = false;
+    in.y1 = in.f1 = in.cA1 = 0.0;
+    if (!in.tail) {
+      in.y1 = L.wY[i + 1];
+      in.f1 = L.wF[i + 1];
+      const long long cA1 = L.wCA[i + 1];
+      in.cA1 = unkey(cA1);
+      const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
+      const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
+      // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
+      // the cB line iff h <= cB_i at both ends (then that side of v equals w)
+      in.Arel = !(g1 == cA1 && g0 <= cA1);
+      in.Brel = !(h0 == cB && h1 <= cB);
+    }
   }
 
   // pass 3: restriction and exercise for every piece of w; writes level t
   OB_HD bool pass3(int t, int wtot, int& ztot) {
     const int lane = tm.lane();
-    const int bt = t & 1, W0 = t + 1, nNodes = 2 * W0;
-    const double* nt = L.nt[bt];
-    const double INF = ob_inf();
-    int* off = L.off[bt];
-    double* Yz = L.zY[bt];
-    double* Fz = L.zF[bt];
-    double* Sz = L.zS[bt];
+    const int nNodes = 2 * (t + 1);
+    int* off = outOff;
+    double* Yz = outY;
+    double* Fz = outF;
+    double* Sz = outS;
     int zpos = 0;
     bool ovf = false;
     double carry_slope = 0.0;
     for (int base = 0; base < wtot; base += Team::W) {
       const int i = base + lane;
       const bool ok = i < wtot;
-      Em em[2 * MAXSUB + 1];
-      int ntl = 0, nm = 0;  // internal emissions of the left tail and of the main piece
-      Em first{0.0, 0.0, 0.0};
-      double last_slope = 0.0, tail_slope = 0.0;
+      PieceOut<double> po;
+      po.ntl = po.nm = 0;
+      po.first = EmT<double>{0.0, 0.0, 0.0};
+      po.last_slope = po.tail_slope = 0.0;
       bool head = false, anchor = false;
       int node = -1;
       if (ok) {
-        node = L.wN[i];
-        head = (i == 0 || L.wN[i - 1] != node);
-        const bool tail = (i + 1 == wtot || L.wN[i + 1] != node);
-        const int p = node >= W0 ? 1 : 0;
-        const int j = node - p * W0;
-        const double Sa = nt[4 * j], Sb = nt[4 * j + 1], xi = nt[4 * j + 2];
-        const bool seller = (p == 0);
-        const double yu = seller ? (double)zeta : -(double)zeta;
-        const double vu = seller ? xi : -xi;
-        anchor = head && same_bits(Sa, Sb);
-        const double y0 = L.wY[i], f0 = L.wF[i], s0 = L.wS[i];
-        const long long cB = L.wCB[i];
-        // line table: 0 piece of w, 1 cA line (slope -S^a), 2 cB line (slope -S^b),
-        //             3 left branch of u (slope -S^a), 4 right branch of u (slope -S^b)
-        Ln lines[5];
-        lines[2] = Ln{0.0, unkey(cB), -Sb, 0.0, 0.0, 1};
-        lines[3] = Ln{yu, vu, -Sa, INF, 0.0, 0};
-        lines[4] = Ln{yu, vu, -Sb, INF, 0.0, 0};
-        if (head) {  // left tail: v is the cA_0 line
-          lines[1] = Ln{0.0, unkey(L.wCA[i]), -Sa, 0.0, 0.0, 1};
-          Subs S;
-          S.ns = 1;
-          S.xs[0] = -INF;
-          S.li[0] = 1;
-          S.hi = y0;
-          if (klt(yu, y0)) subs_split(S, yu);
-          subs_combine(S, lines, 3, 4, yu, seller);
-          for (int k = 1; k < S.ns; ++k) {
-            const Ln& l = lines[S.li[k]];
-            if (!same_bits(l.s, lines[S.li[k - 1]].s)) em[ntl++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
-          }
-          tail_slope = lines[S.li[S.ns - 1]].s;
-        }
-        bool done = false;
-        if (!tail) {
-          const double y1 = L.wY[i + 1], f1 = L.wF[i + 1];
-          const long long cA1 = L.wCA[i + 1];
-          const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
-          const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
-          // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
-          // the cB line iff h <= cB_i at both ends (then that side of v equals w)
-          const bool Arel = !(g1 == cA1 && g0 <= cA1);
-          const bool Brel = !(h0 == cB && h1 <= cB);
-          if (!Arel && !Brel && !(klt(y0, yu) && klt(yu, y1))) {
-            // common case: v = w on the piece and one branch of u covers it
-            done = true;
-            const bool leftside = klt(y0, yu);
-            const double sQ = leftside ? -Sa : -Sb;
-            const double q0 = vu + sQ * (y0 - yu), q1 = vu + sQ * (y1 - yu);
-            const long long kf0 = okey(f0), kq0 = okey(q0), kf1 = okey(f1), kq1 = okey(q1);
-            const long long ks0 = okey(s0), ksQ = okey(sQ);
-            // winner at the left end (0 = w, 1 = u); ties go to the line that wins just right
-            int wl, wr;
-            if (kf0 != kq0) wl = ((kf0 > kq0) == seller) ? 0 : 1;
-            else wl = (ks0 == ksQ) ? 0 : (((ks0 > ksQ) == seller) ? 0 : 1);
-            if (kf1 != kq1) wr = ((kf1 > kq1) == seller) ? 0 : 1;
-            else wr = (ks0 == ksQ) ? 0 : (((ks0 < ksQ) == seller) ? 0 : 1);
-            if (wl == wr || ks0 == ksQ) {
-              first = (wl == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
-              last_slope = (wl == 0) ? s0 : sQ;
-            } else {
-              const double x = y0 + (f0 - q0) / (sQ - s0);
-              const int left_line = ((ks0 < ksQ) == seller) ? 0 : 1;
-              if (!klt(y0, x)) {
-                first = (left_line == 0) ? Em{y0, q0, sQ} : Em{y0, f0, s0};
-                last_slope = first.s;
-              } else if (!klt(x, y1)) {
-                first = (left_line == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
-                last_slope = first.s;
-              } else {
-                first = (left_line == 0) ? Em{y0, f0, s0} : Em{y0, q0, sQ};
-                const double sr = (left_line == 0) ? sQ : s0;
-                const double vr = (left_line == 0) ? vu + sQ * (x - yu) : f0 + s0 * (x - y0);
-                em[ntl + 1 + nm++] = Em{x, vr, sr};
-                last_slope = sr;
-              }
-            }
-          }
-        }
-        if (!done) {
-          Subs S;
-          S.ns = 1;
-          S.xs[0] = y0;
-          if (tail) {  // right tail: v is the cB line
-            S.li[0] = 2;
-            S.hi = INF;
-          } else {
-            const double y1 = L.wY[i + 1], f1 = L.wF[i + 1];
-            const long long cA1 = L.wCA[i + 1];
-            const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
-            const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
-            lines[0] = Ln{y0, f0, s0, y1, f1, 0};
-            lines[1] = Ln{0.0, unkey(cA1), -Sa, 0.0, 0.0, 1};
-            S.li[0] = 0;
-            S.hi = y1;
-            const bool Arel = !(g1 == cA1 && g0 <= cA1);
-            const bool Brel = !(h0 == cB && h1 <= cB);
-            if (Brel) subs_combine(S, lines, 2, 2, INF, false);
-            if (Arel) subs_combine(S, lines, 1, 1, INF, false);
-          }
-          if (klt(y0, yu) && klt(yu, S.hi)) subs_split(S, yu);
-          subs_combine(S, lines, 3, 4, yu, seller);
-          first = Em{y0, ln_eval(lines[S.li[0]], y0), lines[S.li[0]].s};
-          for (int k = 1; k < S.ns; ++k) {
-            const Ln& l = lines[S.li[k]];
-            if (!same_bits(l.s, lines[S.li[k - 1]].s))
-              em[ntl + 1 + nm++] = Em{S.xs[k], ln_eval(l, S.xs[k]), l.s};
-          }
-          last_slope = lines[S.li[S.ns - 1]].s;
-        }
+        PieceIn<double> in;
+        load_piece(t, i, wtot, in, node);
+        head = in.head;
+        anchor = in.anchor;
+        NoDec nd;
+        piece(in, po, nd);
       }
+      const double last_slope = po.last_slope;
       // slope of z just left of this piece's first point
       double tile_last_slope;
       double prev = tm.prev_last(last_slope, carry_slope, tile_last_slope);
-      if (head) prev = tail_slope;
-      const int emit_first = (ok && (anchor || !same_bits(prev, first.s))) ? 1 : 0;
-      const int nout = ok ? ntl + emit_first + nm : 0;
+      if (head) prev = po.tail_slope;
+      const int emit_first = (ok && (anchor || !same_bits(prev, po.first.s))) ? 1 : 0;
+      const int nout = ok ? po.ntl + emit_first + po.nm : 0;
       int total;
       const int pre = tm.excl_sum(nout, total);
       const int p0 = zpos + pre;
       if (ok && head) off[node] = p0;
       if (ok) {
-        if (p0 + nout <= L.capZ) {
+        if (p0 + nout <= outCap) {
           int w = p0;
-          for (int c = 0; c < ntl; ++c, ++w) { Yz[w] = em[c].y; Fz[w] = em[c].f; Sz[w] = em[c].s; }
-          if (emit_first) { Yz[w] = first.y; Fz[w] = first.f; Sz[w] = first.s; ++w; }
-          for (int c = 0; c < nm; ++c, ++w) {
-            Yz[w] = em[ntl + 1 + c].y; Fz[w] = em[ntl + 1 + c].f; Sz[w] = em[ntl + 1 + c].s;
-          }
+          for (int c = 0; c < po.ntl; ++c, ++w) { Yz[w] = po.tl[c].y; Fz[w] = po.tl[c].f; Sz[w] = po.tl[c].s; }
+          if (emit_first) { Yz[w] = po.first.y; Fz[w] = po.first.f; Sz[w] = po.first.s; ++w; }
+          for (int c = 0; c < po.nm; ++c, ++w) { Yz[w] = po.m[c].y; Fz[w] = po.m[c].f; Sz[w] = po.m[c].s; }
         } else if (nout > 0) {
           ovf = true;
         }
@@ -691,7 +886,7 @@ struct TcRun {
     }
     if (lane == 0) off[nNodes] = zpos;
     ztot = zpos;
-    return !(tm.any(ovf) || zpos > L.capZ);
+    return !(tm.any(ovf) || zpos > outCap);
   }
 
   // value at y = 0 of node n of level 0 (bank 0)
@@ -734,6 +929,7 @@ struct TcRun {
     }
     if (2 * (N + 2) > L.capZ) return ST_CAPACITY;
     for (int t = N; t >= 0; --t) {
+      use_banks(t);
       node_table(t);
       tm.sync();
       int wtot = 0, ztot = 0, utot = 0;

@@ -123,6 +123,28 @@ struct WarpTeam {
     carry = __shfl_sync(0xffffffffu, v, 31);
     return v;
   }
+  // seg_min that also carries the index of the minimum
+  __device__ __forceinline__ void seg_argmin(long long& v, int& ix, bool head, long long& cv,
+                                             int& ci) const {
+    const int l = lane();
+    int fl = head ? 1 : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long vu = __shfl_up_sync(0xffffffffu, v, d);
+      const int iu = __shfl_up_sync(0xffffffffu, ix, d);
+      const int fu = __shfl_up_sync(0xffffffffu, fl, d);
+      if (l >= d) {
+        if (!fl && vu < v) { v = vu; ix = iu; }
+        fl |= fu;
+      }
+    }
+    if (!fl && cv < v) { v = cv; ix = ci; }
+    cv = __shfl_sync(0xffffffffu, v, 31);
+    ci = __shfl_sync(0xffffffffu, ix, 31);
+  }
+  __device__ __forceinline__ double sum(double v) const {
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+  }
 };
 
 template <class T>
@@ -147,7 +169,7 @@ __device__ __forceinline__ double from_ll<double>(long long v) { return __longlo
 template <int NW>
 struct BlockTeam {
   static constexpr int W = 32 * NW;
-  static constexpr int BUF = W + 2 * NW + 4;
+  static constexpr int BUF = W + 4 * NW + 8;
   long long* buf;
   __device__ __forceinline__ int lane() const { return threadIdx.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
@@ -237,6 +259,48 @@ struct BlockTeam {
     carry = buf[W + 2 * NW];
     __syncthreads();
     return v;
+  }
+  __device__ __forceinline__ void seg_argmin(long long& v, int& ix, bool head, long long& cv,
+                                             int& ci) const {
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int fl = head ? 1 : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long vu = __shfl_up_sync(0xffffffffu, v, d);
+      const int iu = __shfl_up_sync(0xffffffffu, ix, d);
+      const int fu = __shfl_up_sync(0xffffffffu, fl, d);
+      if (l >= d) {
+        if (!fl && vu < v) { v = vu; ix = iu; }
+        fl |= fu;
+      }
+    }
+    if (l == 31) {
+      buf[W + 3 * w] = v;
+      buf[W + 3 * w + 1] = ix;
+      buf[W + 3 * w + 2] = fl;
+    }
+    __syncthreads();
+    if (!fl) {
+      bool stop = false;
+      for (int k = w - 1; k >= 0 && !stop; --k) {
+        if (buf[W + 3 * k] < v) { v = buf[W + 3 * k]; ix = (int)buf[W + 3 * k + 1]; }
+        stop = buf[W + 3 * k + 2] != 0;
+      }
+      if (!stop && cv < v) { v = cv; ix = ci; }
+    }
+    if (threadIdx.x == W - 1) { buf[W + 3 * NW] = v; buf[W + 3 * NW + 1] = ix; }
+    __syncthreads();
+    cv = buf[W + 3 * NW];
+    ci = (int)buf[W + 3 * NW + 1];
+    __syncthreads();
+  }
+  __device__ __forceinline__ double sum(double v) const {
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) buf[W + (threadIdx.x >> 5)] = __double_as_longlong(v);
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < NW; ++k) t += __longlong_as_double(buf[W + k]);
+    __syncthreads();
+    return t;
   }
 };
 #endif
