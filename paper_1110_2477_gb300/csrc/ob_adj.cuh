@@ -304,7 +304,7 @@ struct TcAdj {
     const double* nt1 = L.nt[(t + 1) & 1];
     const int UB1 = R.ustart(o1, W1, 0, 0, W0);
     const int Utot = R.ustart(o1, W1, UB1, 1, W0);
-    int ncur = 0, wpos = 0, carry_own = 0;
+    int ncur = 0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
     for (int base = 0; base < Utot; base += Team::W) {
       const int q = base + lane;
       const int nl = ncur + lane;
@@ -313,8 +313,9 @@ struct TcAdj {
         const int p = nl >= W0 ? 1 : 0;
         nend = R.ustart(o1, W1, UB1, p, nl - p * W0 + 1);
       }
-      const int pos = tm.count_le(nend, q);
-      const int ncur_next = ncur + tm.count(nend <= base + Team::W);
+      int pos, nend_le;
+      tm.count_le2(nend, q, base + Team::W, pos, nend_le);
+      const int ncur_next = ncur + nend_le;
       P1 e;
       e.dup = true;
       int node = ncur + pos, ql = -1, p = 0, j = 0, aoff = 0, boff = 0, ma = 0, mb = 0;
@@ -330,12 +331,13 @@ struct TcAdj {
         p1_analyze(Y1 + aoff, F1 + aoff, S1 + aoff, ma, -nt1[4 * (j + 1)], Y1 + boff, F1 + boff,
                    S1 + boff, mb, -nt1[4 * j], ql, e);
       }
-      int own = e.own;
-      const int v1 = tm.prev(own, carry_own);
-      if (q < Utot && e.dup) own = v1;
-      int last_own;
-      const int v2 = tm.prev_last(own, carry_own, last_own);
-      carry_own = last_own;
+      // owner of the segment ending at this point: that of the previous union point,
+      // looking past a duplicate (duplicates are never adjacent); encoded 2*own + dup
+      int m1, m2, l1, l2;
+      const int code = (q < Utot && e.dup) ? 1 : 2 * e.own;
+      tm.look2(code, carry_own, carry_own, m1, m2, l1, l2);
+      const int v2 = (m1 & 1) ? (m2 >> 1) : (m1 >> 1);
+      carry_own = (l1 & 1) ? l2 : l1;
       int cnt = 0;
       int wl = 0;
       bool emit_pt = false;

@@ -30,7 +30,7 @@ constexpr int kTiers = 3;            // launches per ob_price_ask_bid call
 constexpr int kTier1Ctas = 16;       // CTAs of the first follow-up launch
 constexpr int kSortMax = 8192;       // largest batch ordered by cost
 constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
-constexpr double kHeavyFactor = 2.0; // heavy: predicted cost > factor x (total / warps)
+constexpr double kHeavyFactor = 0.0; // heavy: predicted cost > factor x (total / warps); 0: all
 // control words
 enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
        C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
@@ -173,11 +173,12 @@ __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, c
 // Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
 // one at a time as a whole-CTA team, then each of its warps takes the remaining
 // options one at a time from a second queue.  Both queues are device counters.
-__global__ void __launch_bounds__(kTeamBlock, 2) k_tc_batched(
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
     char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds) {
-  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
-  obk::BlockTeam<kNW> bt{tbuf};
+  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+  obk::BlockTeam<NW> bt{tbuf};
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
   const int nh = order ? *((volatile int*)&ctl[C_NHEAVY]) : 0;
   for (;;) {
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kTeamBlock, 2) k_tc_batched(
     bt.sync();
   }
   obk::WarpTeam wt;
-  const size_t wbytes = (cta_bytes / kNW) & ~(size_t)255;
+  const size_t wbytes = (cta_bytes / NW) & ~(size_t)255;
   char* wmy = my + (size_t)(threadIdx.x >> 5) * wbytes;
   for (;;) {
     int v = 0;
@@ -436,6 +437,7 @@ struct DevPool {
   int warps_per_sm = 16;
   size_t arena_per_warp = 8ull << 20;
   double heavy_factor = kHeavyFactor;
+  int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -475,6 +477,10 @@ int pool_get(DevPool** out, size_t need_list) {
     P.warps_per_sm = (int)env_size("OB_WARPS_PER_SM", 16);
     P.arena_per_warp = env_size("OB_ARENA_MB", 8) << 20;
     if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
+    if (const char* tw = getenv("OB_TEAM_WARPS")) {
+      const int v = atoi(tw);
+      if (v == 4 || v == 8 || v == 16) P.team_warps = v;
+    }
     const size_t workers = (size_t)P.sms * P.warps_per_sm;
     P.arena_bytes = workers * P.arena_per_warp;
     const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
@@ -537,21 +543,29 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
     P->last_tiers = 1;
     return OB_OK;
   }
-  const int nctas = P->sms * 2;
+  const int nctas = P->sms * (16 / P->team_warps);
   const int* order = nullptr;
   if (n <= kSortMax) {
     int npad = 1;
     while (npad < n) npad <<= 1;
     k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order, P->ctl,
-                                                               nctas * kNW, nctas, P->heavy_factor);
+                                                               nctas * P->team_warps, nctas,
+                                                               P->heavy_factor);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
   const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
-  k_tc_batched<<<nctas, kTeamBlock, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
-                                            list0, P->stats);
+  if (P->team_warps == 4)
+    k_tc_batched<4><<<nctas, 128, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
+                                          list0, P->stats);
+  else if (P->team_warps == 16)
+    k_tc_batched<16><<<nctas, 512, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
+                                           list0, P->stats);
+  else
+    k_tc_batched<8><<<nctas, 256, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
+                                          list0, P->stats);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   k_tc_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF],
@@ -804,7 +818,7 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
                                                              kHeavyFactor);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
-  k_tc_batched<<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
+  k_tc_batched<kNW><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
                                                    list0, ds);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0,

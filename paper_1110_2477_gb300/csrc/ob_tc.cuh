@@ -681,7 +681,7 @@ struct TcRun {
     const int UB1 = ustart(o1, W1, 0, 0, W0);
     const int Utot = ustart(o1, W1, UB1, 1, W0);
     utot = Utot;
-    int ncur = 0, wpos = 0, carry_own = 0;
+    int ncur = 0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
     bool ovf = false;
     for (int base = 0; base < Utot; base += Team::W) {
       const int q = base + lane;
@@ -692,8 +692,9 @@ struct TcRun {
         nend = ustart(o1, W1, UB1, p, nl - p * W0 + 1);
       }
       // node of q: number of node ends <= q among those loaded (ends are increasing)
-      const int pos = tm.count_le(nend, q);
-      const int ncur_next = ncur + tm.count(nend <= base + Team::W);
+      int pos, nend_le;
+      tm.count_le2(nend, q, base + Team::W, pos, nend_le);
+      const int ncur_next = ncur + nend_le;
       Em em[3];
       P1 e;
       e.dup = true;
@@ -709,13 +710,12 @@ struct TcRun {
                    S1 + boff, mb, -nt1[4 * j], ql, e);
       }
       // owner of the segment ending at this point: that of the previous union point,
-      // forwarded across a duplicate (duplicates are never adjacent)
-      int own = e.own;
-      const int v1 = tm.prev(own, carry_own);
-      if (q < Utot && e.dup) own = v1;
-      int last_own;
-      const int v2 = tm.prev_last(own, carry_own, last_own);
-      carry_own = last_own;
+      // looking past a duplicate (duplicates are never adjacent); encoded 2*own + dup
+      int m1, m2, l1, l2;
+      const int code = (q < Utot && e.dup) ? 1 : 2 * e.own;
+      tm.look2(code, carry_own, carry_own, m1, m2, l1, l2);
+      const int v2 = (m1 & 1) ? (m2 >> 1) : (m1 >> 1);
+      carry_own = (l1 & 1) ? l2 : l1;
       if (q < Utot) cnt = p1_emit(e, ql == 0 ? e.wl_first : v2, em);
       int total;
       const int pre = tm.excl_sum(cnt, total);

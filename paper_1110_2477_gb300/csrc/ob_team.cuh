@@ -96,6 +96,21 @@ struct WarpTeam {
     if (pos == 31 && x <= q) pos = 32;
     return pos;
   }
+  // counts of lanes with v <= q1 and v <= q2 (v nondecreasing in lane)
+  __device__ __forceinline__ void count_le2(int v, int q1, int q2, int& c1, int& c2) const {
+    c1 = count_le(v, q1);
+    c2 = __popc(__ballot_sync(0xffffffffu, v <= q2));  // q2 is the same on all lanes
+  }
+  // values of lanes l-1 and l-2 (carries for lanes 0 and 1) and of lanes W-1 and W-2
+  template <class T>
+  __device__ __forceinline__ void look2(T v, T c1, T c2, T& m1, T& m2, T& l1, T& l2) const {
+    const int l = lane();
+    const T a = __shfl_up_sync(0xffffffffu, v, 1), b = __shfl_up_sync(0xffffffffu, v, 2);
+    m1 = (l >= 1) ? a : c1;
+    m2 = (l >= 2) ? b : (l == 1 ? c1 : c2);
+    l1 = __shfl_sync(0xffffffffu, v, 31);
+    l2 = __shfl_sync(0xffffffffu, v, 30);
+  }
   __device__ __forceinline__ int count(bool p) const { return __popc(__ballot_sync(0xffffffffu, p)); }
   __device__ __forceinline__ bool any(bool p) const { return __ballot_sync(0xffffffffu, p) != 0u; }
   __device__ __forceinline__ int excl_sum(int v, int& total) const {
@@ -165,72 +180,102 @@ template <>
 __device__ __forceinline__ double from_ll<double>(long long v) { return __longlong_as_double(v); }
 
 // All threads of one CTA (NW warps, W = 32 NW lanes) working on one option.
-// Exchanges go through a shared-memory buffer of BUF slots.
+// Exchanges go through shared memory, two halves used alternately, so that one
+// barrier per exchange suffices: a half is rewritten only after the next
+// exchange's barrier, which every thread reaches after its reads of that half.
 template <int NW>
 struct BlockTeam {
   static constexpr int W = 32 * NW;
-  static constexpr int BUF = W + 4 * NW + 8;
+  static constexpr int HALF = W + 4 * NW + 8;
+  static constexpr int BUF = 2 * HALF;
   long long* buf;
+  mutable int par = 0;
+  __device__ __forceinline__ long long* half() const {
+    long long* h = buf + par * HALF;
+    par ^= 1;
+    return h;
+  }
   __device__ __forceinline__ int lane() const { return threadIdx.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
   template <class T>
   __device__ __forceinline__ T bcast0(T v) const {
-    if (threadIdx.x == 0) buf[W] = to_ll(v);
+    long long* h = half();
+    if (threadIdx.x == 0) h[0] = to_ll(v);
     __syncthreads();
-    const T r = from_ll<T>(buf[W]);
-    __syncthreads();
-    return r;
+    return from_ll<T>(h[0]);
   }
   template <class T>
   __device__ __forceinline__ T prev(T v, T carry) const {
-    buf[threadIdx.x] = to_ll(v);
+    long long* h = half();
+    h[threadIdx.x] = to_ll(v);
     __syncthreads();
-    const T r = threadIdx.x ? from_ll<T>(buf[threadIdx.x - 1]) : carry;
-    __syncthreads();
-    return r;
+    return threadIdx.x ? from_ll<T>(h[threadIdx.x - 1]) : carry;
   }
   template <class T>
   __device__ __forceinline__ T prev_last(T v, T carry, T& last) const {
-    buf[threadIdx.x] = to_ll(v);
+    long long* h = half();
+    h[threadIdx.x] = to_ll(v);
     __syncthreads();
-    const T r = threadIdx.x ? from_ll<T>(buf[threadIdx.x - 1]) : carry;
-    last = from_ll<T>(buf[W - 1]);
+    last = from_ll<T>(h[W - 1]);
+    return threadIdx.x ? from_ll<T>(h[threadIdx.x - 1]) : carry;
+  }
+  template <class T>
+  __device__ __forceinline__ void look2(T v, T c1, T c2, T& m1, T& m2, T& l1, T& l2) const {
+    long long* h = half();
+    const int l = threadIdx.x;
+    h[l] = to_ll(v);
     __syncthreads();
-    return r;
+    m1 = (l >= 1) ? from_ll<T>(h[l - 1]) : c1;
+    m2 = (l >= 2) ? from_ll<T>(h[l - 2]) : (l == 1 ? c1 : c2);
+    l1 = from_ll<T>(h[W - 1]);
+    l2 = from_ll<T>(h[W - 2]);
   }
   __device__ __forceinline__ int count_le(int v, int q) const {
-    buf[threadIdx.x] = v;
+    int c1, c2;
+    count_le2(v, q, q, c1, c2);
+    return c1;
+  }
+  __device__ __forceinline__ void count_le2(int v, int q1, int q2, int& c1, int& c2) const {
+    long long* h = half();
+    h[threadIdx.x] = v;
     __syncthreads();
-    int lo = 0, hi = W;  // first slot with value > q
+    int lo = 0, hi = W;  // first slot with value > q1
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if ((int)buf[mid] <= q) lo = mid + 1; else hi = mid;
+      if ((int)h[mid] <= q1) lo = mid + 1; else hi = mid;
     }
-    __syncthreads();
-    return lo;
+    c1 = lo;
+    lo = 0;
+    hi = W;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((int)h[mid] <= q2) lo = mid + 1; else hi = mid;
+    }
+    c2 = lo;
   }
   __device__ __forceinline__ int count(bool p) const { return __syncthreads_count(p ? 1 : 0); }
   __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p ? 1 : 0) != 0; }
   __device__ __forceinline__ int excl_sum(int v, int& total) const {
+    long long* h = half();
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = v;
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, d);
       if (l >= d) x += y;
     }
-    if (l == 31) buf[W + w] = x;
+    if (l == 31) h[W + w] = x;
     __syncthreads();
     int off = 0, tot = 0;
     for (int k = 0; k < NW; ++k) {
-      const int c = (int)buf[W + k];
+      const int c = (int)h[W + k];
       if (k < w) off += c;
       tot += c;
     }
-    __syncthreads();
     total = tot;
     return off + x - v;
   }
   __device__ __forceinline__ long long seg_min(long long v, bool head, long long& carry) const {
+    long long* h = half();
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
     int fl = head ? 1 : 0;
     for (int d = 1; d < 32; d <<= 1) {
@@ -242,26 +287,34 @@ struct BlockTeam {
       }
     }
     if (l == 31) {
-      buf[W + 2 * w] = v;
-      buf[W + 2 * w + 1] = fl;
+      h[W + 2 * w] = v;
+      h[W + 2 * w + 1] = fl;
     }
     __syncthreads();
     if (!fl) {  // no head in this warp up to here: continue from earlier warps, then the carry
       bool stop = false;
       for (int k = w - 1; k >= 0 && !stop; --k) {
-        v = kmin(v, buf[W + 2 * k]);
-        stop = buf[W + 2 * k + 1] != 0;
+        v = kmin(v, h[W + 2 * k]);
+        stop = h[W + 2 * k + 1] != 0;
       }
       if (!stop) v = kmin(v, carry);
     }
-    if (threadIdx.x == W - 1) buf[W + 2 * NW] = v;
-    __syncthreads();
-    carry = buf[W + 2 * NW];
-    __syncthreads();
+    // the new carry: the last lane's result, from the warp aggregates
+    {
+      long long c = h[W + 2 * (NW - 1)];
+      bool stop = h[W + 2 * (NW - 1) + 1] != 0;
+      for (int k = NW - 2; k >= 0 && !stop; --k) {
+        c = kmin(c, h[W + 2 * k]);
+        stop = h[W + 2 * k + 1] != 0;
+      }
+      if (!stop) c = kmin(c, carry);
+      carry = c;
+    }
     return v;
   }
   __device__ __forceinline__ void seg_argmin(long long& v, int& ix, bool head, long long& cv,
                                              int& ci) const {
+    long long* h = half();
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
     int fl = head ? 1 : 0;
     for (int d = 1; d < 32; d <<= 1) {
@@ -274,32 +327,39 @@ struct BlockTeam {
       }
     }
     if (l == 31) {
-      buf[W + 3 * w] = v;
-      buf[W + 3 * w + 1] = ix;
-      buf[W + 3 * w + 2] = fl;
+      h[W + 3 * w] = v;
+      h[W + 3 * w + 1] = ix;
+      h[W + 3 * w + 2] = fl;
     }
     __syncthreads();
     if (!fl) {
       bool stop = false;
       for (int k = w - 1; k >= 0 && !stop; --k) {
-        if (buf[W + 3 * k] < v) { v = buf[W + 3 * k]; ix = (int)buf[W + 3 * k + 1]; }
-        stop = buf[W + 3 * k + 2] != 0;
+        if (h[W + 3 * k] < v) { v = h[W + 3 * k]; ix = (int)h[W + 3 * k + 1]; }
+        stop = h[W + 3 * k + 2] != 0;
       }
       if (!stop && cv < v) { v = cv; ix = ci; }
     }
-    if (threadIdx.x == W - 1) { buf[W + 3 * NW] = v; buf[W + 3 * NW + 1] = ix; }
-    __syncthreads();
-    cv = buf[W + 3 * NW];
-    ci = (int)buf[W + 3 * NW + 1];
-    __syncthreads();
+    {
+      long long c = h[W + 3 * (NW - 1)];
+      int cidx = (int)h[W + 3 * (NW - 1) + 1];
+      bool stop = h[W + 3 * (NW - 1) + 2] != 0;
+      for (int k = NW - 2; k >= 0 && !stop; --k) {
+        if (h[W + 3 * k] < c) { c = h[W + 3 * k]; cidx = (int)h[W + 3 * k + 1]; }
+        stop = h[W + 3 * k + 2] != 0;
+      }
+      if (!stop && cv < c) { c = cv; cidx = ci; }
+      cv = c;
+      ci = cidx;
+    }
   }
   __device__ __forceinline__ double sum(double v) const {
+    long long* h = half();
     for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if ((threadIdx.x & 31) == 0) buf[W + (threadIdx.x >> 5)] = __double_as_longlong(v);
+    if ((threadIdx.x & 31) == 0) h[W + (threadIdx.x >> 5)] = __double_as_longlong(v);
     __syncthreads();
     double t = 0.0;
-    for (int k = 0; k < NW; ++k) t += __longlong_as_double(buf[W + k]);
-    __syncthreads();
+    for (int k = 0; k < NW; ++k) t += __longlong_as_double(h[W + k]);
     return t;
   }
 };
