@@ -381,109 +381,67 @@ OB_HD T ln_eval(const LnT<T>& l, const T& x) {
 
 constexpr int MAXSUB = 10;
 
-template <class T>
-struct SubsT {
-  T xs[MAXSUB];  // start of each sub-piece (xs[0] may be -inf)
-  int li[MAXSUB];
-  int ns;
-  T hi;          // end of the last sub-piece (may be +inf)
-};
-
-// Split the sub-piece containing x (strictly inside) at x.
+// Combine the line pi with the line qi on the sub-piece [x0, x1) (x0 may be -inf, x1
+// +inf): the result is max(P, Q) (take_max) or min(P, Q) there, as one or two
+// sub-pieces, returned as (x0, la) and, when split, (xb, lb).  A crossing that rounds
+// onto an end leaves one line: the side of a crossing follows from the slopes (left
+// of it the line of smaller slope is the larger one), so a tie at one end that
+// rounding tipped the wrong way cannot misplace the piece.
 template <class T, class D>
-OB_HD void subs_split(SubsT<T>& S, const T& x, D& dec) {
-  int at = -1;
-  for (int k = 0; k < S.ns; ++k) {
-    const double e = val((k + 1 < S.ns) ? S.xs[k + 1] : S.hi);
-    if (klt(val(S.xs[k]), val(x)) && klt(val(x), e)) { at = k; break; }
-  }
-  at = dec.take(at + 1) - 1;
-  if (at < 0) return;
-  for (int m = S.ns; m > at + 1; --m) {
-    S.xs[m] = S.xs[m - 1];
-    S.li[m] = S.li[m - 1];
-  }
-  S.xs[at + 1] = x;
-  S.li[at + 1] = S.li[at];
-  S.ns += 1;
-}
-
-// Replace every sub-piece line P by max(P, Q) (take_max) or min(P, Q), Q = lines[qi(k)],
-// where qi(k) = q_left if the sub-piece lies left of xq, else q_right.
-template <class T, class D>
-OB_HD void subs_combine(SubsT<T>& S, const LnT<T>* lines, int q_left, int q_right, double xq,
-                        bool take_max, D& dec) {
-  SubsT<T> O;
-  O.ns = 0;
-  O.hi = S.hi;
+OB_HD int comb1(const LnT<T>* lines, const T& x0, const T& x1, int pi, int qi, bool take_max,
+                D& dec, int& la, T& xb, int& lb) {
+  la = pi;
+  if (pi == qi) return 1;
   const double INF = ob_inf();
-  for (int k = 0; k < S.ns; ++k) {
-    const T x0 = S.xs[k];
-    const T x1 = (k + 1 < S.ns) ? S.xs[k + 1] : S.hi;
-    const int pi = S.li[k];
-    const int qi = dec.take(klt(val(x0), xq) ? q_left : q_right);
-    if (pi == qi) {
-      O.xs[O.ns] = x0; O.li[O.ns] = pi; ++O.ns;
-      continue;
-    }
-    const LnT<T>& P = lines[pi];
-    const LnT<T>& Q = lines[qi];
-    const bool finite0 = !same_bits(val(x0), -INF), finite1 = !same_bits(val(x1), INF);
-    const long long kps = okey(val(P.s)), kqs = okey(val(Q.s));
-    // outcome: 0 left winner whole, 1 right line whole, 2 left line whole, 3 split
-    int outcome = 0, lw = pi;
-    T p0 = mk<T>(0.0), q0 = mk<T>(0.0), p1 = mk<T>(0.0), q1 = mk<T>(0.0);
-    if (finite0) { p0 = ln_eval(P, x0); q0 = ln_eval(Q, x0); }
-    if (finite1) { p1 = ln_eval(P, x1); q1 = ln_eval(Q, x1); }
-    const int left_line = ((kps < kqs) == take_max) ? pi : qi;
-    const int right_line = (left_line == pi) ? qi : pi;
-    {
-      int wl, wr;  // 0 = P, 1 = Q
-      if (finite0) {
-        const long long a = okey(val(p0)), b = okey(val(q0));
-        if (a != b) wl = ((a > b) == take_max) ? 0 : 1;
-        else wl = (kps == kqs) ? 0 : (((kps > kqs) == take_max) ? 0 : 1);
-      } else {
-        if (kps != kqs) wl = ((kps < kqs) == take_max) ? 0 : 1;
-        else { const long long a = okey(val(p1)), b = okey(val(q1)); wl = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
-      }
-      if (finite1) {
-        const long long a = okey(val(p1)), b = okey(val(q1));
-        if (a != b) wr = ((a > b) == take_max) ? 0 : 1;
-        else wr = (kps == kqs) ? 0 : (((kps < kqs) == take_max) ? 0 : 1);
-      } else {
-        if (kps != kqs) wr = ((kps > kqs) == take_max) ? 0 : 1;
-        else { const long long a = okey(val(p0)), b = okey(val(q0)); wr = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
-      }
-      lw = wl ? qi : pi;
-      if (wl == wr || kps == kqs) {
-        outcome = 0;
-      } else {
-        // The end values disagree, so the lines cross; which line owns each side of the
-        // crossing follows from the slopes (left of it the smaller slope is larger), so a
-        // tie at one end that rounding tipped the wrong way cannot misplace the piece.
-        const double xd = finite0 ? val(x0) + (val(p0) - val(q0)) / (val(Q.s) - val(P.s))
-                                  : val(x1) + (val(p1) - val(q1)) / (val(Q.s) - val(P.s));
-        if (!klt(val(x0), xd)) outcome = 1;
-        else if (!klt(xd, val(x1))) outcome = 2;
-        else outcome = 3;
-      }
-    }
-    outcome = dec.take(outcome);
-    lw = dec.take(lw);
-    if (outcome == 0) {
-      O.xs[O.ns] = x0; O.li[O.ns] = lw; ++O.ns;
-    } else if (outcome == 1) {
-      O.xs[O.ns] = x0; O.li[O.ns] = right_line; ++O.ns;
-    } else if (outcome == 2) {
-      O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
+  const LnT<T>& P = lines[pi];
+  const LnT<T>& Q = lines[qi];
+  const bool finite0 = !same_bits(val(x0), -INF), finite1 = !same_bits(val(x1), INF);
+  const long long kps = okey(val(P.s)), kqs = okey(val(Q.s));
+  // outcome: 0 left winner whole, 1 right line whole, 2 left line whole, 3 split
+  int outcome = 0, lw = pi;
+  T p0 = mk<T>(0.0), q0 = mk<T>(0.0), p1 = mk<T>(0.0), q1 = mk<T>(0.0);
+  if (finite0) { p0 = ln_eval(P, x0); q0 = ln_eval(Q, x0); }
+  if (finite1) { p1 = ln_eval(P, x1); q1 = ln_eval(Q, x1); }
+  const int left_line = ((kps < kqs) == take_max) ? pi : qi;
+  const int right_line = (left_line == pi) ? qi : pi;
+  {
+    int wl, wr;  // 0 = P, 1 = Q
+    if (finite0) {
+      const long long a = okey(val(p0)), b = okey(val(q0));
+      if (a != b) wl = ((a > b) == take_max) ? 0 : 1;
+      else wl = (kps == kqs) ? 0 : (((kps > kqs) == take_max) ? 0 : 1);
     } else {
-      const T x = finite0 ? x0 + (p0 - q0) / (Q.s - P.s) : x1 + (p1 - q1) / (Q.s - P.s);
-      O.xs[O.ns] = x0; O.li[O.ns] = left_line; ++O.ns;
-      O.xs[O.ns] = x; O.li[O.ns] = right_line; ++O.ns;
+      if (kps != kqs) wl = ((kps < kqs) == take_max) ? 0 : 1;
+      else { const long long a = okey(val(p1)), b = okey(val(q1)); wl = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+    }
+    if (finite1) {
+      const long long a = okey(val(p1)), b = okey(val(q1));
+      if (a != b) wr = ((a > b) == take_max) ? 0 : 1;
+      else wr = (kps == kqs) ? 0 : (((kps < kqs) == take_max) ? 0 : 1);
+    } else {
+      if (kps != kqs) wr = ((kps > kqs) == take_max) ? 0 : 1;
+      else { const long long a = okey(val(p0)), b = okey(val(q0)); wr = (a == b) ? 0 : (((a > b) == take_max) ? 0 : 1); }
+    }
+    lw = wl ? qi : pi;
+    if (wl == wr || kps == kqs) {
+      outcome = 0;
+    } else {
+      const double xd = finite0 ? val(x0) + (val(p0) - val(q0)) / (val(Q.s) - val(P.s))
+                                : val(x1) + (val(p1) - val(q1)) / (val(Q.s) - val(P.s));
+      if (!klt(val(x0), xd)) outcome = 1;
+      else if (!klt(xd, val(x1))) outcome = 2;
+      else outcome = 3;
     }
   }
-  S = O;
+  outcome = dec.take(outcome);
+  lw = dec.take(lw);
+  if (outcome == 0) { la = lw; return 1; }
+  if (outcome == 1) { la = right_line; return 1; }
+  if (outcome == 2) { la = left_line; return 1; }
+  la = left_line;
+  lb = right_line;
+  xb = finite0 ? x0 + (p0 - q0) / (Q.s - P.s) : x1 + (p1 - q1) / (Q.s - P.s);
+  return 2;
 }
 
 template <class T>
@@ -525,21 +483,25 @@ OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
   lines[2] = LnT<T>{mk<T>(0.0), in.cB, -in.Sb, mk<T>(0.0), mk<T>(0.0), 1};
   lines[3] = LnT<T>{yu, in.vu, -in.Sa, mk<T>(INF), mk<T>(0.0), 0};
   lines[4] = LnT<T>{yu, in.vu, -in.Sb, mk<T>(INF), mk<T>(0.0), 0};
-  if (in.head) {  // left tail: v is the cA_0 line
+  if (in.head) {  // left tail: v is the cA_0 line; u turns at yu if yu < y0
     lines[1] = LnT<T>{mk<T>(0.0), in.cA0, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
-    SubsT<T> S;
-    S.ns = 1;
-    S.xs[0] = mk<T>(-INF);
-    S.li[0] = 1;
-    S.hi = in.y0;
-    if (dec.take(klt(in.yu, val(in.y0)) ? 1 : 0)) subs_split(S, yu, dec);
-    subs_combine(S, lines, 3, 4, in.yu, in.seller, dec);
-    for (int k = 1; k < S.ns; ++k) {
-      const LnT<T>& l = lines[S.li[k]];
-      if (dec.take(same_bits(val(l.s), val(lines[S.li[k - 1]].s)) ? 0 : 1))
-        out.tl[out.ntl++] = EmT<T>{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+    const bool split = dec.take(klt(in.yu, val(in.y0)) ? 1 : 0);
+    int prev_l = -1;
+    for (int part = 0; part < (split ? 2 : 1); ++part) {
+      const T x0 = part ? yu : mk<T>(-INF);
+      const T x1 = split && !part ? yu : in.y0;
+      int la, lb;
+      T xb;
+      const int n = comb1(lines, x0, x1, 1, part ? 4 : 3, in.seller, dec, la, xb, lb);
+      for (int c = 0; c < n; ++c) {
+        const int l = c ? lb : la;
+        const T x = c ? xb : x0;
+        if (prev_l >= 0 && dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1))
+          out.tl[out.ntl++] = EmT<T>{x, ln_eval(lines[l], x), lines[l].s};
+        prev_l = l;
+      }
     }
-    out.tail_slope = val(lines[S.li[S.ns - 1]].s);
+    out.tail_slope = val(lines[prev_l].s);
   }
   const bool fast = dec.take((!in.tail && !in.Arel && !in.Brel &&
                               !(klt(val(in.y0), in.yu) && klt(in.yu, val(in.y1)))) ? 1 : 0);
@@ -589,29 +551,68 @@ OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
     }
     return;
   }
-  SubsT<T> S;
-  S.ns = 1;
-  S.xs[0] = in.y0;
-  if (in.tail) {  // right tail: v is the cB line
-    S.li[0] = 2;
-    S.hi = mk<T>(INF);
+  // general case: v = min(w, cB line, cA line) on the piece as up to four sub-pieces
+  // (the right tail: the cB line alone), each then split at yu and combined with u
+  int vl[4];
+  T vx[4];
+  int nv = 1;
+  vx[0] = in.y0;
+  T hi;
+  if (in.tail) {
+    vl[0] = 2;
+    hi = mk<T>(INF);
   } else {
     lines[0] = LnT<T>{in.y0, in.f0, in.s0, in.y1, in.f1, 0};
     lines[1] = LnT<T>{mk<T>(0.0), in.cA1, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
-    S.li[0] = 0;
-    S.hi = in.y1;
-    if (in.Brel) subs_combine(S, lines, 2, 2, INF, false, dec);
-    if (in.Arel) subs_combine(S, lines, 1, 1, INF, false, dec);
+    vl[0] = 0;
+    hi = in.y1;
+    if (in.Brel) {
+      int la, lb;
+      T xb;
+      nv = comb1(lines, in.y0, hi, 0, 2, false, dec, la, xb, lb);
+      vl[0] = la;
+      if (nv == 2) { vx[1] = xb; vl[1] = lb; }
+    }
+    if (in.Arel) {
+      int ml[4];
+      T mx[4];
+      int nm = 0;
+      for (int k = 0; k < nv; ++k) {
+        int la, lb;
+        T xb;
+        const int n = comb1(lines, vx[k], k + 1 < nv ? vx[k + 1] : hi, vl[k], 1, false, dec, la, xb, lb);
+        mx[nm] = vx[k]; ml[nm] = la; ++nm;
+        if (n == 2) { mx[nm] = xb; ml[nm] = lb; ++nm; }
+      }
+      for (int k = 0; k < nm; ++k) { vx[k] = mx[k]; vl[k] = ml[k]; }
+      nv = nm;
+    }
   }
-  if (dec.take((klt(val(in.y0), in.yu) && klt(in.yu, val(S.hi))) ? 1 : 0)) subs_split(S, yu, dec);
-  subs_combine(S, lines, 3, 4, in.yu, in.seller, dec);
-  out.first = EmT<T>{in.y0, ln_eval(lines[S.li[0]], in.y0), lines[S.li[0]].s};
-  for (int k = 1; k < S.ns; ++k) {
-    const LnT<T>& l = lines[S.li[k]];
-    if (dec.take(same_bits(val(l.s), val(lines[S.li[k - 1]].s)) ? 0 : 1))
-      out.m[out.nm++] = EmT<T>{S.xs[k], ln_eval(l, S.xs[k]), l.s};
+  int prev_l = -1;
+  for (int k = 0; k < nv; ++k) {
+    const T a = vx[k];
+    const T b = k + 1 < nv ? vx[k + 1] : hi;
+    const bool split = dec.take((klt(val(a), in.yu) && klt(in.yu, val(b))) ? 1 : 0);
+    for (int part = 0; part < (split ? 2 : 1); ++part) {
+      const T x0 = part ? yu : a;
+      const T x1 = split && !part ? yu : b;
+      int la, lb;
+      T xb;
+      const int qi = klt(val(x0), in.yu) ? 3 : 4;
+      const int n = comb1(lines, x0, x1, vl[k], qi, in.seller, dec, la, xb, lb);
+      for (int c = 0; c < n; ++c) {
+        const int l = c ? lb : la;
+        const T x = c ? xb : x0;
+        if (prev_l < 0) {
+          out.first = EmT<T>{in.y0, ln_eval(lines[l], in.y0), lines[l].s};
+        } else if (dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1)) {
+          out.m[out.nm++] = EmT<T>{x, ln_eval(lines[l], x), lines[l].s};
+        }
+        prev_l = l;
+      }
+    }
   }
-  out.last_slope = val(lines[S.li[S.ns - 1]].s);
+  out.last_slope = val(lines[prev_l].s);
 }
 
 // ------------------------------------------------------------------ the option
