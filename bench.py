@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-greeks", action="store_true", help="skip the Greeks-vs-plain comparison")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small"],
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default team width")
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr"],
                     help="batched: the 4096-option batch (the reported metric); small: 48 options "
                          "with N in [200, 600] (seed 321), for profiler captures")
     return ap.parse_args()
@@ -182,6 +183,96 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_crr(args, rank, world, local):
+    """The zero-cost limit at scale: 65536 CRR American puts, N = 2048 (seed 5), one
+    ob_crr_american launch per step; then one put at N = 20000 (latency)."""
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    dev = torch.device("cuda", local)
+    table = W.crr_puts() if rank == 0 else W.crr_puts(seed=5 + 1000 * rank)
+    n = len(table)
+    nodes = int(np.sum(table["N"].astype(np.int64) * (table["N"].astype(np.int64) + 1) // 2))
+    params = ob.to_device(table, dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ob.ob_crr_american(params, n, out, st, stream)
+    torch.cuda.synchronize(dev)
+    assert int((st != 0).sum().item()) == 0
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    sampler.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ob.ob_crr_american(params, n, out, st, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    job_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * nodes * args.steps / job_s
+    # end to end: pinned host records in, prices out, copies inside the timed region
+    pin_in = torch.from_numpy(table.view(np.uint8).reshape(-1).copy()).pin_memory()
+    pin_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        params.copy_(pin_in, non_blocking=True)
+        ob.ob_crr_american(params, n, out, st, stream)
+        pin_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    big = W.appendix_put(20000)
+    bp = ob.to_device(big, dev)
+    bo = torch.empty(1, dtype=torch.float64, device=dev)
+    ob.ob_crr_american(bp, 1, bo, None, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ob.ob_crr_american(bp, 1, bo, None, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    if rank != 0:
+        return
+    avg = job_s / args.steps
+    flops = 3.0 * nodes / avg / 1e12  # one DFMA (2 flops) and one DMUL per node
+    line = {
+        "metric": "CRR node updates/s (k=0, FP64)", "value": value, "unit": "node updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * avg,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "65536 CRR American puts, N=2048, batched-table distributions, k=0 "
+                               "(seed 5)", "node_updates_per_step": nodes,
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "e2e": {"value": world * nodes * args.steps / e2e_s, "unit": "node updates/s",
+                "h2d_bytes_per_step": int(table.nbytes), "d2h_bytes_per_step": int(n * 8)},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "note": "3 FP64 flops per node (DFMA + DMUL) against the nominal FP64 peak"},
+        "put_n20000": {"price": float(bo.item()), "ms": a.elapsed_time(b)},
+        "step_ms": step_ms, "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        sample = table[:: n // 64]
+        t0 = time.perf_counter()
+        oracle.crr_price(sample, nthreads=cores)
+        dt = time.perf_counter() - t0
+        sn = int(np.sum(sample["N"].astype(np.int64) * (sample["N"].astype(np.int64) + 1) // 2))
+        line["cpu_baseline"] = {"value": sn / dt, "unit": "node updates/s", "cores": cores,
+                                "kind": "oracle", "sample": "every %d-th option (%d options), %.2f s"
+                                % (n // 64, len(sample), dt)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -196,6 +287,9 @@ def main():
     ob.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "crr":
+        run_crr(args, rank, world, local)
+        return
 
     if args.workload == "small":
         table = W.random_table(48, 321 + rank, N_lo=200, N_hi=600)
@@ -209,6 +303,13 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB of L2
     stream = torch.cuda.current_stream(dev)
 
+    # the autotuner picks the team width (CTA size, per-CTA breakpoint capacity) on a
+    # sample of the batch, outside the timed region
+    tuned = None
+    if not args.no_autotune:
+        tw, tms = ob.ob_autotune(params, n, min(n, 1024), stream)
+        tuned = {"team_warps": tw, "sample": min(n, 1024),
+                 "sample_ms": {str(k): round(v, 2) for k, v in tms.items()}}
     for _ in range(args.warmup):
         ob.ob_price_ask_bid(params, n, out, st, stream)
     torch.cuda.synchronize(dev)
@@ -302,7 +403,10 @@ def main():
                    if args.workload == "batched" else "small: 48 options, N in [200, 600], seed 321",
                    "options": n, "node_updates_per_step": nodes_per_step,
                    "l2": "flushed (256 MiB write) before every timed step",
-                   "parallelism": "replicas (one batch per GPU)"},
+                   "parallelism": "replicas (one batch per GPU)",
+                   "team_warps": stats["team_warps"], "autotune": tuned,
+                   "launch": "CUDA graph replay" if stats["graph"] == 2 else
+                             ("CUDA graph" if stats["graph"] == 1 else "direct")},
         "options_per_s": world * n * args.steps / job_s,
         "plain": {"value": nodes_per_step / plain_s, "unit": "node updates/s",
                   "options_per_s": n / plain_s, "kernel": "one warp per option, index order"},

@@ -28,7 +28,7 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
-           "ob_price_ask_bid_noalloc", "ob_greeks")
+           "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune")
 
 
 class ObStats(ctypes.Structure):
@@ -36,7 +36,8 @@ class ObStats(ctypes.Structure):
                 ("u_points", ctypes.c_int64), ("w_points", ctypes.c_int64),
                 ("z_points", ctypes.c_int64),
                 ("max_level_points", ctypes.c_int32), ("retried", ctypes.c_int32),
-                ("failed", ctypes.c_int32), ("tiers", ctypes.c_int32)]
+                ("failed", ctypes.c_int32), ("tiers", ctypes.c_int32),
+                ("graph", ctypes.c_int32), ("team_warps", ctypes.c_int32)]
 
 
 class ObError(RuntimeError):
@@ -62,6 +63,11 @@ def load():
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
         lib.ob_get_stats.argtypes = [ctypes.POINTER(ObStats)]
         lib.ob_get_stats.restype = ctypes.c_int
+        lib.ob_configure.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.ob_configure.restype = ctypes.c_int
+        lib.ob_autotune.argtypes = [P, i64, i64, P, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_float)]
+        lib.ob_autotune.restype = ctypes.c_int
         lib.ob_release.argtypes = []
         lib.ob_release.restype = ctypes.c_int
         lib.ob_strerror.argtypes = [ctypes.c_int]
@@ -148,6 +154,26 @@ def ob_get_stats() -> dict:
 
 def ob_release():
     _check(load().ob_release())
+
+
+def ob_configure(team_warps=0, use_graphs=-1):
+    """Team width of the batched form (4, 8, 16; 0 keeps) and CUDA-graph replay (1, 0; -1 keeps)."""
+    _check(load().ob_configure(int(team_warps), int(use_graphs)))
+
+
+def ob_autotune(params, n, sample=0, stream=None):
+    """Time team widths 16, 8, 4 on a sample of the device records and keep the fastest.
+    Returns (team_warps, {16: ms, 8: ms, 4: ms})."""
+    tw = ctypes.c_int32(0)
+    ms = (ctypes.c_float * 3)()
+    _check(load().ob_autotune(_ptr(params), int(n), int(sample), _stream(stream), ctypes.byref(tw), ms))
+    return int(tw.value), {16: float(ms[0]), 8: float(ms[1]), 4: float(ms[2])}
+
+
+def autotune(table, sample=0):
+    """ob_autotune on a workloads table."""
+    dev = to_device(table)
+    return ob_autotune(dev, int(np.asarray(table).shape[0]), sample)
 
 
 # ---------------------------------------------------------------- conveniences

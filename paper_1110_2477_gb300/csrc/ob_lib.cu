@@ -423,6 +423,15 @@ __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opt
   }
 }
 
+// Every stride-th option, for the autotuner's sample.
+__global__ void k_gather(const obk::Opt* __restrict__ src, int n, int stride, int m, obk::Opt* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    const long long j = (long long)i * stride;
+    dst[i] = src[j < n ? j : n - 1];
+  }
+}
+
 // ------------------------------------------------------------------ host side
 thread_local char g_cuda_err[256] = "";
 
@@ -430,6 +439,18 @@ int cuda_fail(cudaError_t e) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", cudaGetErrorString(e));
   return OB_ERR_CUDA;
 }
+
+// One instantiated CUDA graph of the batched launch sequence, keyed by the call's
+// pointers, size and team width (a replay reads the buffers' current contents).
+struct GraphEntry {
+  const void* params = nullptr;
+  void* out = nullptr;
+  void* status = nullptr;
+  int n = 0;
+  int team_warps = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kGraphCache = 4;
 
 struct DevPool {
   bool init = false;
@@ -452,9 +473,21 @@ struct DevPool {
   int* hstatus = nullptr;
   size_t hcap = 0;
   int last_tiers = 0;
+  // CUDA graphs of the batched form
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  GraphEntry graphs[kGraphCache];
+  int graph_next = 0;
+  int last_graph = 0;  // 0 direct launches, 1 captured now, 2 replayed
+  // autotuner sample buffers
+  obk::Opt* tune_params = nullptr;
+  double* tune_out = nullptr;
+  int* tune_status = nullptr;
+  int tune_cap = 0;
 };
 
 std::mutex g_mu;
+std::mutex g_graph_mu;
 DevPool g_pool[64];
 
 size_t env_size(const char* name, size_t dflt) {
@@ -481,6 +514,7 @@ int pool_get(DevPool** out, size_t need_list) {
       const int v = atoi(tw);
       if (v == 4 || v == 8 || v == 16) P.team_warps = v;
     }
+    if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
     const size_t workers = (size_t)P.sms * P.warps_per_sm;
     P.arena_bytes = workers * P.arena_per_warp;
     const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
@@ -519,6 +553,11 @@ int pool_get(DevPool** out, size_t need_list) {
   return OB_OK;
 }
 
+int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
+                    cudaStream_t s);
+int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
+                 cudaStream_t s);
+
 int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* status, void* stream,
               bool plain) {
   if (n64 < 0 || n64 > (1 << 30)) return OB_ERR_ARG;
@@ -530,10 +569,9 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
   const obk::Opt* opts = (const obk::Opt*)params;
   if (plain) {
+    if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
     const int max_workers = P->sms * P->warps_per_sm;
     const int workers = n < max_workers ? n : max_workers;
     const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
@@ -541,8 +579,24 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
     k_tc_plain<<<blocks, kBlock, 0, s>>>(opts, n, out, status, P->arena, wbytes, workers, P->stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     P->last_tiers = 1;
+    P->last_graph = 0;
     return OB_OK;
   }
+  if (!P->use_graphs) {
+    P->last_graph = 0;
+    return enqueue_batched(P, opts, n, out, status, s);
+  }
+  return launch_graph(P, opts, n, out, status, s);
+}
+
+// The batched launch sequence: reset the queue words and counters, order the options
+// by predicted cost, run the persistent kernel, then the two follow-up tiers for
+// options that outgrew their scratch.  No host synchronisation, so it can be captured.
+int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
+                    cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
   const int nctas = P->sms * (16 / P->team_warps);
   const int* order = nullptr;
   if (n <= kSortMax) {
@@ -578,6 +632,61 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   P->last_tiers = kTiers + (order ? 1 : 0);
   return OB_OK;
+}
+
+// Replay the cached graph of this call's key, or capture the sequence on the pool's
+// capture stream, instantiate it (evicting the oldest entry) and launch it on s.
+int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
+                 cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  cudaError_t e;
+  for (GraphEntry& g : P->graphs) {
+    if (g.exec && g.params == opts && g.n == n && g.out == out && g.status == status &&
+        g.team_warps == P->team_warps) {
+      if ((e = cudaGraphLaunch(g.exec, s)) != cudaSuccess) return cuda_fail(e);
+      P->last_graph = 2;
+      P->last_tiers = kTiers + (n <= kSortMax ? 1 : 0);
+      return OB_OK;
+    }
+  }
+  if (!P->cap_stream &&
+      (e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(e);
+  const int rc = enqueue_batched(P, opts, n, out, status, P->cap_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(P->cap_stream, &graph);
+  if (rc || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc ? rc : cuda_fail(e);
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  GraphEntry& g = P->graphs[P->graph_next];
+  P->graph_next = (P->graph_next + 1) % kGraphCache;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = exec;
+  g.params = opts;
+  g.n = n;
+  g.out = out;
+  g.status = status;
+  g.team_warps = P->team_warps;
+  if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(e);
+  P->last_graph = 1;
+  return OB_OK;
+}
+
+void drop_graphs(DevPool* P) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (GraphEntry& g : P->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = GraphEntry();
+  }
+  P->graph_next = 0;
 }
 
 // ------------------------------------------------------------------ fixed-scratch form
@@ -747,7 +856,80 @@ int ob_get_stats(ob_stats_t* host_out) {
   host_out->retried = d.retried;
   host_out->failed = d.failed;
   host_out->tiers = P->last_tiers;
+  host_out->graph = P->last_graph;
+  host_out->team_warps = P->team_warps;
   return OB_OK;
+}
+
+int ob_configure(int32_t team_warps, int32_t use_graphs) {
+  if (team_warps != 0 && team_warps != 4 && team_warps != 8 && team_warps != 16) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, 1);
+  if (rc) return rc;
+  if (team_warps) P->team_warps = team_warps;
+  if (use_graphs >= 0) P->use_graphs = use_graphs != 0;
+  drop_graphs(P);
+  return OB_OK;
+}
+
+int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, void* stream,
+                int32_t* team_warps_out, float* ms_out) {
+  if (n_options <= 0 || n_options > (1 << 30) || !params) return OB_ERR_ARG;
+  const int n = (int)n_options;
+  int m = (int)(sample > 0 && sample < n_options ? sample : n_options);
+  const int stride = n / m;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, (size_t)m);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (m > P->tune_cap) {
+    cudaFree(P->tune_params);
+    cudaFree(P->tune_out);
+    cudaFree(P->tune_status);
+    P->tune_params = nullptr; P->tune_out = nullptr; P->tune_status = nullptr; P->tune_cap = 0;
+    if (cudaMalloc(&P->tune_params, sizeof(obk::Opt) * m) != cudaSuccess ||
+        cudaMalloc(&P->tune_out, sizeof(double) * 2 * m) != cudaSuccess ||
+        cudaMalloc(&P->tune_status, sizeof(int) * m) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+    P->tune_cap = m;
+  }
+  k_gather<<<(m + 255) / 256, 256, 0, s>>>((const obk::Opt*)params, n, stride, m, P->tune_params);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(e);
+  }
+  const int cands[3] = {16, 8, 4};
+  const int keep = P->team_warps;
+  int best = keep;
+  float best_ms = 0.0f;
+  for (int c = 0; c < 3 && rc == OB_OK; ++c) {
+    P->team_warps = cands[c];
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && rc == OB_OK; ++rep) {  // one warm-up run, one timed run
+      if ((e = cudaEventRecord(a, s)) != cudaSuccess) { rc = cuda_fail(e); break; }
+      rc = enqueue_batched(P, P->tune_params, m, P->tune_out, P->tune_status, s);
+      if (rc) break;
+      if ((e = cudaEventRecord(b, s)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) {
+        rc = cuda_fail(e);
+        break;
+      }
+    }
+    if (rc) break;
+    if (ms_out) ms_out[c] = ms;
+    if (c == 0 || ms < best_ms) { best_ms = ms; best = cands[c]; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  P->team_warps = rc ? keep : best;
+  drop_graphs(P);
+  if (team_warps_out) *team_warps_out = P->team_warps;
+  return rc;
 }
 
 int ob_release(void) {
@@ -758,6 +940,11 @@ int ob_release(void) {
   DevPool& P = g_pool[dev];
   if (!P.init) return OB_OK;
   cudaDeviceSynchronize();
+  drop_graphs(&P);
+  if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
+  cudaFree(P.tune_params);
+  cudaFree(P.tune_out);
+  cudaFree(P.tune_status);
   cudaFree(P.arena);
   cudaFree(P.ctl);
   cudaFree(P.order);

@@ -46,3 +46,16 @@ def test_option_record_layout_matches_header():
     assert W.OPTION_DTYPE.itemsize == 64
     assert [W.OPTION_DTYPE.fields[f][1] for f in ("S0", "K", "K2", "sigma", "R", "T", "k", "N", "payoff")] == \
         [0, 8, 16, 24, 32, 40, 48, 56, 60]
+
+
+def test_stats_record_matches_header():
+    """The binding's ob_stats_t mirrors the header's fields, in order."""
+    import re
+    from paper_1110_2477_gb300 import ObStats
+    text = open(os.path.join(ROOT, "include", "ob.h")).read()
+    body = text[text.index("typedef struct {", text.index("Counters of the most recent")):]
+    body = body[:body.index("} ob_stats_t;")]
+    fields = re.findall(r"^\s*(int64_t|int32_t)\s+(\w+);", body, re.M)
+    assert [n for _, n in fields] == [n for n, _ in ObStats._fields_]
+    sizes = {"int64_t": 8, "int32_t": 4}
+    assert ctypes.sizeof(ObStats) == sum(sizes[t] for t, _ in fields)

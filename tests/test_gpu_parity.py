@@ -263,3 +263,68 @@ def test_capacity_retry_and_exhaustion():
     ok = st == 0
     assert ok.sum() >= 1
     np.testing.assert_array_equal(np.array(tiny["out"])[ok], np.array(base["out"])[ok])
+
+
+# ---------------------------------------------------------------- graphs, team widths, autotuner
+def test_team_widths_give_bitwise_equal_prices():
+    ob = _ob()
+    t = W.random_table(96, 4711, N_lo=20, N_hi=400)
+    try:
+        res = []
+        for tw in (16, 8, 4):
+            ob.ob_configure(team_warps=tw, use_graphs=0)
+            out, st = _gpu(t)
+            assert ob.ob_get_stats()["team_warps"] == tw
+            res.append((out, st))
+        for out, st in res[1:]:
+            assert np.array_equal(st, res[0][1])
+            assert np.array_equal(out.view(np.int64), res[0][0].view(np.int64))
+    finally:
+        ob.ob_configure(team_warps=16, use_graphs=1)
+
+
+def test_graph_capture_then_replay_reads_current_inputs():
+    """The second call with the same buffers replays the captured graph; it must price
+    the records the buffer holds now, and match direct launches bit for bit."""
+    import torch
+    ob = _ob()
+    t1 = W.random_table(64, 808, N_lo=10, N_hi=300)
+    t2 = W.random_table(64, 909, N_lo=10, N_hi=300)
+    dev = ob.to_device(t1)
+    out = torch.empty((64, 2), dtype=torch.float64, device="cuda")
+    st = torch.empty(64, dtype=torch.int32, device="cuda")
+    try:
+        ob.ob_configure(use_graphs=1)
+        ob.ob_price_ask_bid(dev, 64, out, st)
+        torch.cuda.synchronize()
+        assert ob.ob_get_stats()["graph"] == 1
+        r1 = out.cpu().numpy().copy()
+        dev.copy_(ob.to_device(t2))
+        ob.ob_price_ask_bid(dev, 64, out, st)
+        torch.cuda.synchronize()
+        s = ob.ob_get_stats()
+        assert s["graph"] == 2 and s["options"] == 64
+        r2 = out.cpu().numpy().copy()
+        ob.ob_configure(use_graphs=0)
+        d1, _ = _gpu(t1)
+        d2, _ = _gpu(t2)
+        assert ob.ob_get_stats()["graph"] == 0
+        assert np.array_equal(r1.view(np.int64), d1.view(np.int64))
+        assert np.array_equal(r2.view(np.int64), d2.view(np.int64))
+    finally:
+        ob.ob_configure(team_warps=16, use_graphs=1)
+
+
+def test_autotune_keeps_a_valid_width():
+    ob = _ob()
+    t = W.random_table(200, 2024, N_lo=50, N_hi=500)
+    before, _ = _gpu(t)
+    try:
+        tw, ms = ob.autotune(t, sample=100)
+        assert tw in (4, 8, 16) and all(v > 0 for v in ms.values())
+        assert ms[tw] == min(ms.values())
+        after, _ = _gpu(t)
+        assert ob.ob_get_stats()["team_warps"] == tw
+        assert np.array_equal(before.view(np.int64), after.view(np.int64))
+    finally:
+        ob.ob_configure(team_warps=16, use_graphs=1)
