@@ -133,6 +133,19 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
 int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad,
               int32_t* status, void* stream);
 
+/* Whole-GPU form, for large single options (N in the thousands): the options are
+ * priced one after another, each on every SM at once.  One CTA per SM; at each
+ * level the CTAs split the nodes by their merged successor breakpoints (whole
+ * nodes, G equal shares), run the same element-wise passes as ob_price_ask_bid
+ * into private scratch, then place their breakpoints in the shared level; two
+ * grid barriers per level.  One cooperative launch per call.  Results are bitwise
+ * equal to ob_price_ask_bid.  Arguments, ownership and statuses as
+ * ob_price_ask_bid; a barrier wait longer than 10 s gives OB_ERR_TIMEOUT for the
+ * option in progress and every later option of the call; a level that outgrows
+ * the shared scratch (1/8 of the pool) gives OB_ERR_CAPACITY. */
+int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* out,
+                          int32_t* status, void* stream);
+
 /* Plain CRR American price without transaction costs (the Appendix): the
  * scalar recursion over N levels, no extra level; k is ignored.
  *   out  DEVICE pointer, n_options doubles.  Other arguments as above. */

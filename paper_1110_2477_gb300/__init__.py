@@ -28,7 +28,8 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
-           "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune")
+           "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune",
+           "ob_price_ask_bid_wide")
 
 
 class ObStats(ctypes.Structure):
@@ -53,7 +54,7 @@ def load():
         lib = ctypes.CDLL(LIB_PATH)
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         for name in ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american",
-                     "ob_price_ask_bid_noalloc", "ob_greeks"):
+                     "ob_price_ask_bid_noalloc", "ob_greeks", "ob_price_ask_bid_wide"):
             f = getattr(lib, name)
             f.argtypes = [P, i64, P, P, P]
             f.restype = ctypes.c_int
@@ -119,6 +120,12 @@ def ob_price_ask_bid_plain(params, n, out, status=None, stream=None):
                                          _stream(stream)))
 
 
+def ob_price_ask_bid_wide(params, n, out, status=None, stream=None):
+    """Whole-GPU form: each option in turn on every SM (large single options)."""
+    _check(load().ob_price_ask_bid_wide(_ptr(params), int(n), _ptr(out), _ptr(status),
+                                        _stream(stream)))
+
+
 def ob_crr_american(params, n, out, status=None, stream=None):
     _check(load().ob_crr_american(_ptr(params), int(n), _ptr(out), _ptr(status), _stream(stream)))
 
@@ -177,14 +184,16 @@ def autotune(table, sample=0):
 
 
 # ---------------------------------------------------------------- conveniences
-def price(table, plain=False, stream=None):
-    """ask/bid of a workloads table on the current CUDA device: (out[n,2], status[n]) tensors."""
+def price(table, plain=False, stream=None, wide=False):
+    """ask/bid of a workloads table on the current CUDA device: (out[n,2], status[n]) tensors.
+    plain: one warp per option; wide: each option on the whole GPU; else the batched form."""
     import torch
     n = int(np.asarray(table).shape[0])
     dev = to_device(table)
     out = torch.empty((n, 2), dtype=torch.float64, device=dev.device)
     st = torch.empty(n, dtype=torch.int32, device=dev.device)
-    (ob_price_ask_bid_plain if plain else ob_price_ask_bid)(dev, n, out, st, stream)
+    f = ob_price_ask_bid_wide if wide else (ob_price_ask_bid_plain if plain else ob_price_ask_bid)
+    f(dev, n, out, st, stream)
     return out, st
 
 

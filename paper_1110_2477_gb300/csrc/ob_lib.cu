@@ -35,6 +35,8 @@ constexpr double kHeavyFactor = 0.0; // heavy: predicted cost > factor x (total 
 enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
        C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
 
+constexpr int ST_TIMEOUT = -4;  // OB_ERR_TIMEOUT: a bounded device wait ran out
+
 struct DevStats {
   unsigned long long options, node_updates, upts, wpts, zpts;
   int max_level, retried, failed, tiers;
@@ -237,6 +239,131 @@ __global__ void __launch_bounds__(kTeamBlock, 2) k_tc_retry(
     price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
     if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, ovf_count, ovf_list, !last, ds);
     bt.sync();
+  }
+}
+
+// ------------------------------------------------------------------ whole-GPU form
+// Each option in turn on every SM: the CTAs split each level's nodes (TcGroup) and
+// meet at two grid barriers per level.  Launched cooperatively, so all CTAs are
+// resident; every wait is bounded.
+constexpr int kGroupMax = 1024;                                    // CTAs of the grid at most
+constexpr unsigned long long kGroupWaitNs = 10000000000ULL;        // 10 s per barrier wait
+constexpr int kGroupNW = 16;                                       // warps per CTA
+
+struct GroupState {
+  unsigned int count;  // arrivals at the current barrier
+  unsigned int gen;    // barriers completed
+  int err;             // a wait ran out: every later barrier fails at once
+  int pad;
+  int cnt[2][kGroupMax];  // points of each CTA's share of a level (-1: overflow)
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier of all CTAs of the grid.  Thread 0 publishes with a fence and an atomic
+// arrival, the last arrival releases the others by bumping the generation; a wait
+// longer than kGroupWaitNs (or 2^30 polls) sets err.  Returns false once err is set.
+__device__ bool grid_barrier(GroupState* gs, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = *((volatile int*)&gs->err) == 0;
+    if (ok) {
+      const unsigned want = gen + 1u;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&gs->count, 1u) + 1u;
+      if (arrived == gridDim.x) {
+        atomicExch(&gs->count, 0u);
+        __threadfence();
+        atomicExch(&gs->gen, want);
+      } else {
+        const unsigned long long t0 = global_ns();
+        for (unsigned it = 0;; ++it) {
+          if (*((volatile unsigned*)&gs->gen) == want) break;
+          if (*((volatile int*)&gs->err) != 0) { ok = 0; break; }
+          if (it > (1u << 30) || global_ns() - t0 > kGroupWaitNs) {
+            atomicExch(&gs->err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __threadfence();
+      gen = want;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
+    const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
+    size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds) {
+  __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
+  __shared__ int s_cnt[kGroupMax];
+  obk::BlockTeam<kGroupNW> bt{tbuf};
+  const int G = gridDim.x, c = blockIdx.x;
+  char* mine = arena + shared_bytes + (size_t)c * cta_bytes;
+  unsigned gen = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const obk::Opt o = opts[oi];
+    int rc = check_option(o, true);
+    double ask = dnan(), bid = dnan();
+    obk::Stats st;
+    st.upts = st.wpts = st.zpts = 0;
+    st.zmax_level = st.zmax_node = 0;
+    obk::GroupLay S;
+    obk::Lay Lp;
+    if (rc == obk::ST_OK && (!obk::carve_group_shared(arena, shared_bytes, o.N, 2 * (o.N + 2), S) ||
+                             !obk::carve(mine, cta_bytes, o.N, 16, Lp)))
+      rc = obk::ST_CAPACITY;
+    if (rc == obk::ST_OK) {
+      obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
+      rc = g.begin();
+      if (rc == obk::ST_OK && !grid_barrier(gs, gen)) rc = ST_TIMEOUT;
+      for (int t = o.N; t >= 0 && rc == obk::ST_OK; --t) {
+        const bool ok = g.compute(t);
+        if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? g.ztot : -1;
+        if (!grid_barrier(gs, gen)) { rc = ST_TIMEOUT; break; }
+        int bad = 0;
+        for (int k = threadIdx.x; k < G; k += blockDim.x) {
+          s_cnt[k] = __ldcg(&gs->cnt[t & 1][k]);
+          if (s_cnt[k] < 0) bad = 1;
+        }
+        if (__syncthreads_or(bad)) { rc = obk::ST_CAPACITY; break; }
+        if (!g.publish(t, s_cnt)) { rc = obk::ST_CAPACITY; break; }
+        if (!grid_barrier(gs, gen)) { rc = ST_TIMEOUT; break; }
+      }
+      if (rc == obk::ST_OK && c == 0) g.root(ask, bid);
+      st = g.R.st;
+    }
+    if (threadIdx.x == 0) {
+      if (rc == obk::ST_OK) {
+        atomicAdd(&ds->upts, (unsigned long long)st.upts);
+        atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
+        atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
+      }
+      if (c == 0) {
+        out[2 * oi] = rc ? dnan() : ask;
+        out[2 * oi + 1] = rc ? dnan() : bid;
+        if (status) status[oi] = rc;
+        atomicAdd(&ds->options, 1ULL);
+        if (rc == obk::ST_OK) {
+          const unsigned long long N = (unsigned long long)o.N;
+          atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
+          atomicMax(&ds->max_level, st.zmax_level);
+        } else {
+          atomicAdd(&ds->failed, 1);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -479,6 +606,8 @@ struct DevPool {
   GraphEntry graphs[kGraphCache];
   int graph_next = 0;
   int last_graph = 0;  // 0 direct launches, 1 captured now, 2 replayed
+  GroupState* gstate = nullptr;  // whole-GPU form
+  int group_ctas = 0;
   // autotuner sample buffers
   obk::Opt* tune_params = nullptr;
   double* tune_out = nullptr;
@@ -739,6 +868,54 @@ int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double*
   return launch_tc(params, n_options, out, status, stream, true);
 }
 
+int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* out,
+                          int32_t* status, void* stream) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int rc = pool_get(&P, 1);
+  if (rc) return rc;
+  cudaError_t e;
+  if (!P->gstate) {
+    int per_sm = 0, coop = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess)
+      return cuda_fail(e);
+    if (!coop) return OB_ERR_CUDA;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_group, 32 * kGroupNW, 0)) !=
+        cudaSuccess)
+      return cuda_fail(e);
+    if (per_sm < 1) return OB_ERR_CUDA;
+    int G = P->sms;  // one CTA per SM
+    if (G > kGroupMax) G = kGroupMax;
+    if (cudaMalloc(&P->gstate, sizeof(GroupState)) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+    P->group_ctas = G;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((e = cudaMemsetAsync(P->gstate, 0, sizeof(GroupState), s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
+  const int G = P->group_ctas;
+  const size_t shared_bytes = (P->arena_bytes / 8) & ~(size_t)255;
+  const size_t cta_bytes = ((P->arena_bytes - shared_bytes) / (size_t)G) & ~(size_t)255;
+  const obk::Opt* opts = (const obk::Opt*)params;
+  int n = (int)n_options;
+  char* arena = P->arena;
+  GroupState* gs = P->gstate;
+  DevStats* ds = P->stats;
+  void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
+                  (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds};
+  if ((e = cudaLaunchCooperativeKernel((const void*)k_tc_group, dim3(G), dim3(32 * kGroupNW), args, 0,
+                                       s)) != cudaSuccess)
+    return cuda_fail(e);
+  P->last_tiers = 1;
+  P->last_graph = 0;
+  return OB_OK;
+}
+
 int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                     void* stream) {
   if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
@@ -942,6 +1119,7 @@ int ob_release(void) {
   cudaDeviceSynchronize();
   drop_graphs(&P);
   if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
+  cudaFree(P.gstate);
   cudaFree(P.tune_params);
   cudaFree(P.tune_out);
   cudaFree(P.tune_status);

@@ -671,8 +671,17 @@ struct TcRun {
     return (p ? UB1 : 0) + (op[j] - op[0]) + (op[j + 1] - op[1]);
   }
 
-  // pass 1: w = max(z_up, z_down) for every node of level t; returns false on overflow
-  OB_HD bool pass1(int t, int& wtot, int& utot) {
+  // union start of node n (seller nodes 0..t, then buyer nodes) of level t; n in [0, 2(t+1)]
+  OB_HD int ustart_node(int t, int n) const {
+    const int W1 = t + 2, W0 = t + 1;
+    const int UB1 = ustart(inOff, W1, 0, 0, W0);
+    const int p = n >= W0 ? 1 : 0;
+    return ustart(inOff, W1, UB1, p, n - p * W0);
+  }
+
+  // pass 1: w = max(z_up, z_down) for the nodes n0 <= n < n1 of level t (n1 < 0: all
+  // nodes); w of node n0 starts at position 0.  Returns false on overflow.
+  OB_HD bool pass1(int t, int& wtot, int& utot, int n0 = 0, int n1 = -1) {
     const int lane = tm.lane();
     const int b1 = (t + 1) & 1;
     const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
@@ -680,15 +689,17 @@ struct TcRun {
     const double *Y1 = inY, *F1 = inF, *S1 = inS;
     const double* nt1 = L.nt[b1];
     const int UB1 = ustart(o1, W1, 0, 0, W0);
-    const int Utot = ustart(o1, W1, UB1, 1, W0);
-    utot = Utot;
-    int ncur = 0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
+    if (n1 < 0) n1 = nNodes;
+    const int u0 = ustart_node(t, n0);
+    const int Utot = ustart_node(t, n1);  // end of the range
+    utot = Utot - u0;
+    int ncur = n0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
     bool ovf = false;
-    for (int base = 0; base < Utot; base += Team::W) {
+    for (int base = u0; base < Utot; base += Team::W) {
       const int q = base + lane;
       const int nl = ncur + lane;
       int nend = 0x7fffffff;
-      if (nl < nNodes) {
+      if (nl < n1) {
         const int p = nl >= W0 ? 1 : 0;
         nend = ustart(o1, W1, UB1, p, nl - p * W0 + 1);
       }
@@ -735,7 +746,7 @@ struct TcRun {
       wpos += total;
       ncur = ncur_next;
     }
-    if (lane == 0) L.offw[nNodes] = wpos;
+    if (lane == 0) L.offw[n1] = wpos;
     wtot = wpos;
     return !(tm.any(ovf) || wpos > L.capW);
   }
@@ -946,6 +957,166 @@ struct TcRun {
     ask = root_value(0) / lam0;
     bid = -root_value(1) / lam0;
     return ST_OK;
+  }
+};
+
+// ------------------------------------------------------------------ one option, G teams
+// The level step split over G teams (CTAs) that share the level functions.  Team c
+// of G takes the nodes whose merged successor points fall in the c-th G-quantile of
+// the level's union (whole nodes), runs the three passes into its private arrays,
+// and, once every team's count is known, copies its points to their place in the
+// shared level and rewrites the node offsets.  The caller puts a barrier of all G
+// teams between compute() and publish() and after publish().  Every node is
+// computed by the same element-wise code as in the one-team run, so the results
+// are the same bit for bit.
+struct GroupLay {
+  double *zY[2], *zF[2], *zS[2];
+  int* off[2];
+  int capZ;
+};
+
+// Bytes of the shared level arrays for N steps and cap points per bank.
+OB_HD size_t group_shared_bytes(int N, size_t cap) {
+  return 2 * al256(sizeof(int) * (2 * ((size_t)N + 2) + 1)) + 6 * al256(sizeof(double) * cap);
+}
+
+// Carve the shared level arrays from `bytes` at base; false if fewer than min_cap points fit.
+OB_HD bool carve_group_shared(char* base, size_t bytes, int N, int min_cap, GroupLay& S) {
+  const size_t fixed = 2 * al256(sizeof(int) * (2 * ((size_t)N + 2) + 1)) + 6 * 256;
+  if (bytes < fixed) return false;
+  size_t cap = (bytes - fixed) / (6 * sizeof(double));
+  if (cap > 0x3fffffff) cap = 0x3fffffff;
+  if ((long long)cap < (long long)min_cap) return false;
+  char* p = base;
+  auto take = [&](size_t sz) { char* r = p; p += al256(sz); return r; };
+  for (int b = 0; b < 2; ++b) S.off[b] = (int*)take(sizeof(int) * (2 * ((size_t)N + 2) + 1));
+  for (int b = 0; b < 2; ++b) {
+    S.zY[b] = (double*)take(sizeof(double) * cap);
+    S.zF[b] = (double*)take(sizeof(double) * cap);
+    S.zS[b] = (double*)take(sizeof(double) * cap);
+  }
+  S.capZ = (int)cap;
+  return (size_t)(p - base) <= bytes;
+}
+
+template <class Team>
+struct TcGroup {
+  Lay L;           // private arrays; the level banks and offsets point at the shared ones
+  TcRun<Team> R;
+  int G, c;
+  double *zpY, *zpF, *zpS;  // private output of the level (one of the carved banks)
+  int* poff;                // private node offsets of the level
+  int capP;
+  int n0, n1, ztot;         // this team's nodes and point count of the current level
+
+  OB_HD static Lay merge(const Lay& Lp, const GroupLay& S) {
+    Lay L = Lp;
+    for (int b = 0; b < 2; ++b) {
+      L.zY[b] = S.zY[b]; L.zF[b] = S.zF[b]; L.zS[b] = S.zS[b]; L.off[b] = S.off[b];
+    }
+    L.capZ = S.capZ;
+    return L;
+  }
+
+  OB_HD TcGroup(const Team& tm, const Opt& o, const Lay& Lp, const GroupLay& S, int G_, int c_)
+      : L(merge(Lp, S)), R(tm, o, L), G(G_), c(c_), zpY(Lp.zY[0]), zpF(Lp.zF[0]), zpS(Lp.zS[0]),
+        poff(Lp.off[0]), capP(Lp.capZ), n0(0), n1(0), ztot(0) {}
+
+  // tree constants, the leaf level (written by team 0); a status every team agrees on
+  OB_HD int begin() {
+    const Team& tm = R.tm;
+    const Opt& o = R.o;
+    const int N = R.N, lane = tm.lane();
+    const double dt = o.T / N;
+    const double u = exp(o.sigma * sqrt(dt));
+    const double r = exp(o.R * dt);
+    const double d = 1.0 / u;
+    if (!(d < r && r < u)) return ST_ARBITRAGE;
+    if (2 * (N + 2) > L.capZ) return ST_CAPACITY;
+    for (int e = lane; e < 2 * N + 3; e += Team::W) L.Stab[e] = o.S0 * pow(u, (double)(e - (N + 1)));
+    for (int t = lane; t <= N + 1; t += Team::W) L.lam[t] = pow(r, (double)(N + 1 - t));
+    tm.sync();
+    const int b = (N + 1) & 1, W = N + 2;
+    R.node_table(N + 1);
+    tm.sync();
+    if (c == 0) {
+      for (int n = lane; n < 2 * W; n += Team::W) {
+        const int j = n >= W ? n - W : n;
+        L.off[b][n] = n;
+        L.zY[b][n] = 0.0;
+        L.zF[b][n] = 0.0;
+        L.zS[b][n] = -L.nt[b][4 * j + 1];
+      }
+      if (lane == 0) L.off[b][2 * W] = 2 * W;
+    }
+    tm.sync();
+    return ST_OK;
+  }
+
+  // first node whose union start is >= target (nodes 0..nNodes)
+  OB_HD int node_at(int t, long long target) const {
+    int lo = 0, hi = 2 * (t + 1);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)R.ustart_node(t, mid) >= target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  }
+
+  // this team's share of level t, into the private arrays; false on overflow
+  OB_HD bool compute(int t) {
+    const Team& tm = R.tm;
+    R.use_banks(t);
+    R.node_table(t);
+    tm.sync();
+    const int nNodes = 2 * (t + 1);
+    const long long Utot = R.ustart_node(t, nNodes);
+    n0 = (c == 0) ? 0 : node_at(t, (Utot * c + G - 1) / G);
+    n1 = (c == G - 1) ? nNodes : node_at(t, (Utot * (c + 1) + G - 1) / G);
+    R.outY = zpY; R.outF = zpF; R.outS = zpS; R.outOff = poff; R.outCap = capP;
+    int wtot = 0, utot = 0;
+    ztot = 0;
+    if (!R.pass1(t, wtot, utot, n0, n1)) return false;
+    R.st.upts += utot;
+    R.pass2(t, wtot);
+    if (!R.pass3(t, wtot, ztot)) return false;
+    R.st.wpts += wtot;
+    R.st.zpts += ztot;
+    return true;
+  }
+
+  // place this team's points of level t in the shared bank; cnt[g] = points of team g.
+  // False when the level outgrows the shared bank (every team sees the same).
+  OB_HD bool publish(int t, const int* cnt) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    long long pre = 0, total = 0;
+    for (int g = 0; g < G; ++g) {
+      if (g < c) pre += cnt[g];
+      total += cnt[g];
+    }
+    if (total > L.capZ) return false;
+    const int bt = t & 1;
+    double *Y = L.zY[bt], *F = L.zF[bt], *S = L.zS[bt];
+    int* off = L.off[bt];
+    const int p = (int)pre;
+    for (int i = lane; i < ztot; i += Team::W) {
+      Y[p + i] = zpY[i];
+      F[p + i] = zpF[i];
+      S[p + i] = zpS[i];
+    }
+    for (int n = n0 + lane; n < n1; n += Team::W) off[n] = p + poff[n];
+    if (c == 0 && lane == 0) off[2 * (t + 1)] = (int)total;
+    if ((int)total > R.st.zmax_level) R.st.zmax_level = (int)total;
+    tm.sync();
+    return true;
+  }
+
+  // ask and bid from the shared level 0 (after the last publish and barrier)
+  OB_HD void root(double& ask, double& bid) const {
+    const double lam0 = L.lam[0];
+    ask = R.root_value(0) / lam0;
+    bid = -R.root_value(1) / lam0;
   }
 };
 

@@ -328,3 +328,39 @@ def test_autotune_keeps_a_valid_width():
         assert np.array_equal(before.view(np.int64), after.view(np.int64))
     finally:
         ob.ob_configure(team_warps=16, use_graphs=1)
+
+
+# ---------------------------------------------------------------- whole-GPU form (large single options)
+def _wide(table):
+    import torch
+    out, st = _ob().price(table, wide=True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), st.cpu().numpy()
+
+
+def test_wide_equals_batched_bitwise_with_edge_cases():
+    """Every SM on one option at a time: same bits and statuses as the batched form,
+    including N = 1, 2 (most CTAs own no node), invalid records and an arbitrage tree."""
+    t = W.concat(W.random_table(12, 5150, N_lo=1, N_hi=300), W.make(k=0.01, N=1), W.make(k=0.01, N=2),
+                 W.make(N=0), W.make(R=5.0, N=2, T=1.0),
+                 W.make(S0=100, K=100, sigma=0.1, T=0.1, k=0.02, N=200, payoff=W.CALL))
+    a, sa = _gpu(t)
+    b, sb = _wide(t)
+    assert np.array_equal(sa, sb)
+    ok = sa == 0
+    assert np.array_equal(a[ok].view(np.int64), b[ok].view(np.int64))
+    assert np.all(np.isnan(b[~ok]))
+
+
+def test_wide_paper_scale_matches_oracle_and_batched():
+    t = W.paper_scale(Ns=(1500,), ks=(0.005,))
+    b, sb = _wide(t)
+    assert np.all(sb == 0)
+    s = _ob().ob_get_stats()
+    a, sa = _gpu(t)
+    s2 = _ob().ob_get_stats()
+    assert np.array_equal(a.view(np.int64), b.view(np.int64))
+    for k in ("node_updates", "u_points", "w_points", "z_points", "max_level_points"):
+        assert s[k] == s2[k], k
+    ref, rst = oracle.price_ask_bid(t, nthreads=2)
+    _assert_parity(t, b, sb, ref, rst)
