@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-greeks", action="store_true", help="skip the Greeks-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default team width")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr", "paper"],
                     help="batched: the 4096-option batch (the reported metric); small: 48 options "
                          "with N in [200, 600] (seed 321), for profiler captures")
     return ap.parse_args()
@@ -273,6 +273,84 @@ def run_crr(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_paper(args, rank, world, local):
+    """Paper-scale single options: put (K=100) and cash-settled bull spread (95/105),
+    S0=100, sigma=0.2, R=0.1, T=0.25, k in {0.25%, 0.5%, 1%}, N in {1500, 3000, 6000};
+    one option per launch on the whole GPU (ob_price_ask_bid_wide).  A step prices
+    the 18 options in turn; each option is also timed once on one CTA."""
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    dev = torch.device("cuda", local)
+    table = W.paper_scale()
+    n = len(table)
+    nodes = W.node_updates(table)
+    params = [ob.to_device(table[i:i + 1], dev) for i in range(n)]
+    out = torch.empty((1, 2), dtype=torch.float64, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        for i in range(n):
+            ob.ob_price_ask_bid_wide(params[i], 1, out, st, stream)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+          for _ in range(args.steps)]
+    prices = np.zeros((n, 2))
+    barrier(world)
+    sampler.start()
+    for k in range(args.steps):
+        for i in range(n):
+            ev[k][i][0].record(stream)
+            ob.ob_price_ask_bid_wide(params[i], 1, out, st, stream)
+            ev[k][i][1].record(stream)
+            if k == 0:
+                prices[i] = out[0].cpu().numpy()
+                assert int(st.item()) == 0
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = np.array([[a.elapsed_time(b) for a, b in row] for row in ev])
+    job_s = max_over_ranks(ms.sum() / 1e3, world)
+    value = world * float(nodes.sum()) * args.steps / job_s
+    one_cta = []
+    for i in range(n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ob.ob_price_ask_bid(params[i], 1, out, st, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        one_cta.append(a.elapsed_time(b))
+    if rank != 0:
+        return
+    med = np.median(ms, axis=0)
+    rows = [{"N": int(table["N"][i]), "payoff": ["put", "call", "spread"][int(table["payoff"][i])],
+             "k": float(table["k"][i]), "ask": float(prices[i, 0]), "bid": float(prices[i, 1]),
+             "wide_ms": round(float(med[i]), 2), "one_cta_ms": round(one_cta[i], 2)} for i in range(n)]
+    line = {
+        "metric": "paper-scale single options, one per launch on the whole GPU: node updates/s (ask+bid)",
+        "value": value, "unit": "node updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * job_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "put K=100 and bull spread 95/105, S0=100, sigma=0.2, R=0.1, T=0.25, "
+                               "k in {0.0025, 0.005, 0.01}, N in {1500, 3000, 6000}; 18 launches per step",
+                   "node_updates_per_step": int(nodes.sum())},
+        "gpu_launches": n * args.steps, "options": rows, "clocks": clocks,
+        "paper_context": {"put_N1500_k0.005_serial_ms": 1983.7, "put_N1500_k0.005_8cores_ms": 376.8,
+                          "spread_N1500_k0.01_serial_ms": 2005.2, "machine": "2 x Xeon E5405, 8 cores"},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        one = table[2:3]  # the N=1500 put at k=0.005
+        t0 = time.perf_counter()
+        oracle.price_ask_bid(one, nthreads=1)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(nodes[2]) / dt, "unit": "node updates/s", "cores": 1,
+                                "kind": "oracle", "sample": "the N=1500 put at k=0.005, one thread, "
+                                "%.2f s" % dt}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -289,6 +367,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "crr":
         run_crr(args, rank, world, local)
+        return
+    if args.workload == "paper":
+        run_paper(args, rank, world, local)
         return
 
     if args.workload == "small":

@@ -647,12 +647,15 @@ struct TcRun {
     outCap = L.capZ;
   }
 
-  OB_HD void node_table(int t) {
+  OB_HD void node_table(int t) { node_table_range(t, 0, t); }
+
+  // per-node constants of level t for the nodes jlo <= j <= jhi
+  OB_HD void node_table_range(int t, int jlo, int jhi) {
     const int lane = tm.lane();
     double* nt = L.nt[t & 1];
     const double lam = L.lam[t];
     const double kt = (t == 0) ? 0.0 : o.k;
-    for (int j = lane; j <= t; j += Team::W) {
+    for (int j = jlo + lane; j <= jhi; j += Team::W) {
       const double S = L.Stab[2 * j - t + N + 1];
       const double Sl = S * lam;
       nt[4 * j] = Sl * (1.0 + kt);
@@ -1053,12 +1056,20 @@ struct TcGroup {
     return ST_OK;
   }
 
-  // first node whose union start is >= target (nodes 0..nNodes)
+  // first node whose union start is >= target (nodes 0..nNodes): each round the team
+  // probes W evenly spaced nodes of the bracket at once and keeps the gap that holds it
   OB_HD int node_at(int t, long long target) const {
-    int lo = 0, hi = 2 * (t + 1);
+    const Team& tm = R.tm;
+    int lo = 0, hi = 2 * (t + 1);  // the answer lies in [lo, hi]
     while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((long long)R.ustart_node(t, mid) >= target) hi = mid; else lo = mid + 1;
+      const int step = (hi - lo + Team::W - 1) / Team::W;
+      const int n = lo + tm.lane() * step;
+      const bool below = n < hi && (long long)R.ustart_node(t, n) < target;
+      const int cnt = tm.count(below);  // the probes below the answer come first
+      if (cnt == 0) break;              // lo itself is at or above it
+      const int nhi = lo + cnt * step;
+      lo = lo + (cnt - 1) * step + 1;
+      if (nhi < hi) hi = nhi;
     }
     return lo;
   }
@@ -1067,12 +1078,25 @@ struct TcGroup {
   OB_HD bool compute(int t) {
     const Team& tm = R.tm;
     R.use_banks(t);
-    R.node_table(t);
-    tm.sync();
-    const int nNodes = 2 * (t + 1);
+    const int nNodes = 2 * (t + 1), W0 = t + 1;
     const long long Utot = R.ustart_node(t, nNodes);
     n0 = (c == 0) ? 0 : node_at(t, (Utot * c + G - 1) / G);
     n1 = (c == G - 1) ? nNodes : node_at(t, (Utot * (c + 1) + G - 1) / G);
+    // node constants of this share only: level t for its nodes j, level t+1 for j, j+1
+    // (a share that straddles the seller/buyer boundary needs two intervals of j)
+    if (n0 < n1) {
+      const int s_lo = n0, s_hi = (n1 < W0 ? n1 : W0) - 1;               // seller nodes
+      const int b_lo = (n0 > W0 ? n0 : W0) - W0, b_hi = n1 - 1 - W0;      // buyer nodes
+      if (s_lo <= s_hi) {
+        R.node_table_range(t, s_lo, s_hi);
+        R.node_table_range(t + 1, s_lo, s_hi + 1);
+      }
+      if (b_lo <= b_hi) {
+        R.node_table_range(t, b_lo, b_hi);
+        R.node_table_range(t + 1, b_lo, b_hi + 1);
+      }
+    }
+    tm.sync();
     R.outY = zpY; R.outF = zpF; R.outS = zpS; R.outOff = poff; R.outCap = capP;
     int wtot = 0, utot = 0;
     ztot = 0;
