@@ -175,7 +175,7 @@ __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, c
 // Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
 // one at a time as a whole-CTA team, then each of its warps takes the remaining
 // options one at a time from a second queue.  Both queues are device counters.
-template <int NW>
+template <int NW, bool WARPS>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
     char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds) {
@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
     bt.sync();
   }
+  if (!WARPS) return;  // every option went to a CTA team
   obk::WarpTeam wt;
   const size_t wbytes = (cta_bytes / NW) & ~(size_t)255;
   char* wmy = my + (size_t)(threadIdx.x >> 5) * wbytes;
@@ -740,15 +741,21 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
   const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
+  // with a heavy factor of 0 every option goes to a CTA team and the kernel leaves out
+  // the warp-team loop (and its registers); without the cost order, warps take them all
+  const bool warps = P->heavy_factor > 0.0 || !order;
+#define OB_LAUNCH_BATCHED(NWV)                                                                    \
+  (warps ? k_tc_batched<NWV, true><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena, \
+                                                                cta_bytes, P->ctl, list0, P->stats) \
+         : k_tc_batched<NWV, false><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena, \
+                                                                 cta_bytes, P->ctl, list0, P->stats))
   if (P->team_warps == 4)
-    k_tc_batched<4><<<nctas, 128, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
-                                          list0, P->stats);
+    OB_LAUNCH_BATCHED(4);
   else if (P->team_warps == 16)
-    k_tc_batched<16><<<nctas, 512, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
-                                           list0, P->stats);
+    OB_LAUNCH_BATCHED(16);
   else
-    k_tc_batched<8><<<nctas, 256, 0, s>>>(opts, n, order, out, status, P->arena, cta_bytes, P->ctl,
-                                          list0, P->stats);
+    OB_LAUNCH_BATCHED(8);
+#undef OB_LAUNCH_BATCHED
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   k_tc_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF],
@@ -1183,7 +1190,7 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
                                                              kHeavyFactor);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
-  k_tc_batched<kNW><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
+  k_tc_batched<kNW, true><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
                                                    list0, ds);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0,

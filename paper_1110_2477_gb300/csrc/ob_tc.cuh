@@ -713,6 +713,7 @@ struct TcRun {
       Em em[3];
       P1 e;
       e.dup = true;
+      e.own = 0;  // lanes past the end hand a defined code on
       int cnt = 0, node = ncur + pos, ql = -1;
       if (q < Utot) {
         const int p = node >= W0 ? 1 : 0;
