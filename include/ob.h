@@ -128,8 +128,9 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
  * width); d/dT changes the step T/N with N fixed; at k = 0, d/dk is the
  * right-hand derivative.  Method: reverse mode over the levels, root to leaves,
  * with the level functions kept at checkpoints every ceil(sqrt(N+2)) levels and
- * each segment recomputed once.  One warp per option (CTA teams for options that
- * outgrow a warp's scratch); asynchronous on stream. */
+ * each segment recomputed once.  One 8-warp CTA team per option, one CTA per SM,
+ * options taken from a device queue; follow-up launches with larger scratch for
+ * options that outgrow a CTA's share of the pool.  Asynchronous on stream. */
 int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad,
               int32_t* status, void* stream);
 

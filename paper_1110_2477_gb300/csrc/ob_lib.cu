@@ -446,6 +446,28 @@ __global__ void __launch_bounds__(kBlock) k_greeks(const obk::Opt* __restrict__ 
   }
 }
 
+// Greeks on CTA teams: each CTA takes options from the queue over [0, n) as one team.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 8 / NW) k_greeks_team(
+    const obk::Opt* __restrict__ opts, int n, double* out, double* grad, int* status, char* arena,
+    size_t cta_bytes, int* ctl, int* ovf_list) {
+  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+  obk::BlockTeam<NW> bt{tbuf};
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int oi = bt.bcast0(v);
+    if (oi >= n) break;
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
+    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
+    if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
+    bt.sync();
+  }
+}
+
 __global__ void __launch_bounds__(kTeamBlock, 1) k_greeks_retry(
     const obk::Opt* __restrict__ opts, double* out, double* grad, int* status, char* arena,
     size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list,
@@ -587,6 +609,7 @@ struct DevPool {
   size_t arena_per_warp = 8ull << 20;
   double heavy_factor = kHeavyFactor;
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
+  int greeks_team = 8;  // Greeks: warps per CTA team (4 or 8); 0: one warp per option
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -645,6 +668,7 @@ int pool_get(DevPool** out, size_t need_list) {
       if (v == 4 || v == 8 || v == 16) P.team_warps = v;
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
+    if (const char* g = getenv("OB_GREEKS_TEAM")) P.greeks_team = atoi(g);
     const size_t workers = (size_t)P.sms * P.warps_per_sm;
     P.arena_bytes = workers * P.arena_per_warp;
     const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
@@ -958,13 +982,23 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   cudaError_t e;
   if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   const obk::Opt* opts = (const obk::Opt*)params;
-  const int max_workers = P->sms * 8;
-  const int workers = n < max_workers ? n : max_workers;
-  const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
-  k_greeks<<<(workers * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(opts, n, out, grad, status, P->arena,
-                                                                   wbytes, workers, P->ctl, list0);
+  const int gteam = P->greeks_team;
+  if (gteam == 4 || gteam == 8) {
+    const int nctas = P->sms * (8 / gteam);
+    const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
+    if (gteam == 4)
+      k_greeks_team<4><<<nctas, 128, 0, s>>>(opts, n, out, grad, status, P->arena, cta_bytes, P->ctl, list0);
+    else
+      k_greeks_team<8><<<nctas, 256, 0, s>>>(opts, n, out, grad, status, P->arena, cta_bytes, P->ctl, list0);
+  } else {
+    const int max_workers = P->sms * 8;
+    const int workers = n < max_workers ? n : max_workers;
+    const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
+    k_greeks<<<(workers * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(opts, n, out, grad, status, P->arena,
+                                                                     wbytes, workers, P->ctl, list0);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   k_greeks_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, t1_bytes,

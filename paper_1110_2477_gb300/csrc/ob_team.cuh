@@ -239,19 +239,17 @@ struct BlockTeam {
     long long* h = half();
     h[threadIdx.x] = v;
     __syncthreads();
-    int lo = 0, hi = W;  // first slot with value > q1
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((int)h[mid] <= q1) lo = mid + 1; else hi = mid;
+    // first slots with value > q1 and > q2: both searches advance together (W is a power
+    // of two, so each takes log2(W) + 1 probes)
+    int lo1 = 0, lo2 = 0;
+    for (int step = W >> 1; step >= 1; step >>= 1) {
+      if ((int)h[lo1 + step - 1] <= q1) lo1 += step;
+      if ((int)h[lo2 + step - 1] <= q2) lo2 += step;
     }
-    c1 = lo;
-    lo = 0;
-    hi = W;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((int)h[mid] <= q2) lo = mid + 1; else hi = mid;
-    }
-    c2 = lo;
+    if (lo1 == W - 1 && (int)h[W - 1] <= q1) lo1 = W;
+    if (lo2 == W - 1 && (int)h[W - 1] <= q2) lo2 = W;
+    c1 = lo1;
+    c2 = lo2;
   }
   __device__ __forceinline__ int count(bool p) const { return __syncthreads_count(p ? 1 : 0); }
   __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p ? 1 : 0) != 0; }
