@@ -49,6 +49,7 @@ OB_HD bool kle(double a, double b) { return okey(a) <= okey(b); }
 OB_HD bool keq(double a, double b) { return okey(a) == okey(b); }
 OB_HD bool same_bits(double a, double b) { return dbits(a) == dbits(b); }
 OB_HD long long kmin(long long a, long long b) { return a < b ? a : b; }
+constexpr long long KMAXLL = 0x7fffffffffffffffLL;
 
 OB_HD int popc32(unsigned x) {
 #if defined(__CUDA_ARCH__)
@@ -289,25 +290,27 @@ struct BlockTeam {
       h[W + 2 * w + 1] = fl;
     }
     __syncthreads();
-    if (!fl) {  // no head in this warp up to here: continue from earlier warps, then the carry
-      bool stop = false;
-      for (int k = w - 1; k >= 0 && !stop; --k) {
-        v = kmin(v, h[W + 2 * k]);
-        stop = h[W + 2 * k + 1] != 0;
-      }
-      if (!stop) v = kmin(v, carry);
+    // across warps: lane k of every warp takes warp k's record and the warp runs the
+    // segmented scan over lanes 0..NW-1 with shuffles; acc_k = head in warp k ? its value :
+    // min(acc_{k-1}, its value), acc_{-1} = carry
+    long long rv = KMAXLL;
+    int rf = 0;
+    if (l < NW) {
+      rv = h[W + 2 * l];
+      rf = (int)h[W + 2 * l + 1];
     }
-    // the new carry: the last lane's result, from the warp aggregates
-    {
-      long long c = h[W + 2 * (NW - 1)];
-      bool stop = h[W + 2 * (NW - 1) + 1] != 0;
-      for (int k = NW - 2; k >= 0 && !stop; --k) {
-        c = kmin(c, h[W + 2 * k]);
-        stop = h[W + 2 * k + 1] != 0;
+    if (l == 0 && !rf) rv = kmin(rv, carry);
+    for (int d = 1; d < NW; d <<= 1) {
+      const long long vu = __shfl_up_sync(0xffffffffu, rv, d);
+      const int fu = __shfl_up_sync(0xffffffffu, rf, d);
+      if (l >= d) {
+        if (!rf) rv = kmin(rv, vu);
+        rf |= fu;
       }
-      if (!stop) c = kmin(c, carry);
-      carry = c;
     }
+    const long long before = __shfl_sync(0xffffffffu, rv, (w + 31) & 31);  // acc_{w-1}
+    if (!fl) v = kmin(v, w ? before : carry);
+    carry = __shfl_sync(0xffffffffu, rv, NW - 1);
     return v;
   }
   __device__ __forceinline__ void seg_argmin(long long& v, int& ix, bool head, long long& cv,
@@ -330,26 +333,30 @@ struct BlockTeam {
       h[W + 3 * w + 2] = fl;
     }
     __syncthreads();
-    if (!fl) {
-      bool stop = false;
-      for (int k = w - 1; k >= 0 && !stop; --k) {
-        if (h[W + 3 * k] < v) { v = h[W + 3 * k]; ix = (int)h[W + 3 * k + 1]; }
-        stop = h[W + 3 * k + 2] != 0;
-      }
-      if (!stop && cv < v) { v = cv; ix = ci; }
+    // across warps as in seg_min, carrying the index; among equal minima the latest wins
+    long long rv = KMAXLL;
+    int ri = 0, rf = 0;
+    if (l < NW) {
+      rv = h[W + 3 * l];
+      ri = (int)h[W + 3 * l + 1];
+      rf = (int)h[W + 3 * l + 2];
     }
-    {
-      long long c = h[W + 3 * (NW - 1)];
-      int cidx = (int)h[W + 3 * (NW - 1) + 1];
-      bool stop = h[W + 3 * (NW - 1) + 2] != 0;
-      for (int k = NW - 2; k >= 0 && !stop; --k) {
-        if (h[W + 3 * k] < c) { c = h[W + 3 * k]; cidx = (int)h[W + 3 * k + 1]; }
-        stop = h[W + 3 * k + 2] != 0;
+    if (l == 0 && !rf && cv < rv) { rv = cv; ri = ci; }
+    for (int d = 1; d < NW; d <<= 1) {
+      const long long vu = __shfl_up_sync(0xffffffffu, rv, d);
+      const int iu = __shfl_up_sync(0xffffffffu, ri, d);
+      const int fu = __shfl_up_sync(0xffffffffu, rf, d);
+      if (l >= d) {
+        if (!rf && vu < rv) { rv = vu; ri = iu; }
+        rf |= fu;
       }
-      if (!stop && cv < c) { c = cv; cidx = ci; }
-      cv = c;
-      ci = cidx;
     }
+    const int src = (w + 31) & 31;
+    const long long bv = w ? __shfl_sync(0xffffffffu, rv, src) : cv;
+    const int bi = w ? __shfl_sync(0xffffffffu, ri, src) : ci;
+    if (!fl && bv < v) { v = bv; ix = bi; }
+    cv = __shfl_sync(0xffffffffu, rv, NW - 1);
+    ci = __shfl_sync(0xffffffffu, ri, NW - 1);
   }
   __device__ __forceinline__ double sum(double v) const {
     long long* h = half();
