@@ -60,7 +60,8 @@ struct Lay {
   double *zY[2], *zF[2], *zS[2];
   int* offw;      // [2(N+1)+1]
   int* wN;        // node of each point of w
-  double *wY, *wF, *wS, *wG, *wH;
+  double *wY, *wF, *wS;
+  long long *wGK, *wHK;  // keys of g = w + S^a y and h = w + S^b y (only compared)
   long long *wCA, *wCB;
   int capZ, capW;
 };
@@ -99,8 +100,8 @@ OB_HD char* carve_cap(char* base, int N, size_t cap, Lay& L) {
   L.wY = (double*)take(sizeof(double) * cap);
   L.wF = (double*)take(sizeof(double) * cap);
   L.wS = (double*)take(sizeof(double) * cap);
-  L.wG = (double*)take(sizeof(double) * cap);
-  L.wH = (double*)take(sizeof(double) * cap);
+  L.wGK = (long long*)take(sizeof(long long) * cap);
+  L.wHK = (long long*)take(sizeof(long long) * cap);
   L.wCA = (long long*)take(sizeof(long long) * cap);
   L.wCB = (long long*)take(sizeof(long long) * cap);
   L.wN = (int*)take(sizeof(int) * cap);
@@ -775,9 +776,9 @@ struct TcRun {
         const int j = n >= W0 ? n - W0 : n;
         const double y = L.wY[i], f = L.wF[i];
         const double g = f + nt[4 * j] * y, h = f + nt[4 * j + 1] * y;
-        L.wG[i] = g;
-        L.wH[i] = h;
+        L.wGK[i] = okey(g);
         hk = okey(h);
+        L.wHK[i] = hk;
       }
       if (TRACK) {
         int ix = i;
@@ -797,7 +798,7 @@ struct TcRun {
       const bool ok = i < wtot;
       const int n = ok ? L.wN[i] : -1;
       const bool head = ok && (i + 1 == wtot || L.wN[i + 1] != n);
-      long long gk = ok ? okey(L.wG[i]) : KMAX;
+      long long gk = ok ? L.wGK[i] : KMAX;
       if (TRACK) {
         int ix = i;
         tm.seg_argmin(gk, ix, head, carry, carry_i);
@@ -839,8 +840,8 @@ struct TcRun {
       in.f1 = L.wF[i + 1];
       const long long cA1 = L.wCA[i + 1];
       in.cA1 = unkey(cA1);
-      const long long g0 = okey(L.wG[i]), g1 = okey(L.wG[i + 1]);
-      const long long h0 = okey(L.wH[i]), h1 = okey(L.wH[i + 1]);
+      const long long g0 = L.wGK[i], g1 = L.wGK[i + 1];
+      const long long h0 = L.wHK[i], h1 = L.wHK[i + 1];
       // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
       // the cB line iff h <= cB_i at both ends (then that side of v equals w)
       in.Arel = !(g1 == cA1 && g0 <= cA1);
