@@ -180,9 +180,9 @@ typedef struct {
 int ob_get_stats(ob_stats_t* host_out);
 
 /* Configuration of the batched form on the current device.
- *   team_warps  warps per CTA team (4, 8 or 16; the grid is 16 / team_warps CTAs per
- *               SM, each with 1 / (CTAs) of the scratch pool as its breakpoint
- *               capacity); 0 keeps the current value (default 16).
+ *   team_warps  warps per CTA team (4, 8, 12 or 16; the grid is 16 / team_warps CTAs
+ *               per SM (one for 12), each with 1 / (CTAs) of the scratch pool as its
+ *               breakpoint capacity); 0 keeps the current value (default 16).
  *   use_graphs  1: ob_price_ask_bid captures its launch sequence (queue reset, cost
  *               order, persistent kernel, two follow-up tiers) into a CUDA graph per
  *               (params, n, out, status) key, keeps the last 4, and replays a graph
@@ -190,13 +190,14 @@ int ob_get_stats(ob_stats_t* host_out);
  * Drops the cached graphs.  Returns OB_ERR_ARG for another team width. */
 int ob_configure(int32_t team_warps, int32_t use_graphs);
 
-/* Autotuner of the batched form: times each team width (16, 8, 4 warps; hence the
- * CTA size and the per-CTA breakpoint capacity) on a sample of the given options
+/* Autotuner of the batched form: times each team width (16, 12, 8, 4 warps; hence the
+ * CTA size, the registers per thread and the per-CTA breakpoint capacity) on a sample
+ * of the given options
  * (every (n_options / sample)-th option; sample <= 0 or >= n_options: all of them),
  * one warm-up run and one timed run each, with CUDA events on stream, and keeps the
  * fastest for later calls.  Synchronous.  params is a DEVICE pointer as in
  * ob_price_ask_bid.  team_warps_out (HOST, may be NULL) receives the choice; ms_out
- * (HOST, 3 floats, may be NULL) the timed milliseconds of 16, 8 and 4 warps. */
+ * (HOST, 4 floats, may be NULL) the timed milliseconds of 16, 12, 8 and 4 warps. */
 int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, void* stream,
                 int32_t* team_warps_out, float* ms_out);
 

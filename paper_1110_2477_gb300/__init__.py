@@ -164,17 +164,17 @@ def ob_release():
 
 
 def ob_configure(team_warps=0, use_graphs=-1):
-    """Team width of the batched form (4, 8, 16; 0 keeps) and CUDA-graph replay (1, 0; -1 keeps)."""
+    """Team width of the batched form (4, 8, 12, 16; 0 keeps) and CUDA-graph replay (1, 0; -1 keeps)."""
     _check(load().ob_configure(int(team_warps), int(use_graphs)))
 
 
 def ob_autotune(params, n, sample=0, stream=None):
-    """Time team widths 16, 8, 4 on a sample of the device records and keep the fastest.
-    Returns (team_warps, {16: ms, 8: ms, 4: ms})."""
+    """Time team widths 16, 12, 8, 4 on a sample of the device records and keep the fastest.
+    Returns (team_warps, {16: ms, 12: ms, 8: ms, 4: ms})."""
     tw = ctypes.c_int32(0)
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * 4)()
     _check(load().ob_autotune(_ptr(params), int(n), int(sample), _stream(stream), ctypes.byref(tw), ms))
-    return int(tw.value), {16: float(ms[0]), 8: float(ms[1]), 4: float(ms[2])}
+    return int(tw.value), {16: float(ms[0]), 12: float(ms[1]), 8: float(ms[2]), 4: float(ms[3])}
 
 
 def autotune(table, sample=0):

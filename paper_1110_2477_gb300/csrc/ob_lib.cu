@@ -665,7 +665,7 @@ int pool_get(DevPool** out, size_t need_list) {
     if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
     if (const char* tw = getenv("OB_TEAM_WARPS")) {
       const int v = atoi(tw);
-      if (v == 4 || v == 8 || v == 16) P.team_warps = v;
+      if (v == 4 || v == 8 || v == 12 || v == 16) P.team_warps = v;
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
     if (const char* g = getenv("OB_GREEKS_TEAM")) P.greeks_team = atoi(g);
@@ -775,6 +775,8 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
                                                                  cta_bytes, P->ctl, list0, P->stats))
   if (P->team_warps == 4)
     OB_LAUNCH_BATCHED(4);
+  else if (P->team_warps == 12)
+    OB_LAUNCH_BATCHED(12);
   else if (P->team_warps == 16)
     OB_LAUNCH_BATCHED(16);
   else
@@ -1080,7 +1082,8 @@ int ob_get_stats(ob_stats_t* host_out) {
 }
 
 int ob_configure(int32_t team_warps, int32_t use_graphs) {
-  if (team_warps != 0 && team_warps != 4 && team_warps != 8 && team_warps != 16) return OB_ERR_ARG;
+  if (team_warps != 0 && team_warps != 4 && team_warps != 8 && team_warps != 12 && team_warps != 16)
+    return OB_ERR_ARG;
   DevPool* P = nullptr;
   int rc = pool_get(&P, 1);
   if (rc) return rc;
@@ -1121,11 +1124,11 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     if (a) cudaEventDestroy(a);
     return cuda_fail(e);
   }
-  const int cands[3] = {16, 8, 4};
+  const int cands[4] = {16, 12, 8, 4};
   const int keep = P->team_warps;
   int best = keep;
   float best_ms = 0.0f;
-  for (int c = 0; c < 3 && rc == OB_OK; ++c) {
+  for (int c = 0; c < 4 && rc == OB_OK; ++c) {
     P->team_warps = cands[c];
     float ms = 0.0f;
     for (int rep = 0; rep < 2 && rc == OB_OK; ++rep) {  // one warm-up run, one timed run

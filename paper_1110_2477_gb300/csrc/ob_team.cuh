@@ -51,6 +51,13 @@ OB_HD bool same_bits(double a, double b) { return dbits(a) == dbits(b); }
 OB_HD long long kmin(long long a, long long b) { return a < b ? a : b; }
 constexpr long long KMAXLL = 0x7fffffffffffffffLL;
 
+// smallest power of two >= w
+OB_HD constexpr int pow2_ceil(int w) {
+  int p = 1;
+  while (p < w) p <<= 1;
+  return p;
+}
+
 OB_HD int popc32(unsigned x) {
 #if defined(__CUDA_ARCH__)
   return __popc(x);
@@ -240,15 +247,19 @@ struct BlockTeam {
     long long* h = half();
     h[threadIdx.x] = v;
     __syncthreads();
-    // first slots with value > q1 and > q2: both searches advance together (W is a power
-    // of two, so each takes log2(W) + 1 probes)
+    // first slots with value > q1 and > q2: both searches advance together over the
+    // next power of two P >= W (slots past W read as +infinity)
+    constexpr int P = pow2_ceil(W);
     int lo1 = 0, lo2 = 0;
-    for (int step = W >> 1; step >= 1; step >>= 1) {
-      if ((int)h[lo1 + step - 1] <= q1) lo1 += step;
-      if ((int)h[lo2 + step - 1] <= q2) lo2 += step;
+    for (int step = P >> 1; step >= 1; step >>= 1) {
+      const int i1 = lo1 + step - 1, i2 = lo2 + step - 1;
+      if (i1 < W && (int)h[i1] <= q1) lo1 += step;
+      if (i2 < W && (int)h[i2] <= q2) lo2 += step;
     }
-    if (lo1 == W - 1 && (int)h[W - 1] <= q1) lo1 = W;
-    if (lo2 == W - 1 && (int)h[W - 1] <= q2) lo2 = W;
+    if (P == W) {
+      if (lo1 == W - 1 && (int)h[W - 1] <= q1) lo1 = W;
+      if (lo2 == W - 1 && (int)h[W - 1] <= q2) lo2 = W;
+    }
     c1 = lo1;
     c2 = lo2;
   }

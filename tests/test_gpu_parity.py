@@ -271,7 +271,7 @@ def test_team_widths_give_bitwise_equal_prices():
     t = W.random_table(96, 4711, N_lo=20, N_hi=400)
     try:
         res = []
-        for tw in (16, 8, 4):
+        for tw in (16, 12, 8, 4):
             ob.ob_configure(team_warps=tw, use_graphs=0)
             out, st = _gpu(t)
             assert ob.ob_get_stats()["team_warps"] == tw
@@ -321,7 +321,7 @@ def test_autotune_keeps_a_valid_width():
     before, _ = _gpu(t)
     try:
         tw, ms = ob.autotune(t, sample=100)
-        assert tw in (4, 8, 16) and all(v > 0 for v in ms.values())
+        assert tw in (4, 8, 12, 16) and all(v > 0 for v in ms.values())
         assert ms[tw] == min(ms.values())
         after, _ = _gpu(t)
         assert ob.ob_get_stats()["team_warps"] == tw
