@@ -364,3 +364,25 @@ def test_wide_paper_scale_matches_oracle_and_batched():
         assert s[k] == s2[k], k
     ref, rst = oracle.price_ask_bid(t, nthreads=2)
     _assert_parity(t, b, sb, ref, rst)
+
+
+# ---------------------------------------------------------------- price curves at scale
+def test_price_curves_ordering_at_scale():
+    """Section 5's price curves at N = 1500 for 41 values of S0 in [90, 110]: at every S0,
+    bid(0.5%) <= bid(0.25%) <= CRR = ask(0) = bid(0) < ask(0.25%) < ask(0.5%); the k = 0 prices
+    equal the CRR kernel's; a sample matches the oracle."""
+    ks = (0.0, 0.0025, 0.005)
+    t = W.price_curves(ks=ks, N=1500)
+    out, st = _gpu(t)
+    assert np.all(st == 0)
+    o = out.reshape(-1, len(ks), 2)
+    ask, bid = o[..., 0], o[..., 1]
+    crr, _ = _ob().crr(t[0::3])
+    crr = crr.cpu().numpy()
+    assert np.all(np.abs(ask[:, 0] - bid[:, 0]) <= 1e-12 * ask[:, 0])
+    assert np.all(np.abs(ask[:, 0] - crr) <= RTOL * np.maximum(crr, 1.0))
+    assert np.all(bid[:, 2] <= bid[:, 1] + 1e-12) and np.all(bid[:, 1] <= bid[:, 0] + 1e-12)
+    assert np.all(ask[:, 0] < ask[:, 1]) and np.all(ask[:, 1] < ask[:, 2])
+    idx = np.array([1, 5, 61, 119, 122])
+    ref, rst = oracle.price_ask_bid(t[idx], nthreads=5)
+    _assert_parity(t[idx], out[idx], st[idx], ref, rst)

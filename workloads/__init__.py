@@ -56,6 +56,14 @@ def paper_scale(Ns=(1500, 3000, 6000), ks=(0.0025, 0.005, 0.01)):
     return concat(*rows)
 
 
+def price_curves(S0s=None, ks=(0.0, 0.0025, 0.005), N=1500):
+    """Price curves of the put K=100 (sigma=0.2, R=0.1, T=0.25) over S0 in [90, 110]:
+    one row per (S0, k), k varying fastest."""
+    if S0s is None:
+        S0s = np.linspace(90.0, 110.0, 41)
+    return concat(*[make(S0=float(S0), K=100.0, k=float(k), N=N, payoff=PUT) for S0 in S0s for k in ks])
+
+
 def random_table(n, seed, N_lo=100, N_hi=2000, payoffs=(PUT, CALL, SPREAD), k_hi=0.02,
                  fixed_N=None, k_zero=False):
     """n options with N ~ U{N_lo..N_hi}, S0, K ~ U[80,120], sigma ~ U[0.1,0.5],
