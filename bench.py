@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-greeks", action="store_true", help="skip the Greeks-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default team width")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr", "paper"],
+    ap.add_argument("--options", type=int, default=1024,
+                    help="greeks workload: the first n of the 1024 puts (smaller for profiling)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr", "paper", "greeks"],
                     help="batched: the 4096-option batch (the reported metric); small: 48 options "
                          "with N in [200, 600] (seed 321), for profiler captures")
     return ap.parse_args()
@@ -351,6 +353,76 @@ def run_paper(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_greeks(args, rank, world, local):
+    """The adjoint workload: 1024 American puts, N = 1000 (seed 4), prices and the 12
+    derivatives per option in one ob_greeks call per step; options/s against the plain
+    pricing call on the same options."""
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    dev = torch.device("cuda", local)
+    table = W.greeks_puts()[:args.options]
+    n = len(table)
+    params = ob.to_device(table, dev)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    grad = torch.empty((n, 2, 6), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ob.ob_greeks(params, n, out, grad, st, stream)
+    torch.cuda.synchronize(dev)
+    assert int((st != 0).sum().item()) == 0
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    sampler.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ob.ob_greeks(params, n, out, grad, st, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    job_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ob.ob_price_ask_bid(params, n, out, st, stream)
+    pa.record(stream)
+    ob.ob_price_ask_bid(params, n, out, st, stream)
+    pb.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_s = pa.elapsed_time(pb) / 1e3
+    if rank != 0:
+        return
+    value = world * n * args.steps / job_s
+    line = {
+        "metric": "options/s with Greeks (ask, bid and 12 derivatives), FP64", "value": value,
+        "unit": "options/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * job_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%d American puts, N=1000, batched-table distributions (seed 4)" % n,
+                   "node_updates_per_step": int(np.sum(W.node_updates(table))),
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "plain": {"value": n / plain_s, "unit": "options/s", "call": "ob_price_ask_bid"},
+        "greeks_over_plain_time": (job_s / args.steps) / plain_s,
+        "gpu_launches": 3 * args.steps, "step_ms": step_ms, "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        sample = table[:cores]
+        t0 = time.perf_counter()
+        oracle.greeks(sample, nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": "options/s", "cores": cores,
+                                "kind": "oracle", "sample": "the first %d options, forward-mode "
+                                "dual numbers, %.1f s" % (len(sample), dt)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -370,6 +442,9 @@ def main():
         return
     if args.workload == "paper":
         run_paper(args, rank, world, local)
+        return
+    if args.workload == "greeks":
+        run_greeks(args, rank, world, local)
         return
 
     if args.workload == "small":

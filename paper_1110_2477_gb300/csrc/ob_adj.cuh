@@ -83,6 +83,29 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   return A.sd_cap > 0;
 }
 
+// Sink of the local-dual replay of a piece: every emitted point's local derivatives are
+// contracted with that point's adjoint as soon as the point is produced, in output order
+// (left tail, first point if it is part of the output, inside), so no array of LD points
+// is kept.
+struct PullOut {
+  const double *zbY, *zbF, *zbS;
+  int w;           // output position of the next emitted point
+  int emit_first;  // whether the candidate first point is part of the output
+  double adj[LDN];
+  double last_slope, tail_slope;
+  OB_HD void begin() {}
+  OB_HD void pull(const EmT<LD>& em) {
+    const double by = zbY[w], bf = zbF[w], bs = zbS[w];
+    for (int k = 0; k < LDN; ++k) adj[k] += by * em.y.d[k] + bf * em.f.d[k] + bs * em.s.d[k];
+    ++w;
+  }
+  OB_HD void add_tl(const EmT<LD>& e) { pull(e); }
+  OB_HD void set_first(const EmT<LD>& e) {
+    if (emit_first) pull(e);
+  }
+  OB_HD void add_m(const EmT<LD>& e) { pull(e); }
+};
+
 OB_HD void atomic_add(double* a, double v) {
 #if defined(__CUDA_ARCH__)
   if (v != 0.0) atomicAdd(a, v);
@@ -237,26 +260,16 @@ struct TcAdj {
         }
         li.yu = in.yu; li.head = in.head; li.tail = in.tail; li.seller = in.seller;
         li.anchor = in.anchor; li.Arel = in.Arel; li.Brel = in.Brel;
-        PieceOut<LD> pl;
+        PullOut pl;
+        pl.zbY = zbY;
+        pl.zbF = zbF;
+        pl.zbS = zbS;
+        pl.w = p0;
+        pl.emit_first = emit_first;
+        for (int k = 0; k < LDN; ++k) pl.adj[k] = 0.0;
         PlayDec pd{rec.d, 0};
         piece(li, pl, pd);
-        double adj[11];
-        for (int k = 0; k < 11; ++k) adj[k] = 0.0;
-        int w = p0;
-        auto pull = [&](const EmT<LD>& em) {
-          const double by = zbY[w], bf = zbF[w], bs = zbS[w];
-          for (int k = 0; k < 11; ++k) adj[k] += by * em.y.d[k] + bf * em.f.d[k] + bs * em.s.d[k];
-          ++w;
-        };
-        for (int c = 0; c < pl.ntl; ++c) pull(pl.tl[c]);
-        if (emit_first) pull(pl.first);
-        for (int c = 0; c < pl.nm; ++c) pull(pl.m[c]);
-#ifdef OB_ADJ_DEBUG
-        printf("  p3adj t=%d i=%d nout=%d p0=%d ntl=%d/%d first=%d nm=%d/%d head=%d tail=%d adj:", t, i, nout, p0, pl.ntl, po.ntl, emit_first, pl.nm, po.nm, (int)in.head, (int)in.tail);
-        for (int k = 0; k < 11; ++k) printf(" %.4g", adj[k]);
-        printf("\n");
-        if (pl.ntl) printf("    tl0 y %.6g dy:%g %g %g %g %g %g %g %g %g %g %g\n", pl.tl[0].y.v, pl.tl[0].y.d[0], pl.tl[0].y.d[1], pl.tl[0].y.d[2], pl.tl[0].y.d[3], pl.tl[0].y.d[4], pl.tl[0].y.d[5], pl.tl[0].y.d[6], pl.tl[0].y.d[7], pl.tl[0].y.d[8], pl.tl[0].y.d[9], pl.tl[0].y.d[10]);
-#endif
+        const double* adj = pl.adj;
         atomic_add(&A.wbY[i], adj[0]);
         atomic_add(&A.wbF[i], adj[1]);
         atomic_add(&A.wbS[i], adj[2]);
@@ -532,14 +545,6 @@ struct TcAdj {
         zero(A.wbY, wtot); zero(A.wbF, wtot); zero(A.wbS, wtot); zero(A.wbG, wtot); zero(A.wbH, wtot);
         tm.sync();
         pass3_adj(t, wtot, A.zbY[cur], A.zbF[cur], A.zbS[cur]);
-#ifdef OB_ADJ_DEBUG
-        if (lane == 0) {
-          printf("t=%d wtot=%d np_t=%d\n", t, wtot, A.ref[t].np);
-          for (int q = 0; q < A.ref[t].np; ++q) printf("  zbar_t[%d] y %.6g f %.6g s %.6g\n", q, A.zbY[cur][q], A.zbF[cur][q], A.zbS[cur][q]);
-          for (int q = 0; q < wtot; ++q) printf("  wbar[%d] y %.6g f %.6g s %.6g g %.6g h %.6g argA %d argB %d\n", q, A.wbY[q], A.wbF[q], A.wbS[q], A.wbG[q], A.wbH[q], A.argA[q], A.argB[q]);
-        }
-        tm.sync();
-#endif
         pass2_adj(t, wtot);
         const int nxt = cur ^ 1;
         const int np1 = A.ref[t + 1].np;

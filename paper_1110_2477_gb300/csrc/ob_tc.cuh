@@ -470,15 +470,19 @@ struct PieceOut {
   EmT<T> m[MAXSUB];      // emissions inside the piece
   int nm;
   double last_slope, tail_slope;
+  // piece() hands its emissions over in output order: left tail, first, inside
+  OB_HD void begin() { ntl = nm = 0; }
+  OB_HD void add_tl(const EmT<T>& e) { tl[ntl++] = e; }
+  OB_HD void set_first(const EmT<T>& e) { first = e; }
+  OB_HD void add_m(const EmT<T>& e) { m[nm++] = e; }
 };
 
 // The restriction and the exercise step on one piece (and, for the first point
 // of a node, on the left tail).
-template <class T, class D>
-OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
+template <class T, class D, class O>
+OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
   const double INF = ob_inf();
-  out.ntl = 0;
-  out.nm = 0;
+  out.begin();
   LnT<T> lines[5];  // 0 piece of w, 1 cA line, 2 cB line, 3 u left branch, 4 u right branch
   const T yu = mk<T>(in.yu);
   lines[2] = LnT<T>{mk<T>(0.0), in.cB, -in.Sb, mk<T>(0.0), mk<T>(0.0), 1};
@@ -498,7 +502,7 @@ OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
         if (prev_l >= 0 && dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1))
-          out.tl[out.ntl++] = EmT<T>{x, ln_eval(lines[l], x), lines[l].s};
+          out.add_tl(EmT<T>{x, ln_eval(lines[l], x), lines[l].s});
         prev_l = l;
       }
     }
@@ -533,20 +537,20 @@ OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
     }
     outcome = dec.take(outcome);
     if (outcome == 0) {
-      out.first = EmT<T>{in.y0, in.f0, in.s0};
+      out.set_first(EmT<T>{in.y0, in.f0, in.s0});
       out.last_slope = val(in.s0);
     } else if (outcome == 1) {
-      out.first = EmT<T>{in.y0, q0, sQ};
+      out.set_first(EmT<T>{in.y0, q0, sQ});
       out.last_slope = val(sQ);
     } else {
       const T x = in.y0 + (in.f0 - q0) / (sQ - in.s0);
       if (outcome == 2) {  // w, then u from x
-        out.first = EmT<T>{in.y0, in.f0, in.s0};
-        out.m[out.nm++] = EmT<T>{x, in.vu + sQ * (x - yu), sQ};
+        out.set_first(EmT<T>{in.y0, in.f0, in.s0});
+        out.add_m(EmT<T>{x, in.vu + sQ * (x - yu), sQ});
         out.last_slope = val(sQ);
       } else {  // u, then w from x
-        out.first = EmT<T>{in.y0, q0, sQ};
-        out.m[out.nm++] = EmT<T>{x, in.f0 + in.s0 * (x - in.y0), in.s0};
+        out.set_first(EmT<T>{in.y0, q0, sQ});
+        out.add_m(EmT<T>{x, in.f0 + in.s0 * (x - in.y0), in.s0});
         out.last_slope = val(in.s0);
       }
     }
@@ -605,9 +609,9 @@ OB_HD void piece(const PieceIn<T>& in, PieceOut<T>& out, D& dec) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
         if (prev_l < 0) {
-          out.first = EmT<T>{in.y0, ln_eval(lines[l], in.y0), lines[l].s};
+          out.set_first(EmT<T>{in.y0, ln_eval(lines[l], in.y0), lines[l].s});
         } else if (dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1)) {
-          out.m[out.nm++] = EmT<T>{x, ln_eval(lines[l], x), lines[l].s};
+          out.add_m(EmT<T>{x, ln_eval(lines[l], x), lines[l].s});
         }
         prev_l = l;
       }
