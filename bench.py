@@ -33,6 +33,10 @@ import workloads as W  # noqa: E402
 METRIC = "tree node updates/s (ask+bid, FP64) batched; options/s with Greeks vs plain"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 dense FP64 (profiling recipe); see the design doc
 CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_batched<16, false> launch on the
+# 4096-option batch (ncu --metrics ..., one pass; 561,888,736,256 + 1,142,301,330,176 bytes),
+# the kernel as built from this source; reset to None when the kernel changes
+BATCHED_TRAFFIC = 561888736256 + 1142301330176
 
 
 def parse():
@@ -569,9 +573,12 @@ def main():
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": BATCHED_TRAFFIC if args.workload == "batched" else None,
                      "note": "algorithmic FP64 flops = 2U + 4W + 2Z per step (U successor points "
-                             "merged, W points of w, Z points of z), FP64 peak nominal"},
+                             "merged, W points of w, Z points of z), FP64 peak nominal; traffic = "
+                             "DRAM bytes read + written by one k_tc_batched launch of this "
+                             "workload (ncu, one pass)"},
         "breakpoints": {"u_points": stats["u_points"], "w_points": stats["w_points"],
                         "z_points": stats["z_points"], "max_level_points": stats["max_level_points"],
                         "retried": stats["retried"]},
