@@ -368,15 +368,16 @@ struct PlayDec {
 // (exact there); an F line (a piece of w) is also exact at its right end x1.
 template <class T>
 struct LnT {
-  T x0, v0, s, x1, v1;
+  T x0, v0, s;
   int icpt;  // 1: intercept form, value = v0 + s*x
+  int endp;  // 1: the piece of w, also exact at the piece's right end (ex, ev below)
 };
 
 template <class T>
-OB_HD T ln_eval(const LnT<T>& l, const T& x) {
+OB_HD T ln_eval(const LnT<T>& l, const T& x, const T& ex, const T& ev) {
   if (l.icpt) return l.v0 + l.s * x;
   if (same_bits(val(x), val(l.x0))) return l.v0;
-  if (same_bits(val(x), val(l.x1))) return l.v1;
+  if (l.endp && same_bits(val(x), val(ex))) return ev;
   return l.v0 + l.s * (x - l.x0);
 }
 
@@ -389,8 +390,8 @@ constexpr int MAXSUB = 10;
 // of it the line of smaller slope is the larger one), so a tie at one end that
 // rounding tipped the wrong way cannot misplace the piece.
 template <class T, class D>
-OB_HD int comb1(const LnT<T>* lines, const T& x0, const T& x1, int pi, int qi, bool take_max,
-                D& dec, int& la, T& xb, int& lb) {
+OB_HD int comb1(const LnT<T>* lines, const T& ex, const T& ev, const T& x0, const T& x1, int pi,
+                int qi, bool take_max, D& dec, int& la, T& xb, int& lb) {
   la = pi;
   if (pi == qi) return 1;
   const double INF = ob_inf();
@@ -401,8 +402,8 @@ OB_HD int comb1(const LnT<T>* lines, const T& x0, const T& x1, int pi, int qi, b
   // outcome: 0 left winner whole, 1 right line whole, 2 left line whole, 3 split
   int outcome = 0, lw = pi;
   T p0 = mk<T>(0.0), q0 = mk<T>(0.0), p1 = mk<T>(0.0), q1 = mk<T>(0.0);
-  if (finite0) { p0 = ln_eval(P, x0); q0 = ln_eval(Q, x0); }
-  if (finite1) { p1 = ln_eval(P, x1); q1 = ln_eval(Q, x1); }
+  if (finite0) { p0 = ln_eval(P, x0, ex, ev); q0 = ln_eval(Q, x0, ex, ev); }
+  if (finite1) { p1 = ln_eval(P, x1, ex, ev); q1 = ln_eval(Q, x1, ex, ev); }
   const int left_line = ((kps < kqs) == take_max) ? pi : qi;
   const int right_line = (left_line == pi) ? qi : pi;
   {
@@ -485,11 +486,11 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
   out.begin();
   LnT<T> lines[5];  // 0 piece of w, 1 cA line, 2 cB line, 3 u left branch, 4 u right branch
   const T yu = mk<T>(in.yu);
-  lines[2] = LnT<T>{mk<T>(0.0), in.cB, -in.Sb, mk<T>(0.0), mk<T>(0.0), 1};
-  lines[3] = LnT<T>{yu, in.vu, -in.Sa, mk<T>(INF), mk<T>(0.0), 0};
-  lines[4] = LnT<T>{yu, in.vu, -in.Sb, mk<T>(INF), mk<T>(0.0), 0};
+  lines[2] = LnT<T>{mk<T>(0.0), in.cB, -in.Sb, 1, 0};
+  lines[3] = LnT<T>{yu, in.vu, -in.Sa, 0, 0};
+  lines[4] = LnT<T>{yu, in.vu, -in.Sb, 0, 0};
   if (in.head) {  // left tail: v is the cA_0 line; u turns at yu if yu < y0
-    lines[1] = LnT<T>{mk<T>(0.0), in.cA0, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
+    lines[1] = LnT<T>{mk<T>(0.0), in.cA0, -in.Sa, 1, 0};
     const bool split = dec.take(klt(in.yu, val(in.y0)) ? 1 : 0);
     int prev_l = -1;
     for (int part = 0; part < (split ? 2 : 1); ++part) {
@@ -497,12 +498,13 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
       const T x1 = split && !part ? yu : in.y0;
       int la, lb;
       T xb;
-      const int n = comb1(lines, x0, x1, 1, part ? 4 : 3, in.seller, dec, la, xb, lb);
+      const int n =
+          comb1(lines, in.y1, in.f1, x0, x1, 1, part ? 4 : 3, in.seller, dec, la, xb, lb);
       for (int c = 0; c < n; ++c) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
         if (prev_l >= 0 && dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1))
-          out.add_tl(EmT<T>{x, ln_eval(lines[l], x), lines[l].s});
+          out.add_tl(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s});
         prev_l = l;
       }
     }
@@ -567,14 +569,14 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
     vl[0] = 2;
     hi = mk<T>(INF);
   } else {
-    lines[0] = LnT<T>{in.y0, in.f0, in.s0, in.y1, in.f1, 0};
-    lines[1] = LnT<T>{mk<T>(0.0), in.cA1, -in.Sa, mk<T>(0.0), mk<T>(0.0), 1};
+    lines[0] = LnT<T>{in.y0, in.f0, in.s0, 0, 1};
+    lines[1] = LnT<T>{mk<T>(0.0), in.cA1, -in.Sa, 1, 0};
     vl[0] = 0;
     hi = in.y1;
     if (in.Brel) {
       int la, lb;
       T xb;
-      nv = comb1(lines, in.y0, hi, 0, 2, false, dec, la, xb, lb);
+      nv = comb1(lines, in.y1, in.f1, in.y0, hi, 0, 2, false, dec, la, xb, lb);
       vl[0] = la;
       if (nv == 2) { vx[1] = xb; vl[1] = lb; }
     }
@@ -585,7 +587,8 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
       for (int k = 0; k < nv; ++k) {
         int la, lb;
         T xb;
-        const int n = comb1(lines, vx[k], k + 1 < nv ? vx[k + 1] : hi, vl[k], 1, false, dec, la, xb, lb);
+        const int n = comb1(lines, in.y1, in.f1, vx[k], k + 1 < nv ? vx[k + 1] : hi, vl[k], 1,
+                            false, dec, la, xb, lb);
         mx[nm] = vx[k]; ml[nm] = la; ++nm;
         if (n == 2) { mx[nm] = xb; ml[nm] = lb; ++nm; }
       }
@@ -604,14 +607,14 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
       int la, lb;
       T xb;
       const int qi = klt(val(x0), in.yu) ? 3 : 4;
-      const int n = comb1(lines, x0, x1, vl[k], qi, in.seller, dec, la, xb, lb);
+      const int n = comb1(lines, in.y1, in.f1, x0, x1, vl[k], qi, in.seller, dec, la, xb, lb);
       for (int c = 0; c < n; ++c) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
         if (prev_l < 0) {
-          out.set_first(EmT<T>{in.y0, ln_eval(lines[l], in.y0), lines[l].s});
+          out.set_first(EmT<T>{in.y0, ln_eval(lines[l], in.y0, in.y1, in.f1), lines[l].s});
         } else if (dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1)) {
-          out.add_m(EmT<T>{x, ln_eval(lines[l], x), lines[l].s});
+          out.add_m(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s});
         }
         prev_l = l;
       }
