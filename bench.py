@@ -36,7 +36,7 @@ CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_batched<16, false> launch on the
 # 4096-option batch (ncu --metrics ..., one pass), the kernel as built from this source;
 # None when the kernel has changed since the counters were taken
-BATCHED_TRAFFIC = None
+BATCHED_TRAFFIC = 513273616640 + 1013414508288
 
 
 def parse():
