@@ -1,0 +1,106 @@
+// The level passes of paper_1110_2477_gb300/csrc (ob_tc.cuh, ob_adj.cuh) compiled for the
+// host with a one-lane team, for CPU tests of their logic: pricing (TcRun), the split of a
+// level over G teams (TcGroup, run phase by phase) and the adjoint (TcAdj).  Test
+// infrastructure only; the library itself runs these passes on the GPU.
+#include <cstring>
+#include <vector>
+
+#include "ob_adj.cuh"
+
+namespace {
+
+struct OneLane {
+  static constexpr int W = 1;
+  int lane() const { return 0; }
+  void sync() const {}
+  template <class T> T bcast0(T v) const { return v; }
+  template <class T> T prev(T, T carry) const { return carry; }
+  template <class T> T prev_last(T v, T carry, T& last) const { last = v; return carry; }
+  int count_le(int v, int q) const { return v <= q; }
+  void count_le2(int v, int q1, int q2, int& c1, int& c2) const { c1 = v <= q1; c2 = v <= q2; }
+  template <class T> void look2(T v, T c1, T c2, T& m1, T& m2, T& l1, T& l2) const {
+    m1 = c1; m2 = c2; l1 = v; l2 = c1;
+  }
+  int count(bool p) const { return p; }
+  bool any(bool p) const { return p; }
+  int excl_sum(int v, int& total) const { total = v; return 0; }
+  long long seg_min(long long v, bool head, long long& carry) const {
+    const long long r = head ? v : (v < carry ? v : carry);
+    carry = r;
+    return r;
+  }
+  void seg_argmin(long long& v, int& ix, bool head, long long& cv, int& ci) const {
+    if (!head && cv < v) { v = cv; ix = ci; }
+    cv = v;
+    ci = ix;
+  }
+  template <class T> T sum(T v) const { return v; }
+};
+
+std::vector<char> g_arena;
+
+char* arena(size_t bytes) {
+  if (g_arena.size() < bytes) g_arena.resize(bytes);
+  return g_arena.data();
+}
+
+}  // namespace
+
+extern "C" int hp_price(const obk::Opt* o, double* out, long long* pts) {
+  const size_t bytes = 256ull << 20;
+  OneLane tm;
+  obk::Lay L;
+  if (!obk::carve(arena(bytes), bytes, o->N, 16, L)) return obk::ST_CAPACITY;
+  obk::TcRun<OneLane> R(tm, *o, L);
+  const int rc = R.run(out[0], out[1]);
+  pts[0] = R.st.upts;
+  pts[1] = R.st.wpts;
+  pts[2] = R.st.zpts;
+  return rc;
+}
+
+extern "C" int hp_price_split(const obk::Opt* o, int G, double* out, long long* pts) {
+  const size_t shared_bytes = 64ull << 20, priv_bytes = 32ull << 20;
+  char* base = arena(shared_bytes + priv_bytes * (size_t)G);
+  std::memset(base, 0xff, shared_bytes + priv_bytes * (size_t)G);  // NaN: stale data shows
+  OneLane tm;
+  obk::GroupLay S;
+  if (!obk::carve_group_shared(base, shared_bytes, o->N, 2 * (o->N + 2), S)) return obk::ST_CAPACITY;
+  std::vector<obk::Lay> Lp(G);
+  std::vector<obk::TcGroup<OneLane>*> team(G);
+  for (int c = 0; c < G; ++c) {
+    if (!obk::carve(base + shared_bytes + priv_bytes * (size_t)c, priv_bytes, o->N, 16, Lp[c]))
+      return obk::ST_CAPACITY;
+    team[c] = new obk::TcGroup<OneLane>(tm, *o, Lp[c], S, G, c);
+  }
+  int rc = team[0]->begin();
+  for (int c = 1; c < G; ++c) team[c]->begin();
+  std::vector<int> cnt(G);
+  for (int t = o->N; t >= 0 && rc == obk::ST_OK; --t) {
+    for (int c = 0; c < G; ++c) cnt[c] = team[c]->compute(t) ? team[c]->ztot : -1;
+    for (int c = 0; c < G; ++c)
+      if (cnt[c] < 0) rc = obk::ST_CAPACITY;
+    for (int c = 0; c < G && rc == obk::ST_OK; ++c)
+      if (!team[c]->publish(t, cnt.data())) rc = obk::ST_CAPACITY;
+  }
+  if (rc == obk::ST_OK) team[0]->root(out[0], out[1]);
+  pts[0] = pts[1] = pts[2] = 0;
+  for (int c = 0; c < G; ++c) {
+    pts[0] += team[c]->R.st.upts;
+    pts[1] += team[c]->R.st.wpts;
+    pts[2] += team[c]->R.st.zpts;
+    delete team[c];
+  }
+  return rc;
+}
+
+extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad) {
+  const size_t bytes = 512ull << 20;
+  OneLane tm;
+  obk::Lay L;
+  obk::AdjLay A;
+  if (!obk::carve_greeks(arena(bytes), bytes, o->N, 2 * (o->N + 2), L, A)) return obk::ST_CAPACITY;
+  obk::TcRun<OneLane> R(tm, *o, L);
+  obk::TcAdj<OneLane> G(R, A);
+  return G.run(out[0], out[1], grad, grad + obk::NPAR);
+}

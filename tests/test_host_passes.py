@@ -1,0 +1,94 @@
+"""The kernel's level passes compiled for the host with a one-lane team (tests/host_passes.cpp)
+against the oracle: prices at the parity tolerance, the same points whether a level is split
+over 1 or G teams (bitwise), and the adjoint against the oracle's dual-number gradient.  This
+checks the passes' logic (merge with owner handoff, running minima, restriction and exercise
+per piece, the split of a level, the reverse sweep) without a GPU."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+RTOL = 1e-10
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        out = os.path.join(tempfile.mkdtemp(prefix="hostpasses"), "libhostpasses.so")
+        src = os.path.join(ROOT, "tests", "host_passes.cpp")
+        inc = os.path.join(ROOT, "paper_1110_2477_gb300", "csrc")
+        r = subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", inc, "-o", out, src],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.fail("g++ failed: " + r.stderr[-2000:])
+        _LIB = ctypes.CDLL(out)
+    return _LIB
+
+
+def _rec(row):
+    return np.ascontiguousarray(np.array([row], dtype=W.OPTION_DTYPE))
+
+
+def _price(row, G=0):
+    a = _rec(row)
+    out = np.zeros(2)
+    pts = np.zeros(3, np.int64)
+    P = ctypes.c_void_p
+    if G:
+        rc = _lib().hp_price_split(a.ctypes.data_as(P), G, out.ctypes.data_as(P), pts.ctypes.data_as(P))
+    else:
+        rc = _lib().hp_price(a.ctypes.data_as(P), out.ctypes.data_as(P), pts.ctypes.data_as(P))
+    return rc, out, pts
+
+
+def _table():
+    return W.concat(W.random_table(24, 31000, N_lo=1, N_hi=90, k_hi=0.05),
+                    W.make(S0=100, K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=60, payoff=W.SPREAD),
+                    W.make(S0=100, K=100, sigma=0.1, T=0.1, k=0.02, N=60, payoff=W.CALL),
+                    W.make(k=0.0, N=40), W.make(k=0.01, N=1), W.make(R=5.0, N=2, T=1.0))
+
+
+def test_host_passes_match_oracle():
+    t = _table()
+    ref, rst = oracle.price_ask_bid(t, nthreads=4)
+    for i in range(len(t)):
+        rc, out, _ = _price(t[i])
+        assert rc == rst[i], (i, rc, rst[i])
+        if rc == 0:
+            scale = np.maximum(np.abs(ref[i]), 1e-2 * t["K"][i])
+            assert np.all(np.abs(out - ref[i]) <= RTOL * scale), (i, out, ref[i])
+
+
+@pytest.mark.parametrize("G", [2, 3, 16])
+def test_level_split_over_teams_is_bitwise_equal(G):
+    t = _table()
+    for i in range(len(t)):
+        rc1, out1, pts1 = _price(t[i])
+        rc2, out2, pts2 = _price(t[i], G)
+        assert rc1 == rc2
+        if rc1 == 0:
+            assert np.array_equal(out1.view(np.int64), out2.view(np.int64))
+            assert np.array_equal(pts1, pts2)
+
+
+def test_host_adjoint_matches_dual_gradient():
+    t = W.random_table(6, 31500, N_lo=2, N_hi=50)
+    t["k"] = np.maximum(t["k"], 1e-4)
+    rout, rgrad, rst = oracle.greeks(t, nthreads=3)
+    P = ctypes.c_void_p
+    for i in range(len(t)):
+        a = _rec(t[i])
+        out = np.zeros(2)
+        grad = np.zeros(12)
+        rc = _lib().hp_greeks(a.ctypes.data_as(P), out.ctypes.data_as(P), grad.ctypes.data_as(P))
+        assert rc == rst[i] == 0
+        scale = np.maximum(np.abs(rgrad[i].reshape(-1)), 1e-3 * t["K"][i])
+        assert np.all(np.abs(grad - rgrad[i].reshape(-1)) <= 1e-6 * scale), (i, grad, rgrad[i])
