@@ -68,14 +68,18 @@ enum {
  *           option's error code; an option that fails leaves NaN in out and
  *           does not stop the others.
  *   stream  cudaStream_t (NULL = legacy default stream).
- * Batched form: one persistent launch whose warps take options from a device
- * queue, costliest first (work stealing); options whose functions outgrow a
- * warp's scratch are retried by follow-up launches with larger scratch, on
- * the same stream, without returning to the host.  Asynchronous: returns
- * OB_OK once the work is enqueued, or an error code (nothing enqueued) for
- * bad arguments, allocation failure or a launch error.  The library's scratch
- * pool is allocated on the first call on a device (cudaMalloc, so make that
- * call before any stream capture) and kept until ob_release(). */
+ * Batched form: one persistent launch whose CTAs take options from a device
+ * queue, costliest first (work stealing), each option on a whole-CTA team (one
+ * 512-thread CTA per SM by default, see ob_configure); options whose functions
+ * outgrow a CTA's scratch are retried by follow-up launches with larger
+ * scratch, on the same stream, without returning to the host.  The launch
+ * sequence is captured in a CUDA graph per (params, n_options, out, status)
+ * and replayed when the same buffers come back (it reads their current
+ * contents).  Asynchronous: returns OB_OK once the work is enqueued, or an
+ * error code (nothing enqueued) for bad arguments, allocation failure or a
+ * launch error.  The library's scratch pool is allocated on the first call on
+ * a device (cudaMalloc, so make that call before any stream capture) and kept
+ * until ob_release(). */
 int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                      void* stream);
 

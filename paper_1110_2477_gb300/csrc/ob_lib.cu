@@ -1,13 +1,17 @@
 // ob_lib.cu -- kernels and the C ABI declared in include/ob.h.
 //
-//  k_order  one CTA sorts the option indices by estimated cost (largest first)
-//  k_tc     persistent warps: each warp takes an option from a device queue and
-//           runs the piecewise-linear induction (ob_tc.cuh) in its own slice of
-//           the scratch pool; an option that outgrows the slice is appended to
-//           an overflow list that the next launch (fewer warps, larger slices)
-//           takes over, on the same stream
-//  k_crr    persistent warps: plain CRR recursion without costs, the level kept
-//           in shared memory and updated in place
+//  k_order        one CTA sorts the option indices by predicted cost (largest first)
+//  k_tc_batched   persistent CTAs: each takes options from a device queue and runs the
+//                 piecewise-linear induction (ob_tc.cuh) on a whole-CTA team in its own
+//                 slice of the scratch pool; an option that outgrows the slice goes to an
+//                 overflow list that the follow-up launches (k_tc_retry: 16 CTAs, then one,
+//                 larger slices) take over on the same stream
+//  k_tc_plain     one warp per option in index order (the comparison kernel)
+//  k_tc_group     one cooperative launch of a CTA per SM: each option in turn, every level
+//                 split over all CTAs (TcGroup), bounded grid barriers
+//  k_greeks_team  the adjoint (ob_adj.cuh) on CTA teams, with warp and retry variants
+//  k_crr          persistent warps: plain CRR recursion without costs, the level kept in
+//                 shared memory and updated in place
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>

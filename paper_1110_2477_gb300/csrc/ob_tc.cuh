@@ -2,8 +2,8 @@
 // buyer's (bid) piecewise-linear functions on a recombining binomial tree
 // (Zhang, Roux & Zastawniak, Section 3 and Section 4.1; the sequential
 // procedures are Roux & Zastawniak's Algorithms 3.1 and 3.5), written as
-// element-parallel passes for one team of threads (a warp) working on one
-// option.
+// element-parallel passes for one team of threads (a warp or a whole CTA) working
+// on one option; TcGroup at the end splits each level over several teams.
 //
 // Representation.  A node function is a list of breakpoints (y, value,
 // slope to the right of y).  Its left-tail slope is always -S^a_t and its
