@@ -13,6 +13,11 @@ host cores on a bounded sample of the same workload.
 Under torchrun each rank prices its own batch of the same distribution
 (weak scaling, no collective on the data path); the max over ranks of the
 timed region sets the job time.
+
+Other workloads (--workload): small (48 options, for profiler captures), crr
+(65536 CRR puts at N = 2048 and one put at N = 20000), paper (18 paper-scale
+single options, one per launch on the whole GPU), greeks (1024 puts, prices
+and the 12 derivatives; --options n for a smaller case).
 """
 import argparse
 import json
