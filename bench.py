@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "tree node updates/s (ask+bid, FP64) batched; options/s with Greeks vs plain"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 dense FP64 (profiling recipe); see the design doc
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 dense FP64: 152 SMs x 2.07 GHz x 2 DFMA lanes x 2 flops
 CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_batched<16, false> launch on the
 # 4096-option batch (ncu --metrics ..., one pass), the kernel as built from this source;

@@ -214,6 +214,16 @@ const char* ob_strerror(int code);
 /* The CUDA error string of the last OB_ERR_CUDA returned on this thread. */
 const char* ob_last_cuda_error(void);
 
+/* Measurement helper (the paper has no counterpart): the device's FP64 fused
+ * multiply-add throughput, the denominator of the FP64 rooflines the benchmark
+ * reports.  One launch of 8 CTAs of 256 threads per SM, each thread running 8
+ * independent chains of `iters` DFMAs (2 flops each), timed with CUDA events on
+ * stream; three runs, the fastest of the last two is kept.  Synchronous.
+ *   tflops_out  HOST pointer: measured TFLOP/s.
+ *   ms_out      HOST pointer (may be NULL): the kept run's milliseconds.
+ * Returns OB_ERR_ARG for iters <= 0 or a NULL tflops_out. */
+int ob_fp64_peak(int64_t iters, void* stream, double* tflops_out, double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@
 //  * Forward-mode dual numbers through the same induction give the
 //    derivatives of ask and bid with respect to (S0, K, sigma, R, T, k).
 //
-// Readings of the paper taken here (each is also listed in the design doc):
+// Readings of the paper taken here:
 //  * "restricting the slopes" of w_t/r to [-S^a_t, -S^b_t] is the
 //    inf-convolution v(y) = inf_{y'} [ w(y')/r + theta(y'-y) ], with
 //    theta(x) = S^a x for x >= 0 and S^b x for x < 0: the cheapest way to

@@ -29,7 +29,7 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
            "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune",
-           "ob_price_ask_bid_wide")
+           "ob_price_ask_bid_wide", "ob_fp64_peak")
 
 
 class ObStats(ctypes.Structure):
@@ -69,6 +69,8 @@ def load():
         lib.ob_autotune.argtypes = [P, i64, i64, P, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_float)]
         lib.ob_autotune.restype = ctypes.c_int
+        lib.ob_fp64_peak.argtypes = [i64, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.ob_fp64_peak.restype = ctypes.c_int
         lib.ob_release.argtypes = []
         lib.ob_release.restype = ctypes.c_int
         lib.ob_strerror.argtypes = [ctypes.c_int]
@@ -157,6 +159,13 @@ def ob_get_stats() -> dict:
     s = ObStats()
     _check(load().ob_get_stats(ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in ObStats._fields_}
+
+
+def ob_fp64_peak(iters=1 << 16, stream=None):
+    """Measured FP64 FMA throughput of the device: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().ob_fp64_peak(int(iters), _stream(stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return float(tf.value), float(ms.value)
 
 
 def ob_release():

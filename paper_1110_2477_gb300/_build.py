@@ -5,7 +5,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "ob_lib.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("ob_tc.cuh", "ob_team.cuh")] + [
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("ob_tc.cuh", "ob_team.cuh", "ob_adj.cuh")] + [
     os.path.join(ROOT, "include", "ob.h")]
 LIB = os.path.join(HERE, "libob.so")
 

@@ -130,9 +130,10 @@ __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int*
 }
 
 // ------------------------------------------------------------------ induction with costs
-template <class Team>
+template <class Team, bool CHIP = false>
 __device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
-                                          int& rc, double& ask, double& bid, obk::Stats& st) {
+                                          int& rc, double& ask, double& bid, obk::Stats& st,
+                                          const obk::WBuf* chip = nullptr) {
   rc = check_option(o, true);
   ask = dnan();
   bid = dnan();
@@ -144,7 +145,8 @@ __device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, cha
     rc = obk::ST_CAPACITY;
     return;
   }
-  obk::TcRun<Team> R(tm, o, L);
+  obk::TcRun<Team, CHIP> R(tm, o, L);
+  if (CHIP) R.chip = *chip;
   rc = R.run(ask, bid);
   st = R.st;
 }
@@ -179,12 +181,16 @@ __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, c
 // Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
 // one at a time as a whole-CTA team, then each of its warps takes the remaining
 // options one at a time from a second queue.  Both queues are device counters.
-template <int NW, bool WARPS>
+// CHIP: the CTA's dynamic shared memory holds the w arrays of chip_points points (the
+// fused level step of CTA teams, TcRun::level_fused).
+template <int NW, bool WARPS, bool CHIP = false>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
-    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds) {
+    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds, int chip_points) {
   __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+  extern __shared__ __align__(16) char chip_smem[];
   obk::BlockTeam<NW> bt{tbuf};
+  const obk::WBuf chip = obk::carve_wbuf(chip_smem, chip_points);
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
   const int nh = order ? *((volatile int*)&ctl[C_NHEAVY]) : 0;
   for (;;) {
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     int rc;
     double ask, bid;
     obk::Stats st;
-    price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
+    price_one<obk::BlockTeam<NW>, CHIP>(bt, o, my, cta_bytes, rc, ask, bid, st, &chip);
     if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
     bt.sync();
   }
@@ -271,8 +277,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Barrier of all CTAs of the grid.  Thread 0 publishes with a fence and an atomic
 // arrival, the last arrival releases the others by bumping the generation; a wait
-// longer than kGroupWaitNs (or 2^30 polls) sets err.  Returns false once err is set.
-__device__ bool grid_barrier(GroupState* gs, unsigned& gen) {
+// longer than wait_ns (or 2^30 polls) sets err.  Returns false once err is set.
+__device__ bool grid_barrier(GroupState* gs, unsigned& gen, unsigned long long wait_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -290,7 +296,7 @@ __device__ bool grid_barrier(GroupState* gs, unsigned& gen) {
         for (unsigned it = 0;; ++it) {
           if (*((volatile unsigned*)&gs->gen) == want) break;
           if (*((volatile int*)&gs->err) != 0) { ok = 0; break; }
-          if (it > (1u << 30) || global_ns() - t0 > kGroupWaitNs) {
+          if (it > (1u << 30) || global_ns() - t0 > wait_ns) {
             atomicExch(&gs->err, 1);
             ok = 0;
             break;
@@ -309,11 +315,15 @@ __device__ bool grid_barrier(GroupState* gs, unsigned& gen) {
 
 __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
-    size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds) {
+    size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds, unsigned long long wait_ns,
+    int skip_cta) {
   __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
   __shared__ int s_cnt[kGroupMax];
   obk::BlockTeam<kGroupNW> bt{tbuf};
   const int G = gridDim.x, c = blockIdx.x;
+  // test control: this CTA never arrives at any barrier, so the others' bounded waits
+  // run out and every option of the call reports OB_ERR_TIMEOUT
+  if (c == skip_cta) return;
   char* mine = arena + shared_bytes + (size_t)c * cta_bytes;
   unsigned gen = 0;
   for (int oi = 0; oi < n; ++oi) {
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     double ask = dnan(), bid = dnan();
     obk::Stats st;
     st.upts = st.wpts = st.zpts = 0;
-    st.zmax_level = st.zmax_node = 0;
+    st.zmax_level = 0;
     obk::GroupLay S;
     obk::Lay Lp;
     if (rc == obk::ST_OK && (!obk::carve_group_shared(arena, shared_bytes, o.N, 2 * (o.N + 2), S) ||
@@ -331,11 +341,11 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     if (rc == obk::ST_OK) {
       obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
       rc = g.begin();
-      if (rc == obk::ST_OK && !grid_barrier(gs, gen)) rc = ST_TIMEOUT;
+      if (rc == obk::ST_OK && !grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
       for (int t = o.N; t >= 0 && rc == obk::ST_OK; --t) {
         const bool ok = g.compute(t);
         if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? g.ztot : -1;
-        if (!grid_barrier(gs, gen)) { rc = ST_TIMEOUT; break; }
+        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
         int bad = 0;
         for (int k = threadIdx.x; k < G; k += blockDim.x) {
           s_cnt[k] = __ldcg(&gs->cnt[t & 1][k]);
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
         }
         if (__syncthreads_or(bad)) { rc = obk::ST_CAPACITY; break; }
         if (!g.publish(t, s_cnt)) { rc = obk::ST_CAPACITY; break; }
-        if (!grid_barrier(gs, gen)) { rc = ST_TIMEOUT; break; }
+        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
       }
       if (rc == obk::ST_OK && c == 0) g.root(ask, bid);
       st = g.R.st;
@@ -577,6 +587,23 @@ __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opt
   }
 }
 
+// ------------------------------------------------------------------ FP64 throughput probe
+// Each thread runs kProbeChains independent chains of a = a * b + c (one DFMA each),
+// so the FP64 pipe, not latency, bounds the loop; the result is written so that the
+// compiler keeps every chain.  2 flops per DFMA.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) k_fp64_probe(long long iters, double b, double c, double* sink) {
+  double a[kProbeChains];
+  for (int i = 0; i < kProbeChains; ++i) a[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+  for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kProbeChains; ++i) a[i] = fma(a[i], b, c);
+  }
+  double t = 0.0;
+  for (int i = 0; i < kProbeChains; ++i) t += a[i];
+  if (t == 12345.678) sink[0] = t;  // never true for b, c near 1 and 0
+}
+
 // Every stride-th option, for the autotuner's sample.
 __global__ void k_gather(const obk::Opt* __restrict__ src, int n, int stride, int m, obk::Opt* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,11 +633,22 @@ struct GraphEntry {
 };
 constexpr int kGraphCache = 4;
 
+// Scratch budgets.  The pool is one device allocation that grows to the largest
+// need of any call so far (never shrinks before ob_release); OB_POOL_MB fixes its size.
+constexpr size_t kMinArena = 1ull << 30;          // smallest pool (room for the retry tiers)
+constexpr size_t kPlainWarpBytes = 8ull << 20;    // per warp of the one-warp-per-option form
+constexpr size_t kCrrWarpBytes = 512ull << 10;    // per warp of the CRR kernel
+constexpr size_t kGreeksSmBytes = 128ull << 20;   // per SM of the Greeks form (level store)
+
 struct DevPool {
   bool init = false;
   int sms = 0;
   int warps_per_sm = 16;
-  size_t arena_per_warp = 8ull << 20;
+  size_t sm_bytes = 32ull << 20;  // first-tier scratch per SM of the batched form
+  int smem_sm = 0;                // shared memory per SM and the largest per CTA (bytes)
+  int smem_cta = 0;
+  int chip_req = 0;               // on-chip w points per CTA (-1 all that fit, 0 off; OB_CHIP_POINTS)
+  size_t fixed_bytes = 0;         // OB_POOL_MB: the pool has exactly this size
   double heavy_factor = kHeavyFactor;
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
   int greeks_team = 8;  // Greeks: warps per CTA team (4 or 8); 0: one warp per option
@@ -636,15 +674,22 @@ struct DevPool {
   int last_graph = 0;  // 0 direct launches, 1 captured now, 2 replayed
   GroupState* gstate = nullptr;  // whole-GPU form
   int group_ctas = 0;
+  unsigned long long wide_wait_ns = kGroupWaitNs;  // bound of one grid-barrier wait
+  int test_skip_calls = 0;  // OB_TEST_WIDE_SKIP: calls in which one CTA never arrives
   // autotuner sample buffers
   obk::Opt* tune_params = nullptr;
   double* tune_out = nullptr;
   int* tune_status = nullptr;
   int tune_cap = 0;
+  // ordering of calls: each call's work waits for the previous call's on the device
+  cudaEvent_t order_ev = nullptr;
+  bool order_valid = false;
 };
 
 std::mutex g_mu;
 std::mutex g_graph_mu;
+std::mutex g_call_mu[64];  // one enqueue at a time per device
+std::mutex g_host_mu[64];  // one host-buffer call at a time per device
 DevPool g_pool[64];
 
 size_t env_size(const char* name, size_t dflt) {
@@ -654,7 +699,28 @@ size_t env_size(const char* name, size_t dflt) {
   return v > 0 ? (size_t)v : dflt;
 }
 
-int pool_get(DevPool** out, size_t need_list) {
+void drop_graphs(DevPool* P);
+
+// Dynamic shared memory a CTA of NW warps can take for the on-chip w arrays: its share
+// of the SM (16 / NW CTAs per SM; 1 KiB per CTA is reserved by the system) less the
+// team's exchange area, capped by the per-CTA limit.
+int chip_smem_cap(int smem_sm, int smem_cta, int nw) {
+  const int per_sm = 16 / nw;
+  int b = smem_sm / per_sm - 1024 - (int)sizeof(long long) * 2 * (32 * nw + 4 * nw + 8);
+  const int lim = smem_cta - (int)sizeof(long long) * 2 * (32 * nw + 4 * nw + 8);
+  if (b > lim) b = lim;
+  return b > 0 ? b & ~255 : 0;
+}
+
+// Points of the on-chip w arrays for teams of nw warps (0: the fused step is off).
+int chip_points(const DevPool* P, int nw) {
+  const int fit = chip_smem_cap(P->smem_sm, P->smem_cta, nw) / obk::WBUF_POINT_BYTES;
+  if (P->chip_req < 0) return fit;
+  return P->chip_req < fit ? P->chip_req : fit;
+}
+
+// The pool of the current device, initialised on first use (no scratch yet).
+int pool_get(DevPool** out, int* dev_out = nullptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -665,7 +731,8 @@ int pool_get(DevPool** out, size_t need_list) {
     e = cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e);
     P.warps_per_sm = (int)env_size("OB_WARPS_PER_SM", 16);
-    P.arena_per_warp = env_size("OB_ARENA_MB", 8) << 20;
+    P.sm_bytes = (env_size("OB_ARENA_MB", 2) << 20) * 16;  // OB_ARENA_MB: MiB per warp slot
+    P.fixed_bytes = env_size("OB_POOL_MB", 0) << 20;
     if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
     if (const char* tw = getenv("OB_TEAM_WARPS")) {
       const int v = atoi(tw);
@@ -673,15 +740,18 @@ int pool_get(DevPool** out, size_t need_list) {
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
     if (const char* g = getenv("OB_GREEKS_TEAM")) P.greeks_team = atoi(g);
-    const size_t workers = (size_t)P.sms * P.warps_per_sm;
-    P.arena_bytes = workers * P.arena_per_warp;
-    const size_t pool_mb = env_size("OB_POOL_MB", 0);  // optional cap on the whole pool
-    if (pool_mb) P.arena_bytes = pool_mb << 20;
-    if (cudaMalloc(&P.arena, P.arena_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      P.arena = nullptr;
-      return OB_ERR_NOMEM;
-    }
+    P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
+    P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
+    if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
+    if ((e = cudaDeviceGetAttribute(&P.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+            cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&P.smem_cta, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = cudaFuncSetAttribute(k_tc_batched<16, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  chip_smem_cap(P.smem_sm, P.smem_cta, 16))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_tc_batched<8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  chip_smem_cap(P.smem_sm, P.smem_cta, 8))) != cudaSuccess)
+      return cuda_fail(e);
     if (cudaMalloc(&P.ctl, sizeof(int) * C_WORDS) != cudaSuccess ||
         cudaMalloc(&P.order, sizeof(int) * kSortMax) != cudaSuccess ||
         cudaMalloc(&P.stats, sizeof(DevStats)) != cudaSuccess) {
@@ -689,6 +759,8 @@ int pool_get(DevPool** out, size_t need_list) {
       return OB_ERR_NOMEM;
     }
     cudaMemset(P.stats, 0, sizeof(DevStats));
+    if ((e = cudaEventCreateWithFlags(&P.order_ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e);
     e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(unsigned long long) * kSortMax));
     if (e != cudaSuccess) return cuda_fail(e);
@@ -697,18 +769,82 @@ int pool_get(DevPool** out, size_t need_list) {
     if (e != cudaSuccess) return cuda_fail(e);
     P.init = true;
   }
-  if (need_list > P.list_cap) {
-    if (P.lists) cudaFree(P.lists);
-    P.lists = nullptr;
-    P.list_cap = 0;
-    if (cudaMalloc(&P.lists, sizeof(int) * 2 * need_list) != cudaSuccess) {
+  *out = &P;
+  if (dev_out) *dev_out = dev;
+  return OB_OK;
+}
+
+// Make room for a call: overflow lists of need_list entries and a scratch pool of at
+// least need_arena bytes (at least kMinArena; exactly OB_POOL_MB when that is set).
+// Growing synchronises the device first (work in flight may use the old buffers) and
+// drops the cached graphs (they hold the old addresses).  The caller holds g_call_mu.
+int pool_reserve(DevPool* P, size_t need_list, size_t need_arena) {
+  if (need_arena < kMinArena) need_arena = kMinArena;
+  if (P->fixed_bytes) need_arena = P->fixed_bytes;
+  const bool grow_list = need_list > P->list_cap;
+  const bool grow_arena = P->fixed_bytes ? (P->arena == nullptr) : need_arena > P->arena_bytes;
+  if (!grow_list && !grow_arena) return OB_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e);
+  drop_graphs(P);
+  if (grow_list) {
+    cudaFree(P->lists);
+    P->lists = nullptr;
+    P->list_cap = 0;
+    if (cudaMalloc(&P->lists, sizeof(int) * 2 * need_list) != cudaSuccess) {
       cudaGetLastError();
       return OB_ERR_NOMEM;
     }
-    P.list_cap = need_list;
+    P->list_cap = need_list;
   }
-  *out = &P;
+  if (grow_arena) {
+    cudaFree(P->arena);
+    P->arena = nullptr;
+    P->arena_bytes = 0;
+    if (cudaMalloc(&P->arena, need_arena) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+    P->arena_bytes = need_arena;
+  }
   return OB_OK;
+}
+
+// Calls on one device are ordered on the GPU in the order they were made: a call's
+// first operation waits for the previous call's last one (an event), whatever streams
+// they use, so concurrent calls never share the queue words, lists and scratch.  Not
+// applied while the caller's stream is being captured into a graph (an event from
+// outside the capture cannot be waited on there); such calls are ordered by the caller.
+struct CallOrder {
+  DevPool* P;
+  cudaStream_t s;
+  bool on = false;
+  int begin() {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e);
+    on = cs == cudaStreamCaptureStatusNone;
+    if (on && P->order_valid && (e = cudaStreamWaitEvent(s, P->order_ev, 0)) != cudaSuccess)
+      return cuda_fail(e);
+    return OB_OK;
+  }
+  int end() {
+    if (!on) return OB_OK;
+    cudaError_t e = cudaEventRecord(P->order_ev, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    P->order_valid = true;
+    return OB_OK;
+  }
+};
+
+// Scratch of the batched form for a call of n options: the first tier's CTAs and the
+// bytes each gets (the per-SM budget split over the CTAs of an SM).
+int batched_ctas(const DevPool* P, int n) {
+  const int nctas = P->sms * (16 / P->team_warps);
+  return n < nctas ? n : nctas;
+}
+size_t batched_need(const DevPool* P, int n) {
+  return (size_t)batched_ctas(P, n) * (P->sm_bytes / (16 / P->team_warps));
 }
 
 int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
@@ -723,28 +859,41 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   if (!params || !out) return OB_ERR_ARG;
   const int n = (int)n64;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, (size_t)n);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   const obk::Opt* opts = (const obk::Opt*)params;
   if (plain) {
-    if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
     const int max_workers = P->sms * P->warps_per_sm;
     const int workers = n < max_workers ? n : max_workers;
-    const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
+    if ((rc = pool_reserve(P, 1, (size_t)workers * kPlainWarpBytes))) return rc;
+    CallOrder co{P, s};
+    if ((rc = co.begin())) return rc;
+    if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
+    size_t wbytes = P->arena_bytes / (size_t)workers;
+    if (wbytes > kPlainWarpBytes) wbytes = kPlainWarpBytes;
+    wbytes &= ~(size_t)255;
     const int blocks = (workers * 32 + kBlock - 1) / kBlock;
     k_tc_plain<<<blocks, kBlock, 0, s>>>(opts, n, out, status, P->arena, wbytes, workers, P->stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     P->last_tiers = 1;
     P->last_graph = 0;
-    return OB_OK;
+    return co.end();
   }
+  if ((rc = pool_reserve(P, (size_t)n, batched_need(P, n)))) return rc;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
   if (!P->use_graphs) {
     P->last_graph = 0;
-    return enqueue_batched(P, opts, n, out, status, s);
+    rc = enqueue_batched(P, opts, n, out, status, s);
+  } else {
+    rc = launch_graph(P, opts, n, out, status, s);
   }
-  return launch_graph(P, opts, n, out, status, s);
+  if (rc) return rc;
+  return co.end();
 }
 
 // The batched launch sequence: reset the queue words and counters, order the options
@@ -755,7 +904,7 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
   cudaError_t e;
   if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
-  const int nctas = P->sms * (16 / P->team_warps);
+  const int nctas = batched_ctas(P, n);
   const int* order = nullptr;
   if (n <= kSortMax) {
     int npad = 1;
@@ -766,18 +915,29 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
-  const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
+  size_t cta_bytes = P->arena_bytes / (size_t)nctas;
+  if (cta_bytes > P->sm_bytes / (16 / P->team_warps)) cta_bytes = P->sm_bytes / (16 / P->team_warps);
+  cta_bytes &= ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
   // with a heavy factor of 0 every option goes to a CTA team and the kernel leaves out
   // the warp-team loop (and its registers); without the cost order, warps take them all
   const bool warps = P->heavy_factor > 0.0 || !order;
-#define OB_LAUNCH_BATCHED(NWV)                                                                    \
-  (warps ? k_tc_batched<NWV, true><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena, \
-                                                                cta_bytes, P->ctl, list0, P->stats) \
+  // the on-chip w arrays of the fused level step (CTA teams of 16 or 8 warps only)
+  const int chip = (warps || (P->team_warps != 16 && P->team_warps != 8)) ? 0 : chip_points(P, P->team_warps);
+  const size_t chip_bytes = (size_t)chip * obk::WBUF_POINT_BYTES;
+#define OB_LAUNCH_BATCHED(NWV)                                                                      \
+  (warps ? k_tc_batched<NWV, true><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena,  \
+                                                              cta_bytes, P->ctl, list0, P->stats, 0) \
          : k_tc_batched<NWV, false><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena, \
-                                                                 cta_bytes, P->ctl, list0, P->stats))
-  if (P->team_warps == 4)
+                                                               cta_bytes, P->ctl, list0, P->stats, 0))
+  if (chip > 0 && P->team_warps == 16)
+    k_tc_batched<16, false, true><<<nctas, 512, chip_bytes, s>>>(opts, n, order, out, status, P->arena,
+                                                                 cta_bytes, P->ctl, list0, P->stats, chip);
+  else if (chip > 0)
+    k_tc_batched<8, false, true><<<nctas, 256, chip_bytes, s>>>(opts, n, order, out, status, P->arena,
+                                                                cta_bytes, P->ctl, list0, P->stats, chip);
+  else if (P->team_warps == 4)
     OB_LAUNCH_BATCHED(4);
   else if (P->team_warps == 12)
     OB_LAUNCH_BATCHED(12);
@@ -911,12 +1071,13 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
   if (n_options == 0) return OB_OK;
   if (!params || !out) return OB_ERR_ARG;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, 1);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   cudaError_t e;
   if (!P->gstate) {
-    int per_sm = 0, coop = 0, dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    int per_sm = 0, coop = 0;
     if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess)
       return cuda_fail(e);
     if (!coop) return OB_ERR_CUDA;
@@ -932,7 +1093,10 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
     }
     P->group_ctas = G;
   }
+  if ((rc = pool_reserve(P, 1, (size_t)P->sms * P->sm_bytes))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
   if ((e = cudaMemsetAsync(P->gstate, 0, sizeof(GroupState), s)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
   const int G = P->group_ctas;
@@ -943,14 +1107,21 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
   char* arena = P->arena;
   GroupState* gs = P->gstate;
   DevStats* ds = P->stats;
+  unsigned long long wait_ns = P->wide_wait_ns;
+  int skip_cta = -1;
+  if (P->test_skip_calls > 0) {
+    --P->test_skip_calls;
+    skip_cta = G - 1;
+  }
   void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
-                  (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds};
+                  (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds, (void*)&wait_ns,
+                  (void*)&skip_cta};
   if ((e = cudaLaunchCooperativeKernel((const void*)k_tc_group, dim3(G), dim3(32 * kGroupNW), args, 0,
                                        s)) != cudaSuccess)
     return cuda_fail(e);
   P->last_tiers = 1;
   P->last_graph = 0;
-  return OB_OK;
+  return co.end();
 }
 
 int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
@@ -960,19 +1131,26 @@ int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, i
   if (!params || !out) return OB_ERR_ARG;
   const int n = (int)n_options;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, 1);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   const int max_workers = P->sms * 12;  // 3 CTAs of 4 warps per SM fit the shared memory
   const int workers = n < max_workers ? n : max_workers;
-  const size_t wbytes = (P->arena_bytes / (size_t)workers) & ~(size_t)255;
+  if ((rc = pool_reserve(P, 1, (size_t)workers * kCrrWarpBytes))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
+  size_t wbytes = P->arena_bytes / (size_t)workers;
+  if (wbytes > kCrrWarpBytes) wbytes = kCrrWarpBytes;
+  wbytes &= ~(size_t)255;
   const int blocks = (workers * 32 + kBlock - 1) / kBlock;
   k_crr<<<blocks, kBlock, sizeof(double) * kCrrSmem * (kBlock / 32), s>>>(
       (const obk::Opt*)params, n, out, status, P->arena, wbytes, workers, P->ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  return OB_OK;
+  return co.end();
 }
 
 int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad, int32_t* status,
@@ -982,29 +1160,34 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   if (!params || !out || !grad) return OB_ERR_ARG;
   const int n = (int)n_options;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, (size_t)n);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
+  const int gteam = P->greeks_team;
+  const bool teams = gteam == 4 || gteam == 8;
+  const int per_sm = teams ? 8 / gteam : 8;  // CTA teams, or warps of the one-warp form
+  const int max_workers = P->sms * per_sm;
+  const int workers = n < max_workers ? n : max_workers;
+  if ((rc = pool_reserve(P, (size_t)n, (size_t)workers * (kGreeksSmBytes / per_sm)))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
   cudaError_t e;
   if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   const obk::Opt* opts = (const obk::Opt*)params;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
-  const int gteam = P->greeks_team;
-  if (gteam == 4 || gteam == 8) {
-    const int nctas = P->sms * (8 / gteam);
-    const size_t cta_bytes = (P->arena_bytes / (size_t)nctas) & ~(size_t)255;
-    if (gteam == 4)
-      k_greeks_team<4><<<nctas, 128, 0, s>>>(opts, n, out, grad, status, P->arena, cta_bytes, P->ctl, list0);
-    else
-      k_greeks_team<8><<<nctas, 256, 0, s>>>(opts, n, out, grad, status, P->arena, cta_bytes, P->ctl, list0);
-  } else {
-    const int max_workers = P->sms * 8;
-    const int workers = n < max_workers ? n : max_workers;
-    const size_t wbytes = (P->arena_bytes / (size_t)max_workers) & ~(size_t)255;
+  size_t wbytes = P->arena_bytes / (size_t)workers;
+  if (wbytes > kGreeksSmBytes / per_sm) wbytes = kGreeksSmBytes / per_sm;
+  wbytes &= ~(size_t)255;
+  if (gteam == 4)
+    k_greeks_team<4><<<workers, 128, 0, s>>>(opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
+  else if (gteam == 8)
+    k_greeks_team<8><<<workers, 256, 0, s>>>(opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
+  else
     k_greeks<<<(workers * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(opts, n, out, grad, status, P->arena,
                                                                      wbytes, workers, P->ctl, list0);
-  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   k_greeks_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, t1_bytes,
@@ -1015,7 +1198,7 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
                                           &P->ctl[C_T1_OVF], list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF],
                                           nullptr, 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  return OB_OK;
+  return co.end();
 }
 
 int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* out,
@@ -1024,11 +1207,13 @@ int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* 
   if (n_options == 0) return OB_OK;
   if (!params || !out) return OB_ERR_ARG;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, (size_t)n_options);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
   cudaError_t e;
+  // one host-buffer call at a time per device: the staging buffers are shared
+  std::lock_guard<std::mutex> hl(g_host_mu[dev]);
   {
-    std::lock_guard<std::mutex> lk(g_mu);
     if (!P->hstream) {
       if ((e = cudaStreamCreateWithFlags(&P->hstream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e);
@@ -1066,7 +1251,7 @@ int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* 
 int ob_get_stats(ob_stats_t* host_out) {
   if (!host_out) return OB_ERR_ARG;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, 1);
+  int rc = pool_get(&P);
   if (rc) return rc;
   DevStats d;
   cudaError_t e = cudaMemcpy(&d, P->stats, sizeof(d), cudaMemcpyDeviceToHost);
@@ -1089,8 +1274,10 @@ int ob_configure(int32_t team_warps, int32_t use_graphs) {
   if (team_warps != 0 && team_warps != 4 && team_warps != 8 && team_warps != 12 && team_warps != 16)
     return OB_ERR_ARG;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, 1);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   if (team_warps) P->team_warps = team_warps;
   if (use_graphs >= 0) P->use_graphs = use_graphs != 0;
   drop_graphs(P);
@@ -1104,9 +1291,22 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
   int m = (int)(sample > 0 && sample < n_options ? sample : n_options);
   const int stride = n / m;
   DevPool* P = nullptr;
-  int rc = pool_get(&P, (size_t)m);
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
   if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
+  const int keep = P->team_warps;
+  size_t need = 0;
+  for (int tw : {16, 12, 8, 4}) {
+    P->team_warps = tw;
+    const size_t b = batched_need(P, m);
+    if (b > need) need = b;
+  }
+  P->team_warps = keep;
+  if ((rc = pool_reserve(P, (size_t)m, need))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
   cudaError_t e;
   if (m > P->tune_cap) {
     cudaFree(P->tune_params);
@@ -1129,7 +1329,6 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     return cuda_fail(e);
   }
   const int cands[4] = {16, 12, 8, 4};
-  const int keep = P->team_warps;
   int best = keep;
   float best_ms = 0.0f;
   for (int c = 0; c < 4 && rc == OB_OK; ++c) {
@@ -1154,18 +1353,22 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
   P->team_warps = rc ? keep : best;
   drop_graphs(P);
   if (team_warps_out) *team_warps_out = P->team_warps;
-  return rc;
+  if (rc) return rc;
+  return co.end();
 }
 
 int ob_release(void) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> hl(g_host_mu[dev]);
+  std::lock_guard<std::mutex> cl(g_call_mu[dev]);
   std::lock_guard<std::mutex> lk(g_mu);
   DevPool& P = g_pool[dev];
   if (!P.init) return OB_OK;
   cudaDeviceSynchronize();
   drop_graphs(&P);
+  if (P.order_ev) cudaEventDestroy(P.order_ev);
   if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
   cudaFree(P.gstate);
   cudaFree(P.tune_params);
@@ -1199,6 +1402,42 @@ const char* ob_strerror(int code) {
 
 const char* ob_last_cuda_error(void) { return g_cuda_err; }
 
+int ob_fp64_peak(int64_t iters, void* stream, double* tflops_out, double* ms_out) {
+  if (iters <= 0 || !tflops_out) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const int blocks = P->sms * 8, threads = 256;  // 64 warps per SM
+  cudaEvent_t a = nullptr, b = nullptr;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b)) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return cuda_fail(e);
+  }
+  float best = 0.0f;
+  for (int rep = 0; rep < 3 && rc == OB_OK; ++rep) {  // the first run warms the clocks
+    float ms = 0.0f;
+    if ((e = cudaEventRecord(a, s)) != cudaSuccess) { rc = cuda_fail(e); break; }
+    k_fp64_probe<<<blocks, threads, 0, s>>>((long long)iters, 0.999999999, 1e-9, (double*)P->ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(b, s)) != cudaSuccess ||
+        (e = cudaEventSynchronize(b)) != cudaSuccess || (e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    if (rep == 1 || (rep > 1 && ms < best)) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  const double flops = 2.0 * kProbeChains * (double)iters * blocks * threads;
+  *tflops_out = flops / (best * 1e-3) / 1e12;
+  if (ms_out) *ms_out = best;
+  return OB_OK;
+}
+
 int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, double* out,
                              int32_t* status, void* stream) {
   if (n_options < 0 || n_options > kNoAllocMaxOptions) return OB_ERR_ARG;
@@ -1208,11 +1447,7 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
   char* base = nullptr;
   int rc = noalloc_base(&base);
   if (rc) return rc;
-  int sms = 0, dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-    return cuda_fail(e);
+  cudaError_t e;
   int* ctl = (int*)base;
   DevStats* ds = (DevStats*)(base + 256);
   int* order = (int*)(base + kNoAllocHead);
@@ -1231,13 +1466,13 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
                                                              kHeavyFactor);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
-  k_tc_batched<kNW, true><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes, ctl,
-                                                   list0, ds);
+  // every option goes to a CTA team (heavy factor 0), as in the pooled form
+  k_tc_batched<kNW, false><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes,
+                                                              ctl, list0, ds, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0,
                                       &ctl[C_T1_HEAD], &ctl[C_T1_OVF], list1, 1, ds);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  (void)sms;
   return OB_OK;
 }
 

@@ -48,7 +48,6 @@ struct Stats {
   long long upts;        // successor breakpoints merged (union points) over all levels
   long long wpts, zpts;  // points of w and of z summed over all levels (both parties)
   int zmax_level;        // largest number of z points in one level
-  int zmax_node;         // not tracked per node (reserved)
 };
 
 // Per-option scratch carved from one worker's arena.
@@ -58,7 +57,6 @@ struct Lay {
   double* nt[2];  // [4(N+2)] per node of a level: S^a lambda, S^b lambda, xi lambda
   int* off[2];    // [2(N+2)+1] first point of each node (seller nodes, then buyer nodes)
   double *zY[2], *zF[2], *zS[2];
-  int* offw;      // [2(N+1)+1]
   int* wN;        // node of each point of w
   double *wY, *wF, *wS;
   long long *wGK, *wHK;  // keys of g = w + S^a y and h = w + S^b y (only compared)
@@ -75,7 +73,6 @@ OB_HD size_t node_bytes(int N) {
   n += al256(sizeof(double) * ((size_t)N + 2));
   n += 2 * al256(sizeof(double) * 4 * ((size_t)N + 2));
   n += 2 * al256(sizeof(int) * (2 * ((size_t)N + 2) + 1));
-  n += al256(sizeof(int) * (2 * ((size_t)N + 1) + 1));
   return n;
 }
 
@@ -91,7 +88,6 @@ OB_HD char* carve_cap(char* base, int N, size_t cap, Lay& L) {
   L.lam = (double*)take(sizeof(double) * ((size_t)N + 2));
   for (int b = 0; b < 2; ++b) L.nt[b] = (double*)take(sizeof(double) * 4 * ((size_t)N + 2));
   for (int b = 0; b < 2; ++b) L.off[b] = (int*)take(sizeof(int) * (2 * ((size_t)N + 2) + 1));
-  L.offw = (int*)take(sizeof(int) * (2 * ((size_t)N + 1) + 1));
   for (int b = 0; b < 2; ++b) {
     L.zY[b] = (double*)take(sizeof(double) * cap);
     L.zF[b] = (double*)take(sizeof(double) * cap);
@@ -120,6 +116,37 @@ OB_HD bool carve(char* base, size_t bytes, int N, int min_cap, Lay& L) {
   if ((long long)cap < (long long)min_cap) return false;
   char* p = carve_cap(base, N, cap, L);
   return (size_t)(p - base) <= bytes;
+}
+
+// The arrays of one level's successor maximum w (and of g, h and their running
+// minima): the option's global scratch, or a chunk of nodes in shared memory.
+struct WBuf {
+  double *Y, *F, *S;
+  int* N;                 // node of each point
+  long long *GK, *HK;     // keys of g = w + S^a y and h = w + S^b y
+  long long *CA, *CB;     // running minima of the g keys (from the right) and h keys (from the left)
+  int cap;
+};
+
+OB_HD WBuf global_wbuf(const Lay& L) {
+  return WBuf{L.wY, L.wF, L.wS, L.wN, L.wGK, L.wHK, L.wCA, L.wCB, L.capW};
+}
+
+// Bytes of shared memory per point of a WBuf, and the WBuf of cap points carved at p
+// (8-byte arrays first, so every array stays 8-byte aligned).
+constexpr int WBUF_POINT_BYTES = 3 * 8 + 4 * 8 + 4;
+OB_HD WBuf carve_wbuf(char* p, int cap) {
+  WBuf w;
+  w.Y = (double*)p; p += 8 * (size_t)cap;
+  w.F = (double*)p; p += 8 * (size_t)cap;
+  w.S = (double*)p; p += 8 * (size_t)cap;
+  w.GK = (long long*)p; p += 8 * (size_t)cap;
+  w.HK = (long long*)p; p += 8 * (size_t)cap;
+  w.CA = (long long*)p; p += 8 * (size_t)cap;
+  w.CB = (long long*)p; p += 8 * (size_t)cap;
+  w.N = (int*)p;
+  w.cap = cap;
+  return w;
 }
 
 OB_HD double ob_inf() { return bitsd(0x7FF0000000000000LL); }
@@ -345,14 +372,25 @@ OB_HD LD operator*(double a, const LD& b) { return mk<LD>(a) * b; }
 
 // Decisions: the pricing run computes them (NoDec); the adjoint records them with
 // a double run (RecDec) and replays them with an LD run (PlayDec).
+//
+// Bound on the decisions of one piece() call.  Left tail (head only): the split (1)
+// and, per part (at most 2), comb1 (2) and the slope tests of its at most 2 sub-pieces
+// (2): 9.  The fast-path test (1), then either the fast outcome (1) or, on the
+// general path, the cB combination (2), the cA combination of at most 2 sub-pieces (4), then
+// per sub-piece of v (at most 4) the split at yu (1) and, per part (at most 2), comb1
+// (2) and at most 2 slope tests: 4 * 9.  Counting both paths bounds it by
+// 9 + 1 + 1 + 2 + 4 + 36 = 53.
+constexpr int MAXDEC = 9 + 1 + 1 + 2 + 4 + 4 * (1 + 2 * (2 + 2));
+constexpr int DECCAP = 96;
+static_assert(MAXDEC <= DECCAP, "decision record too small for one piece");
 struct NoDec {
   OB_HD int take(int c) { return c; }
 };
 struct RecDec {
-  unsigned char d[96];
+  unsigned char d[DECCAP];
   int n = 0;
   OB_HD int take(int c) {
-    if (n < 96) d[n] = (unsigned char)c;
+    if (n < DECCAP) d[n] = (unsigned char)c;
     ++n;
     return c;
   }
@@ -360,7 +398,7 @@ struct RecDec {
 struct PlayDec {
   const unsigned char* d;
   int n = 0;
-  OB_HD int take(int) { return d[n++]; }
+  OB_HD int take(int) { return d[n < DECCAP ? n++ : DECCAP - 1]; }
 };
 
 // ------------------------------------------------------------------ pass 3 helpers
@@ -624,7 +662,9 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
 }
 
 // ------------------------------------------------------------------ the option
-template <class Team>
+// CHIP: the instantiation with the fused level step (w of chunks of nodes in on-chip
+// arrays, level_fused); the plain instantiation reads and writes w in the global scratch.
+template <class Team, bool CHIP = false>
 struct TcRun {
   const Team& tm;
   const Opt& o;
@@ -638,14 +678,30 @@ struct TcRun {
   double *outY, *outF, *outS;
   int* outOff;
   int outCap;
+  WBuf wb;    // CHIP: where passes 1-3 keep w (chip, or the global scratch for big nodes)
+  WBuf chip;  // CHIP: on-chip arrays of the fused level step
 
   OB_HD TcRun(const Team& tm_, const Opt& o_, const Lay& L_) : tm(tm_), o(o_), L(L_), N(o_.N) {
     zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
     st.upts = st.wpts = st.zpts = 0;
     st.zmax_level = 0;
-    st.zmax_node = 0;
     use_banks(N);
+    if (CHIP) {
+      wb = global_wbuf(L);
+      chip = wb;
+    }
   }
+
+  // the arrays of w the passes use
+  OB_HD double* wY() const { return CHIP ? wb.Y : L.wY; }
+  OB_HD double* wF() const { return CHIP ? wb.F : L.wF; }
+  OB_HD double* wS() const { return CHIP ? wb.S : L.wS; }
+  OB_HD int* wN() const { return CHIP ? wb.N : L.wN; }
+  OB_HD long long* wGK() const { return CHIP ? wb.GK : L.wGK; }
+  OB_HD long long* wHK() const { return CHIP ? wb.HK : L.wHK; }
+  OB_HD long long* wCA() const { return CHIP ? wb.CA : L.wCA; }
+  OB_HD long long* wCB() const { return CHIP ? wb.CB : L.wCB; }
+  OB_HD int wcap() const { return CHIP ? wb.cap : L.capW; }
 
   // level t reads the bank of t+1 and writes the bank of t
   OB_HD void use_banks(int t) {
@@ -744,13 +800,12 @@ struct TcRun {
       int total;
       const int pre = tm.excl_sum(cnt, total);
       const int p0 = wpos + pre;
-      if (q < Utot && ql == 0) L.offw[node] = p0;
-      if (p0 + cnt <= L.capW) {
+      if (p0 + cnt <= wcap()) {
         for (int c = 0; c < cnt; ++c) {
-          L.wY[p0 + c] = em[c].y;
-          L.wF[p0 + c] = em[c].f;
-          L.wS[p0 + c] = em[c].s;
-          L.wN[p0 + c] = node;
+          wY()[p0 + c] = em[c].y;
+          wF()[p0 + c] = em[c].f;
+          wS()[p0 + c] = em[c].s;
+          wN()[p0 + c] = node;
         }
       } else if (cnt > 0) {
         ovf = true;
@@ -758,9 +813,8 @@ struct TcRun {
       wpos += total;
       ncur = ncur_next;
     }
-    if (lane == 0) L.offw[n1] = wpos;
     wtot = wpos;
-    return !(tm.any(ovf) || wpos > L.capW);
+    return !(tm.any(ovf) || wpos > wcap());
   }
 
   // pass 2: g, h and the per-node running minima of their keys (and, for the
@@ -776,24 +830,24 @@ struct TcRun {
     for (int base = 0; base < wtot; base += Team::W) {
       const int i = base + lane;
       const bool ok = i < wtot;
-      const int n = ok ? L.wN[i] : -1;
-      const bool head = ok && (i == 0 || L.wN[i - 1] != n);
+      const int n = ok ? wN()[i] : -1;
+      const bool head = ok && (i == 0 || wN()[i - 1] != n);
       long long hk = KMAX;
       if (ok) {
         const int j = n >= W0 ? n - W0 : n;
-        const double y = L.wY[i], f = L.wF[i];
+        const double y = wY()[i], f = wF()[i];
         const double g = f + nt[4 * j] * y, h = f + nt[4 * j + 1] * y;
-        L.wGK[i] = okey(g);
+        wGK()[i] = okey(g);
         hk = okey(h);
-        L.wHK[i] = hk;
+        wHK()[i] = hk;
       }
       if (TRACK) {
         int ix = i;
         tm.seg_argmin(hk, ix, head, carry, carry_i);
-        if (ok) { L.wCB[i] = hk; argB[i] = ix; }
+        if (ok) { wCB()[i] = hk; argB[i] = ix; }
       } else {
         const long long v = tm.seg_min(hk, head, carry);
-        if (ok) L.wCB[i] = v;
+        if (ok) wCB()[i] = v;
       }
     }
     tm.sync();
@@ -803,16 +857,16 @@ struct TcRun {
     for (int tile = ntiles - 1; tile >= 0; --tile) {
       const int i = tile * Team::W + (Team::W - 1 - lane);
       const bool ok = i < wtot;
-      const int n = ok ? L.wN[i] : -1;
-      const bool head = ok && (i + 1 == wtot || L.wN[i + 1] != n);
-      long long gk = ok ? L.wGK[i] : KMAX;
+      const int n = ok ? wN()[i] : -1;
+      const bool head = ok && (i + 1 == wtot || wN()[i + 1] != n);
+      long long gk = ok ? wGK()[i] : KMAX;
       if (TRACK) {
         int ix = i;
         tm.seg_argmin(gk, ix, head, carry, carry_i);
-        if (ok) { L.wCA[i] = gk; argA[i] = ix; }
+        if (ok) { wCA()[i] = gk; argA[i] = ix; }
       } else {
         const long long v = tm.seg_min(gk, head, carry);
-        if (ok) L.wCA[i] = v;
+        if (ok) wCA()[i] = v;
       }
     }
     tm.sync();
@@ -822,9 +876,9 @@ struct TcRun {
   OB_HD void load_piece(int t, int i, int wtot, PieceIn<double>& in, int& node) const {
     const int W0 = t + 1;
     const double* nt = L.nt[t & 1];
-    node = L.wN[i];
-    in.head = (i == 0 || L.wN[i - 1] != node);
-    in.tail = (i + 1 == wtot || L.wN[i + 1] != node);
+    node = wN()[i];
+    in.head = (i == 0 || wN()[i - 1] != node);
+    in.tail = (i + 1 == wtot || wN()[i + 1] != node);
     const int p = node >= W0 ? 1 : 0;
     const int j = node - p * W0;
     in.Sa = nt[4 * j];
@@ -834,21 +888,21 @@ struct TcRun {
     in.yu = in.seller ? (double)zeta : -(double)zeta;
     in.vu = in.seller ? xi : -xi;
     in.anchor = in.head && same_bits(in.Sa, in.Sb);
-    in.y0 = L.wY[i];
-    in.f0 = L.wF[i];
-    in.s0 = L.wS[i];
-    const long long cB = L.wCB[i];
+    in.y0 = wY()[i];
+    in.f0 = wF()[i];
+    in.s0 = wS()[i];
+    const long long cB = wCB()[i];
     in.cB = unkey(cB);
-    in.cA0 = unkey(L.wCA[i]);
+    in.cA0 = unkey(wCA()[i]);
     in.Arel = in.Brel = false;
     in.y1 = in.f1 = in.cA1 = 0.0;
     if (!in.tail) {
-      in.y1 = L.wY[i + 1];
-      in.f1 = L.wF[i + 1];
-      const long long cA1 = L.wCA[i + 1];
+      in.y1 = wY()[i + 1];
+      in.f1 = wF()[i + 1];
+      const long long cA1 = wCA()[i + 1];
       in.cA1 = unkey(cA1);
-      const long long g0 = L.wGK[i], g1 = L.wGK[i + 1];
-      const long long h0 = L.wHK[i], h1 = L.wHK[i + 1];
+      const long long g0 = wGK()[i], g1 = wGK()[i + 1];
+      const long long h0 = wHK()[i], h1 = wHK()[i + 1];
       // the cA line lies above w on the whole piece iff g <= cA_{i+1} at both ends;
       // the cB line iff h <= cB_i at both ends (then that side of v equals w)
       in.Arel = !(g1 == cA1 && g0 <= cA1);
@@ -856,15 +910,16 @@ struct TcRun {
     }
   }
 
-  // pass 3: restriction and exercise for every piece of w; writes level t
-  OB_HD bool pass3(int t, int wtot, int& ztot) {
+  // pass 3: restriction and exercise for every piece of w; writes level t, the
+  // points from position zbase on (w of a chunk of nodes: its first node's points)
+  OB_HD bool pass3(int t, int wtot, int& ztot, int zbase = 0) {
     const int lane = tm.lane();
     const int nNodes = 2 * (t + 1);
     int* off = outOff;
     double* Yz = outY;
     double* Fz = outF;
     double* Sz = outS;
-    int zpos = 0;
+    int zpos = zbase;
     bool ovf = false;
     double carry_slope = 0.0;
     for (int base = 0; base < wtot; base += Team::W) {
@@ -909,8 +964,70 @@ struct TcRun {
       zpos += total;
     }
     if (lane == 0) off[nNodes] = zpos;
-    ztot = zpos;
+    ztot = zpos - zbase;
     return !(tm.any(ovf) || zpos > outCap);
+  }
+
+  // first node n of level t (0 <= n <= 2(t+1)) whose union start is >= target: each
+  // round the team probes W evenly spaced nodes of the bracket at once and keeps the
+  // gap that holds it
+  OB_HD int node_at(int t, long long target) const {
+    int lo = 0, hi = 2 * (t + 1);  // the answer lies in [lo, hi]
+    while (lo < hi) {
+      const int step = (hi - lo + Team::W - 1) / Team::W;
+      const int n = lo + tm.lane() * step;
+      const bool below = n < hi && (long long)ustart_node(t, n) < target;
+      const int cnt = tm.count(below);  // the probes below the answer come first
+      if (cnt == 0) break;              // lo itself is at or above it
+      const int nhi = lo + cnt * step;
+      lo = lo + (cnt - 1) * step + 1;
+      if (nhi < hi) hi = nhi;
+    }
+    return lo;
+  }
+
+  // One level with w on chip: the level's nodes in chunks of whole nodes whose merged
+  // successor points number at most chip.cap; passes 1-3 run per chunk with w, the keys
+  // of g and h and their running minima in `chip` (shared memory), and only z is written
+  // to the level's bank.  A node too large for the chip arrays, or a chunk whose w
+  // outgrows them (crossings add points), runs on the global arrays instead.  The
+  // running minima restart at every node, so chunks of whole nodes give the same
+  // numbers as the one-pass level.  Returns false on overflow of the global arrays.
+  OB_HD bool level_fused(int t, int& utot, int& wtot, int& ztot) {
+    static_assert(CHIP, "the fused level step needs the on-chip instantiation");
+    const int nNodes = 2 * (t + 1);
+    const WBuf gw = global_wbuf(L);
+    const int cap = chip.cap - chip.cap / 8;  // merged points per chunk: room for crossings
+    int zpos = 0, n0 = 0;
+    utot = wtot = 0;
+    while (n0 < nNodes) {
+      const long long u0 = ustart_node(t, n0);
+      int n1 = (u0 + cap >= (long long)ustart_node(t, nNodes)) ? nNodes : node_at(t, u0 + cap + 1) - 1;
+      bool on_chip = true;
+      if (n1 <= n0) {  // node n0 alone has more than cap merged points
+        n1 = n0 + 1;
+        on_chip = false;
+      }
+      int wt = 0, ut = 0, zt = 0;
+      if (on_chip) {
+        wb = chip;
+        if (!pass1(t, wt, ut, n0, n1)) on_chip = false;
+      }
+      if (!on_chip) {
+        wb = gw;
+        if (!pass1(t, wt, ut, n0, n1)) { wb = gw; return false; }
+      }
+      pass2(t, wt);
+      const bool ok = pass3(t, wt, zt, zpos);
+      wb = gw;
+      if (!ok) return false;
+      utot += ut;
+      wtot += wt;
+      zpos += zt;
+      n0 = n1;
+    }
+    ztot = zpos;
+    return true;
   }
 
   // value at y = 0 of node n of level 0 (bank 0)
@@ -957,10 +1074,14 @@ struct TcRun {
       node_table(t);
       tm.sync();
       int wtot = 0, ztot = 0, utot = 0;
-      if (!pass1(t, wtot, utot)) return ST_CAPACITY;
+      if constexpr (CHIP) {
+        if (!level_fused(t, utot, wtot, ztot)) return ST_CAPACITY;
+      } else {
+        if (!pass1(t, wtot, utot)) return ST_CAPACITY;
+        pass2(t, wtot);
+        if (!pass3(t, wtot, ztot)) return ST_CAPACITY;
+      }
       st.upts += utot;
-      pass2(t, wtot);
-      if (!pass3(t, wtot, ztot)) return ST_CAPACITY;
       st.wpts += wtot;
       st.zpts += ztot;
       if (ztot > st.zmax_level) st.zmax_level = ztot;
@@ -1065,32 +1186,14 @@ struct TcGroup {
     return ST_OK;
   }
 
-  // first node whose union start is >= target (nodes 0..nNodes): each round the team
-  // probes W evenly spaced nodes of the bracket at once and keeps the gap that holds it
-  OB_HD int node_at(int t, long long target) const {
-    const Team& tm = R.tm;
-    int lo = 0, hi = 2 * (t + 1);  // the answer lies in [lo, hi]
-    while (lo < hi) {
-      const int step = (hi - lo + Team::W - 1) / Team::W;
-      const int n = lo + tm.lane() * step;
-      const bool below = n < hi && (long long)R.ustart_node(t, n) < target;
-      const int cnt = tm.count(below);  // the probes below the answer come first
-      if (cnt == 0) break;              // lo itself is at or above it
-      const int nhi = lo + cnt * step;
-      lo = lo + (cnt - 1) * step + 1;
-      if (nhi < hi) hi = nhi;
-    }
-    return lo;
-  }
-
   // this team's share of level t, into the private arrays; false on overflow
   OB_HD bool compute(int t) {
     const Team& tm = R.tm;
     R.use_banks(t);
     const int nNodes = 2 * (t + 1), W0 = t + 1;
     const long long Utot = R.ustart_node(t, nNodes);
-    n0 = (c == 0) ? 0 : node_at(t, (Utot * c + G - 1) / G);
-    n1 = (c == G - 1) ? nNodes : node_at(t, (Utot * (c + 1) + G - 1) / G);
+    n0 = (c == 0) ? 0 : R.node_at(t, (Utot * c + G - 1) / G);
+    n1 = (c == G - 1) ? nNodes : R.node_at(t, (Utot * (c + 1) + G - 1) / G);
     // node constants of this share only: level t for its nodes j, level t+1 for j, j+1
     // (a share that straddles the seller/buyer boundary needs two intervals of j)
     if (n0 < n1) {

@@ -59,6 +59,24 @@ extern "C" int hp_price(const obk::Opt* o, double* out, long long* pts) {
   return rc;
 }
 
+// The fused level step (TcRun::level_fused): w of chunks of whole nodes in an array of
+// `cap` points (shared memory on the GPU; here host memory poisoned with NaN).
+extern "C" int hp_price_chip(const obk::Opt* o, int cap, double* out, long long* pts) {
+  const size_t bytes = 256ull << 20;
+  OneLane tm;
+  obk::Lay L;
+  if (!obk::carve(arena(bytes), bytes, o->N, 16, L)) return obk::ST_CAPACITY;
+  std::vector<char> chip((size_t)cap * obk::WBUF_POINT_BYTES + 64);
+  std::memset(chip.data(), 0xff, chip.size());
+  obk::TcRun<OneLane, true> R(tm, *o, L);
+  R.chip = obk::carve_wbuf(chip.data(), cap);
+  const int rc = R.run(out[0], out[1]);
+  pts[0] = R.st.upts;
+  pts[1] = R.st.wpts;
+  pts[2] = R.st.zpts;
+  return rc;
+}
+
 extern "C" int hp_price_split(const obk::Opt* o, int G, double* out, long long* pts) {
   const size_t shared_bytes = 64ull << 20, priv_bytes = 32ull << 20;
   char* base = arena(shared_bytes + priv_bytes * (size_t)G);

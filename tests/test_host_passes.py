@@ -79,6 +79,25 @@ def test_level_split_over_teams_is_bitwise_equal(G):
             assert np.array_equal(pts1, pts2)
 
 
+@pytest.mark.parametrize("cap", [3, 8, 40, 600])
+def test_fused_level_step_is_bitwise_equal(cap):
+    """Passes 1-3 per chunk of whole nodes with w in a small on-chip array (chunks of a few
+    nodes, nodes too large for the array on the global path, chunks whose w outgrows the
+    array rerun globally) give the same bits and point counts as the one-pass level."""
+    t = _table()
+    P = ctypes.c_void_p
+    for i in range(len(t)):
+        rc1, out1, pts1 = _price(t[i])
+        a = _rec(t[i])
+        out2 = np.zeros(2)
+        pts2 = np.zeros(3, np.int64)
+        rc2 = _lib().hp_price_chip(a.ctypes.data_as(P), cap, out2.ctypes.data_as(P), pts2.ctypes.data_as(P))
+        assert rc1 == rc2
+        if rc1 == 0:
+            assert np.array_equal(out1.view(np.int64), out2.view(np.int64)), (i, out1, out2)
+            assert np.array_equal(pts1, pts2)
+
+
 def test_host_adjoint_matches_dual_gradient():
     t = W.random_table(6, 31500, N_lo=2, N_hi=50)
     t["k"] = np.maximum(t["k"], 1e-4)

@@ -248,7 +248,8 @@ EXACT_CASES = [
     dict(K=95.0, K2=105.0, k=0.01, N=12, payoff=W.SPREAD),
     dict(k=0.05, N=8, payoff=W.PUT, S0=97.0),
     dict(K=95.0, K2=105.0, k=0.02, N=10, payoff=W.SPREAD, sigma=0.1, T=0.1),
-]
+] + [dict(K=(95.0 if pay == W.SPREAD else 100.0), K2=105.0, k=k, N=24, payoff=pay)
+     for pay in (W.PUT, W.CALL, W.SPREAD) for k in (0.0025, 0.01, 0.05)]
 
 
 @pytest.mark.parametrize("case", EXACT_CASES)
@@ -284,6 +285,36 @@ def test_oracle_matches_hedging_lp(case):
     bid_lp = hedging_lp.bid_enumerate(*args) if case["N"] <= 3 else hedging_lp.bid_milp(*args)
     assert out[0, 0] == pytest.approx(ask_lp, rel=1e-9, abs=1e-9)
     assert out[0, 1] == pytest.approx(bid_lp, rel=1e-9, abs=1e-9)
+
+
+SELLER_LP_CASES = [
+    dict(k=0.01, N=5, payoff=W.PUT),
+    dict(k=0.02, N=6, payoff=W.PUT, S0=97.0),
+    dict(k=0.01, N=6, payoff=W.CALL),
+    dict(K=95.0, K2=105.0, k=0.01, N=6, payoff=W.SPREAD),
+    dict(K=95.0, K2=105.0, k=0.05, N=5, payoff=W.SPREAD, sigma=0.1),
+]
+
+
+@pytest.mark.parametrize("case", SELLER_LP_CASES)
+def test_oracle_ask_matches_superhedging_lp_n6(case):
+    """The seller's superhedging LP on the non-recombining tree at N = 5, 6 (2^(N+2) - 1 nodes).
+    The buyer's side is pinned up to N = 4 only: its stopping-time program (binary stop
+    indicators) took 17-30 s at N = 4 and did not finish in 10 minutes at N = 5."""
+    t = W.make(**case)
+    out, _ = oracle.price_ask_bid(t)
+    row = t[0]
+    ask_lp = hedging_lp.ask(*[float(row[f]) for f in ("S0", "K", "K2", "sigma", "R", "T", "k")],
+                            int(row["N"]), int(row["payoff"]))
+    assert out[0, 0] == pytest.approx(ask_lp, rel=1e-9, abs=1e-9)
+
+
+def test_oracle_bid_matches_stopping_time_milp_spread_n4():
+    row = W.make(K=95.0, K2=105.0, k=0.01, N=4, payoff=W.SPREAD)
+    out, _ = oracle.price_ask_bid(row)
+    args = [float(row[0][f]) for f in ("S0", "K", "K2", "sigma", "R", "T", "k")] + [4, W.SPREAD]
+    assert out[0, 1] == pytest.approx(hedging_lp.bid_milp(*args, ybound=3.0, xbound=1000.0),
+                                      rel=1e-9, abs=1e-9)
 
 
 def test_buyer_milp_agrees_with_enumeration():
