@@ -142,8 +142,10 @@ T pl_eval(const PL<T>& F, const T& x) {
 // Pointwise max (take_max) or min of F and G.  The union of both breakpoint
 // sets is evaluated on both functions; wherever F - G changes sign strictly
 // between neighbouring union points (or in a tail) the crossing is inserted.
+// owners (optional): for each piece of the result (the left tail, the piece right of each
+// breakpoint), 1 if it is a piece of F, 2 if of G.
 template <class T>
-PL<T> pl_envelope(const PL<T>& F, const PL<T>& G, bool take_max) {
+PL<T> pl_envelope(const PL<T>& F, const PL<T>& G, bool take_max, std::vector<int>* owners = nullptr) {
   enum { OF = 1, OG = 2 };
   struct UP { T y; int iF, iG; };
   std::vector<UP> U;
@@ -232,12 +234,21 @@ PL<T> pl_envelope(const PL<T>& F, const PL<T>& G, bool take_max) {
   PL<T> out;
   out.sL = own.front() == OF ? F.sL : G.sL;
   out.sR = own.back() == OF ? F.sR : G.sR;
+  if (owners) owners->assign(1, own.front());
   for (size_t q = 0; q < P.size(); ++q) {
     const int ol = own[q], orr = own[q + 1];
     const bool kink = (ol != orr) || (ol == OF ? P[q].iF >= 0 : P[q].iG >= 0);
-    if (kink) { out.y.push_back(P[q].y); out.f.push_back(P[q].f); }
+    if (kink) {
+      out.y.push_back(P[q].y);
+      out.f.push_back(P[q].f);
+      if (owners) owners->push_back(orr);
+    }
   }
-  if (out.y.empty()) { out.y.push_back(P[0].y); out.f.push_back(P[0].f); }
+  if (out.y.empty()) {
+    out.y.push_back(P[0].y);
+    out.f.push_back(P[0].f);
+    if (owners) owners->push_back(own.back());
+  }
   return out;
 }
 
@@ -254,8 +265,17 @@ PL<T> pl_div(const PL<T>& F, const T& r) {
 //   A(y) = min_{y' >= y} [F(y') + Sa y'] - Sa y   (buy stock, swept from the right)
 //   B(y) = min_{y' <= y} [F(y') + Sb y'] - Sb y   (sell stock, swept from the left)
 // Each of A, B follows F ("active") or a line of slope -Sa / -Sb ("flat").
+// The pieces of a restriction, for the derivatives: for each piece of A and of B (left
+// tail first) whether it follows F (ACT) or is a flat line, and for a flat line the
+// breakpoint of F where the running minimum it carries is attained; for each piece of V
+// whether it is a piece of A (1) or of B (2).
+struct RestrictPieces {
+  std::vector<int> a_own, a_arg, b_own, b_arg, v_own;
+  std::vector<double> a_y, b_y;  // breakpoints of A and B
+};
+
 template <class T>
-int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V) {
+int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V, RestrictPieces* rp = nullptr) {
   enum { ACT = 1, FLAT = 2 };
   const size_t m = F.y.size();
   if (val(F.sR) + val(Sa) < 0 || val(F.sL) + val(Sb) > 0) return OR_ERR_UNBOUNDED;
@@ -266,35 +286,40 @@ int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V) {
   {
     std::vector<SP> P;     // right-to-left
     std::vector<int> own;  // own[q]: owner of the segment right of P[q] (own[0] = right tail)
+    std::vector<int> arg;  // arg[q]: for a flat segment, the breakpoint where its minimum is attained
     own.push_back(ACT);
+    arg.push_back(-1);
     T cur = F.f[m - 1] + Sa * F.y[m - 1];
+    int cur_i = (int)(m - 1);
     bool act_right = true;  // is M equal to g at the current right end point?
     P.push_back({F.y[m - 1], F.f[m - 1], (int)(m - 1)});
     for (size_t ii = m - 1; ii-- > 0;) {
       T gi = F.f[ii] + Sa * F.y[ii];
       T gr = F.f[ii + 1] + Sa * F.y[ii + 1];
       if (val(gi) >= val(cur)) {
-        own.push_back(FLAT);
+        own.push_back(FLAT); arg.push_back(cur_i);
         P.push_back({F.y[ii], cur - Sa * F.y[ii], (int)ii});
         act_right = false;
       } else if (act_right) {
-        own.push_back(ACT);
+        own.push_back(ACT); arg.push_back(-1);
         P.push_back({F.y[ii], F.f[ii], (int)ii});
         cur = gi;
+        cur_i = (int)ii;
       } else {
         T t = (cur - gi) / (gr - gi);  // g(y*) = cur, measured from y_i
         T ys = F.y[ii] + (F.y[ii + 1] - F.y[ii]) * t;
         if (val(ys) > val(F.y[ii]) && val(ys) < val(F.y[ii + 1])) {
-          own.push_back(FLAT);
+          own.push_back(FLAT); arg.push_back(cur_i);
           P.push_back({ys, cur - Sa * ys, -1});
-          own.push_back(ACT);
+          own.push_back(ACT); arg.push_back(-1);
         } else if (val(ys) >= val(F.y[ii + 1])) {
-          own.push_back(ACT);
+          own.push_back(ACT); arg.push_back(-1);
         } else {
-          own.push_back(FLAT);
+          own.push_back(FLAT); arg.push_back(cur_i);
         }
         P.push_back({F.y[ii], F.f[ii], (int)ii});
         cur = gi;
+        cur_i = (int)ii;
         act_right = true;
       }
     }
@@ -302,33 +327,43 @@ int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V) {
     const double slg = val(F.sL) + val(Sa);
     T tailslope;
     if (slg <= 0) {
-      own.push_back(FLAT);
+      own.push_back(FLAT); arg.push_back(cur_i);
       tailslope = -Sa;
     } else if (act_right) {
-      own.push_back(ACT);
+      own.push_back(ACT); arg.push_back(-1);
       tailslope = F.sL;
     } else {
       T g0 = F.f[0] + Sa * F.y[0];
       T ys = F.y[0] - (g0 - cur) / (F.sL + Sa);
       if (val(ys) < val(F.y[0])) {
-        own.push_back(FLAT);
+        own.push_back(FLAT); arg.push_back(cur_i);
         P.push_back({ys, cur - Sa * ys, -1});
       }
-      own.push_back(ACT);
+      own.push_back(ACT); arg.push_back(-1);
       tailslope = F.sL;
     }
     // P is right-to-left; own[q] is right of P[q], own[q+1] is left of P[q].
     A.sR = F.sR;  // own[0] == ACT
     A.sL = tailslope;
     std::vector<T> yy, ff;
+    std::vector<int> lo, la;  // owner and argument of the piece left of each kept point
     for (size_t q = 0; q < P.size(); ++q) {
       const int orr = own[q], ol = own[q + 1];
       const bool kink = (ol != orr) || (ol == ACT && P[q].iF >= 0);
-      if (kink) { yy.push_back(P[q].y); ff.push_back(P[q].f); }
+      if (kink) { yy.push_back(P[q].y); ff.push_back(P[q].f); lo.push_back(ol); la.push_back(arg[q + 1]); }
     }
-    if (yy.empty()) { yy.push_back(P[0].y); ff.push_back(P[0].f); }
+    if (yy.empty()) {
+      yy.push_back(P[0].y); ff.push_back(P[0].f);
+      lo.push_back(own.back()); la.push_back(arg.back());
+    }
     A.y.assign(yy.rbegin(), yy.rend());
     A.f.assign(ff.rbegin(), ff.rend());
+    if (rp) {  // pieces of A from the left: left of each kept point (leftmost first), the right tail
+      rp->a_own.assign(lo.rbegin(), lo.rend());
+      rp->a_arg.assign(la.rbegin(), la.rend());
+      rp->a_own.push_back(own[0]);
+      rp->a_arg.push_back(arg[0]);
+    }
   }
 
   // ---- B: sweep from the left over h = F + Sb*y.
@@ -336,67 +371,86 @@ int pl_restrict(const PL<T>& F, const T& Sa, const T& Sb, PL<T>& V) {
   {
     std::vector<SP> P;     // left-to-right
     std::vector<int> own;  // own[q]: owner of the segment left of P[q] (own[0] = left tail)
+    std::vector<int> arg;  // arg[q]: for a flat segment, the breakpoint where its minimum is attained
     own.push_back(ACT);
+    arg.push_back(-1);
     T cur = F.f[0] + Sb * F.y[0];
+    int cur_i = 0;
     bool act_left = true;
     P.push_back({F.y[0], F.f[0], 0});
     for (size_t ii = 1; ii < m; ++ii) {
       T hi = F.f[ii] + Sb * F.y[ii];
       T hl = F.f[ii - 1] + Sb * F.y[ii - 1];
       if (val(hi) >= val(cur)) {
-        own.push_back(FLAT);
+        own.push_back(FLAT); arg.push_back(cur_i);
         P.push_back({F.y[ii], cur - Sb * F.y[ii], (int)ii});
         act_left = false;
       } else if (act_left) {
-        own.push_back(ACT);
+        own.push_back(ACT); arg.push_back(-1);
         P.push_back({F.y[ii], F.f[ii], (int)ii});
         cur = hi;
+        cur_i = (int)ii;
       } else {
         T t = (hl - cur) / (hl - hi);  // h(y*) = cur, measured from y_{i-1}
         T ys = F.y[ii - 1] + (F.y[ii] - F.y[ii - 1]) * t;
         if (val(ys) > val(F.y[ii - 1]) && val(ys) < val(F.y[ii])) {
-          own.push_back(FLAT);
+          own.push_back(FLAT); arg.push_back(cur_i);
           P.push_back({ys, cur - Sb * ys, -1});
-          own.push_back(ACT);
+          own.push_back(ACT); arg.push_back(-1);
         } else if (val(ys) <= val(F.y[ii - 1])) {
-          own.push_back(ACT);
+          own.push_back(ACT); arg.push_back(-1);
         } else {
-          own.push_back(FLAT);
+          own.push_back(FLAT); arg.push_back(cur_i);
         }
         P.push_back({F.y[ii], F.f[ii], (int)ii});
         cur = hi;
+        cur_i = (int)ii;
         act_left = true;
       }
     }
     const double srh = val(F.sR) + val(Sb);
     T tailslope;
     if (srh >= 0) {
-      own.push_back(FLAT);
+      own.push_back(FLAT); arg.push_back(cur_i);
       tailslope = -Sb;
     } else if (act_left) {
-      own.push_back(ACT);
+      own.push_back(ACT); arg.push_back(-1);
       tailslope = F.sR;
     } else {
       T hm = F.f[m - 1] + Sb * F.y[m - 1];
       T ys = F.y[m - 1] + (cur - hm) / (F.sR + Sb);
       if (val(ys) > val(F.y[m - 1])) {
-        own.push_back(FLAT);
+        own.push_back(FLAT); arg.push_back(cur_i);
         P.push_back({ys, cur - Sb * ys, -1});
       }
-      own.push_back(ACT);
+      own.push_back(ACT); arg.push_back(-1);
       tailslope = F.sR;
     }
     B.sL = F.sL;  // own[0] == ACT
     B.sR = tailslope;
+    if (rp) { rp->b_own.clear(); rp->b_arg.clear(); }
     for (size_t q = 0; q < P.size(); ++q) {
       const int ol = own[q], orr = own[q + 1];
       const bool kink = (ol != orr) || (ol == ACT && P[q].iF >= 0);
-      if (kink) { B.y.push_back(P[q].y); B.f.push_back(P[q].f); }
+      if (kink) {
+        B.y.push_back(P[q].y); B.f.push_back(P[q].f);
+        if (rp) { rp->b_own.push_back(ol); rp->b_arg.push_back(arg[q]); }
+      }
     }
-    if (B.y.empty()) { B.y.push_back(P[0].y); B.f.push_back(P[0].f); }
+    if (B.y.empty()) {
+      B.y.push_back(P[0].y); B.f.push_back(P[0].f);
+      if (rp) { rp->b_own.push_back(own[0]); rp->b_arg.push_back(arg[0]); }
+    }
+    if (rp) { rp->b_own.push_back(own.back()); rp->b_arg.push_back(arg.back()); }
   }
 
-  V = pl_envelope(A, B, false);
+  if (rp) {
+    rp->a_y.clear();
+    rp->b_y.clear();
+    for (const T& y : A.y) rp->a_y.push_back(val(y));
+    for (const T& y : B.y) rp->b_y.push_back(val(y));
+  }
+  V = pl_envelope(A, B, false, rp ? &rp->v_own : nullptr);
   return OR_OK;
 }
 
@@ -426,6 +480,120 @@ int node_step(const PL<T>& zu, const PL<T>& zd, const T& r, const T& Sa, const T
   if (rc) return rc;
   PL<T> u = pl_expense(xi, zeta, Sa, Sb, buyer);
   z = pl_envelope(u, v, !buyer);
+  return OR_OK;
+}
+
+// ---------------------------------------------------------------- derivatives by lines
+// With the breakpoint structure held fixed, every piece of every function of the
+// induction is a line c + s*y, and each step takes its output pieces from the lines of
+// its inputs or builds new lines from them: the maximum and the minimum take the lines
+// of the winning function; the division by r divides both coefficients; the flat pieces
+// of the restriction are lines of slope -S^a (or -S^b) through the breakpoint y* where
+// g = F + S^a y (or h = F + S^b y) attains the running minimum; the expense function is
+// two lines.  So the derivatives are carried on (c, s) of every piece.  At y*, between the
+// lines P (left) and Q (right) of F, the minimum value moves with
+//   dg = (1 - mu) dg_P(y*) + mu dg_Q(y*),   mu = (s_P + S^a) / (s_P - s_Q),
+// (y* held fixed in g_P, g_Q; mu lies in [0, 1] because the slopes of g on the two sides
+// bracket zero at a minimum), which is the derivative of g_P(y*) with y* = the crossing of
+// P and Q moving.  No breakpoint position enters a derivative: a crossing of two lines at
+// a shallow angle moves fast, but the functions do not, and carrying the positions would
+// cancel large terms in floating point.
+struct Line {
+  Dual c, s;  // value and gradient of the intercept and of the slope
+};
+
+// A function for the derivatives: its breakpoints and values (double, as priced) and
+// the line of each piece: L[0] the left tail, L[k] between y[k-1] and y[k], L[m] the
+// right tail.
+struct LPL {
+  PL<double> F;
+  std::vector<Line> L;
+};
+
+// Piece of src that contains piece k of out (out's pieces lie inside src's pieces):
+// the number of src breakpoints at or left of the piece's left end.
+int src_piece(const std::vector<double>& src_y, const std::vector<double>& out_y, int k) {
+  if (k == 0) return 0;
+  return (int)(std::upper_bound(src_y.begin(), src_y.end(), out_y[k - 1]) - src_y.begin());
+}
+
+LPL lines_envelope(const LPL& X, const LPL& Y, bool take_max) {
+  LPL out;
+  std::vector<int> own;
+  out.F = pl_envelope(X.F, Y.F, take_max, &own);
+  const int m = (int)out.F.y.size();
+  out.L.resize(m + 1);
+  for (int k = 0; k <= m; ++k) {
+    const LPL& src = (own[k] == 1) ? X : Y;
+    out.L[k] = src.L[src_piece(src.F.y, out.F.y, k)];
+  }
+  return out;
+}
+
+LPL lines_div(const LPL& X, const Dual& r) {
+  LPL out;
+  out.F = pl_div(X.F, r.v);
+  out.L.resize(X.L.size());
+  for (size_t k = 0; k < X.L.size(); ++k) out.L[k] = Line{X.L[k].c / r, X.L[k].s / r};
+  return out;
+}
+
+// Line of slope -S through the breakpoint j of F where F + S y is least.  Breakpoints
+// that coincide with y_j to within rounding (crossings that round to within a few ulps
+// of a kink) leave the choice among them to rounding noise in the values; the minimum
+// sits where the slopes of the lines, + S, change sign, so the search moves to the
+// breakpoint of the cluster where they do, and the weight is kept in [0, 1].
+Line flat_line(const LPL& F, int j, const Dual& S) {
+  const int m = (int)F.F.y.size();
+  const double tol = 1e-12 * std::max(1.0, std::fabs(F.F.y[j]));
+  while (j + 1 < m && F.L[j + 1].s.v + S.v < 0 && F.F.y[j + 1] - F.F.y[j] <= tol) ++j;
+  while (j > 0 && F.L[j].s.v + S.v > 0 && F.F.y[j] - F.F.y[j - 1] <= tol) --j;
+  const double ys = F.F.y[j];
+  const Line& P = F.L[j];
+  const Line& Q = F.L[j + 1];
+  const double sp = P.s.v, sq = Q.s.v;
+  double mu = (sp == sq) ? 0.0 : (sp + S.v) / (sp - sq);
+  mu = std::min(1.0, std::max(0.0, mu));
+  const Dual gP = P.c + (P.s + S) * Dual(ys);
+  const Dual gQ = Q.c + (Q.s + S) * Dual(ys);
+  return Line{gP * Dual(1.0 - mu) + gQ * Dual(mu), -S};
+}
+
+int lines_restrict(const LPL& F, const Dual& Sa, const Dual& Sb, LPL& V) {
+  RestrictPieces rp;
+  int rc = pl_restrict(F.F, Sa.v, Sb.v, V.F, &rp);
+  if (rc) return rc;
+  enum { ACT = 1 };
+  std::vector<Line> LA(rp.a_own.size()), LB(rp.b_own.size());
+  for (size_t k = 0; k < LA.size(); ++k)
+    LA[k] = rp.a_own[k] == ACT ? F.L[src_piece(F.F.y, rp.a_y, (int)k)] : flat_line(F, rp.a_arg[k], Sa);
+  for (size_t k = 0; k < LB.size(); ++k)
+    LB[k] = rp.b_own[k] == ACT ? F.L[src_piece(F.F.y, rp.b_y, (int)k)] : flat_line(F, rp.b_arg[k], Sb);
+  const int m = (int)V.F.y.size();
+  V.L.resize(m + 1);
+  for (int k = 0; k <= m; ++k)
+    V.L[k] = rp.v_own[k] == 1 ? LA[src_piece(rp.a_y, V.F.y, k)] : LB[src_piece(rp.b_y, V.F.y, k)];
+  return OR_OK;
+}
+
+// Expense function (Eq. 1, Eq. 6) as two lines: left of its kink slope -S^a, right -S^b.
+LPL lines_expense(const Dual& xi, const Dual& zeta, const Dual& Sa, const Dual& Sb, bool buyer) {
+  LPL u;
+  u.F = pl_expense<double>(xi.v, zeta.v, Sa.v, Sb.v, buyer);
+  const Dual x = buyer ? -xi : xi, z = buyer ? -zeta : zeta;
+  u.L = {Line{x + Sa * z, -Sa}, Line{x + Sb * z, -Sb}};  // through the kink (z, x)
+  return u;
+}
+
+int lines_node_step(const LPL& zu, const LPL& zd, const Dual& r, const Dual& Sa, const Dual& Sb,
+                    const Dual& xi, const Dual& zeta, bool buyer, LPL& z) {
+  LPL w = lines_envelope(zu, zd, true);
+  LPL f = lines_div(w, r);
+  LPL v;
+  int rc = lines_restrict(f, Sa, Sb, v);
+  if (rc) return rc;
+  LPL u = lines_expense(xi, zeta, Sa, Sb, buyer);
+  z = lines_envelope(u, v, !buyer);
   return OR_OK;
 }
 
@@ -528,6 +696,46 @@ int price_tc(const Model<T>& m, T& ask, T& bid, Stats* st) {
   }
   ask = pl_eval(zs[0], T(0.0));
   bid = -pl_eval(zb[0], T(0.0));
+  return OR_OK;
+}
+
+// The induction of price_tc on LPL functions: the same prices (the breakpoints and values
+// are computed by the same double functions), and their derivatives through the lines.
+// The value at y = 0 of the root functions is that of the piece right of every breakpoint
+// at or left of 0.
+int price_tc_lines(const Model<Dual>& m, Dual& ask, Dual& bid) {
+  const int N = m.N;
+  std::vector<LPL> zs(N + 2), zb(N + 2);
+  for (int j = 0; j <= N + 1; ++j) {
+    Dual S = stock(m, N + 1, j);
+    Dual Sa = (Dual(1.0) + m.k) * S, Sb = (Dual(1.0) - m.k) * S;
+    zs[j] = lines_expense(Dual(0.0), Dual(0.0), Sa, Sb, false);
+    zb[j] = lines_expense(Dual(0.0), Dual(0.0), Sa, Sb, true);
+  }
+  for (int t = N; t >= 0; --t) {
+    for (int j = 0; j <= t; ++j) {
+      Dual S = stock(m, t, j);
+      Dual kt = (t == 0) ? Dual(0.0) : m.k;
+      Dual Sa = (Dual(1.0) + kt) * S, Sb = (Dual(1.0) - kt) * S;
+      Dual xi, zeta;
+      payoff_at(m, S, xi, zeta);
+      LPL ns, nb;
+      int rc = lines_node_step(zs[j + 1], zs[j], m.r, Sa, Sb, xi, zeta, false, ns);
+      if (rc) return rc;
+      rc = lines_node_step(zb[j + 1], zb[j], m.r, Sa, Sb, xi, zeta, true, nb);
+      if (rc) return rc;
+      zs[j] = std::move(ns);
+      zb[j] = std::move(nb);
+    }
+  }
+  auto at0 = [](const LPL& z) {
+    const int k = (int)(std::upper_bound(z.F.y.begin(), z.F.y.end(), 0.0) - z.F.y.begin());
+    Dual v = z.L[k].c;  // c + s * 0
+    v.v = pl_eval(z.F, 0.0);
+    return v;
+  };
+  ask = at0(zs[0]);
+  bid = -at0(zb[0]);
   return OR_OK;
 }
 
@@ -641,8 +849,9 @@ int or_tc_stats(const or_option_t* o, int64_t* counts, int64_t* per_level) {
   return OR_OK;
 }
 
-// Derivatives of ask and bid by forward-mode dual numbers:
-// grad[12i + 0..5] = d ask / d(S0, K, sigma, R, T, k), grad[12i + 6..11] = d bid / d(...).
+// Derivatives of ask and bid by forward-mode dual numbers carried on the lines of the
+// pieces (price_tc_lines): grad[12i + 0..5] = d ask / d(S0, K, sigma, R, T, k),
+// grad[12i + 6..11] = d bid / d(...).
 int or_greeks_tc(const or_option_t* opts, int64_t n, double* out, double* grad, int32_t* status,
                  int nthreads) {
   parallel_for(n, nthreads, [&](int64_t i) {
@@ -654,7 +863,7 @@ int or_greeks_tc(const or_option_t* opts, int64_t n, double* out, double* grad, 
       const double base[NG] = {o.S0, o.K, o.sigma, o.R, o.T, o.k};
       for (int a = 0; a < NG; ++a) { in[a] = Dual(base[a]); in[a].g[a] = 1.0; }
       Model<Dual> m = make_model<Dual>(o, in[0], in[1], in[2], in[3], in[4], in[5]);
-      rc = price_tc(m, ask, bid, nullptr);
+      rc = price_tc_lines(m, ask, bid);
     }
     out[2 * i] = rc ? NAN : ask.v;
     out[2 * i + 1] = rc ? NAN : bid.v;
