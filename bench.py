@@ -36,12 +36,66 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "tree node updates/s (ask+bid, FP64) batched; options/s with Greeks vs plain"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 dense FP64: 152 SMs x 2.07 GHz x 2 DFMA lanes x 2 flops
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64: 152 SMs x 2.07 GHz x 2 DFMA lanes x 2 flops (context)
+FLOPS_PER_MERGED_POINT = 10  # algorithmic FP64 flops per merged successor breakpoint: the low end
+                             # of the c = 10-15 per (m_u + m_d) of the step-by-step count
 CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_tc_batched<16, false> launch on the
-# 4096-option batch (ncu --metrics ..., one pass), the kernel as built from this source;
-# None when the kernel has changed since the counters were taken
-BATCHED_TRAFFIC = 513273616640 + 1013414508288
+# DRAM traffic of one k_tc_batched launch on the 4096-option batch, from an ncu capture
+# recorded with the hash of the kernel's sources; reported only while the sources match
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_tc_batched_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1110_2477_gb300", "csrc", f)
+                  for f in ("ob_tc.cuh", "ob_team.cuh", "ob_kern.cuh", "ob_batched16.cu")]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the batched kernel from the committed capture record, or None
+    when the kernel's sources have changed since it was taken."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("src_sha256") != kernel_source_hash():
+        return None
+    return int(rec["dram_read_bytes"]) + int(rec["dram_write_bytes"])
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def measure_fp64_peak(local):
+    """FP64 FMA throughput of this GPU (ob_fp64_peak), with the clocks seen while it ran."""
+    import paper_1110_2477_gb300 as ob
+    sampler = ClockSampler(local)
+    sampler.start()
+    tf, ms = ob.ob_fp64_peak(1 << 17)
+    clocks = sampler.stop()
+    return {"tflops": tf, "ms": ms, "clocks": clocks,
+            "how": "ob_fp64_peak: 8 CTAs x 256 threads per SM, 8 independent DFMA chains per thread, "
+                   "CUDA events, fastest of 2 timed runs"}
 
 
 def parse():
@@ -52,6 +106,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-greeks", action="store_true", help="skip the Greeks-vs-plain comparison")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the one-warp-per-option comparison kernel (for profiler captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default team width")
     ap.add_argument("--options", type=int, default=1024,
                     help="greeks workload: the first n of the 1024 puts (smaller for profiling)")
@@ -158,7 +214,8 @@ def cpu_baseline(table, seed=7):
     oracle.price_ask_bid(sample, nthreads=cores)
     dt = time.perf_counter() - t0
     nodes = int(np.sum(W.node_updates(sample)))
-    return {"value": nodes / dt, "unit": "node updates/s", "cores": cores, "kind": "oracle",
+    return {"value": nodes / dt, "unit": "node updates/s", "cores": cores, "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": "%d random options of the 4096-option batch (seed %d), %d node updates, %.1f s"
                       % (CPU_SAMPLE, seed, nodes, dt)}
 
@@ -187,7 +244,8 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched uneven 4096 (N~U{100..2000}, put/call/spread)",
                        "sample_per_step": "16 random options of the batch"},
-            "cpu_baseline": {"value": v, "unit": "node updates/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "node updates/s", "cores": cores, "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": "16 random options per step of the 4096-option batch"},
             "e2e": {"value": v, "unit": "node updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -201,6 +259,7 @@ def run_crr(args, rank, world, local):
 
     import paper_1110_2477_gb300 as ob
     dev = torch.device("cuda", local)
+    peak = measure_fp64_peak(local)
     table = W.crr_puts() if rank == 0 else W.crr_puts(seed=5 + 1000 * rank)
     n = len(table)
     nodes = int(np.sum(table["N"].astype(np.int64) * (table["N"].astype(np.int64) + 1) // 2))
@@ -263,9 +322,10 @@ def run_crr(args, rank, world, local):
         "e2e": {"value": world * nodes * args.steps / e2e_s, "unit": "node updates/s",
                 "h2d_bytes_per_step": int(table.nbytes), "d2h_bytes_per_step": int(n * 8)},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "note": "3 FP64 flops per node (DFMA + DMUL) against the nominal FP64 peak"},
+        "roofline": {"bound": "alu", "achieved": flops, "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": flops / peak["tflops"], "traffic": None,
+                     "note": "3 FP64 flops per node (DFMA + DMUL) against the measured FP64 FMA peak "
+                             "(ob_fp64_peak)", "peak_measurement": peak},
         "put_n20000": {"price": float(bo.item()), "ms": a.elapsed_time(b)},
         "step_ms": step_ms, "clocks": clocks,
     }
@@ -467,6 +527,7 @@ def main():
     st = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB of L2
     stream = torch.cuda.current_stream(dev)
+    peak = measure_fp64_peak(local)
 
     # the autotuner picks the team width (CTA size, per-CTA breakpoint capacity) on a
     # sample of the batch, outside the timed region
@@ -518,14 +579,16 @@ def main():
            "d2h_bytes_per_step": int(pin_out.numel() * 8 + pin_st.numel() * 4)}
 
     # plain single-option kernel on the same batch (one warp per option, no queue)
-    ob.ob_price_ask_bid_plain(params, n, out, st, stream)
-    torch.cuda.synchronize(dev)
-    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pa.record(stream)
-    ob.ob_price_ask_bid_plain(params, n, out, st, stream)
-    pb.record(stream)
-    torch.cuda.synchronize(dev)
-    plain_s = pa.elapsed_time(pb) / 1e3
+    plain_s = None
+    if not args.no_plain:
+        ob.ob_price_ask_bid_plain(params, n, out, st, stream)
+        torch.cuda.synchronize(dev)
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa.record(stream)
+        ob.ob_price_ask_bid_plain(params, n, out, st, stream)
+        pb.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_s = pa.elapsed_time(pb) / 1e3
 
     # options/s with Greeks vs plain pricing: 1024 puts, N = 1000 (seed 4)
     greeks_line = None
@@ -556,8 +619,10 @@ def main():
     if rank != 0:
         return
     avg_step = dev_s / args.steps
-    alg_flops = 2.0 * stats["u_points"] + 4.0 * stats["w_points"] + 2.0 * stats["z_points"]
+    alg_flops = FLOPS_PER_MERGED_POINT * float(stats["u_points"])
+    fma_flops = 2.0 * stats["u_points"] + 4.0 * stats["w_points"] + 2.0 * stats["z_points"]
     achieved = alg_flops / avg_step / 1e12
+    traffic = recorded_traffic() if args.workload == "batched" else None
     line = {
         "metric": METRIC, "value": value, "unit": "node updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * job_s / args.steps,
@@ -573,17 +638,23 @@ def main():
                    "launch": "CUDA graph replay" if stats["graph"] == 2 else
                              ("CUDA graph" if stats["graph"] == 1 else "direct")},
         "options_per_s": world * n * args.steps / job_s,
-        "plain": {"value": nodes_per_step / plain_s, "unit": "node updates/s",
-                  "options_per_s": n / plain_s, "kernel": "one warp per option, index order"},
+        "plain": None if plain_s is None else {
+            "value": nodes_per_step / plain_s, "unit": "node updates/s", "options_per_s": n / plain_s,
+            "kernel": "one warp per option, index order"},
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": BATCHED_TRAFFIC if args.workload == "batched" else None,
-                     "note": "algorithmic FP64 flops = 2U + 4W + 2Z per step (U successor points "
-                             "merged, W points of w, Z points of z), FP64 peak nominal; traffic = "
-                             "DRAM bytes read + written by one k_tc_batched launch of this "
-                             "workload (ncu, one pass)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / peak["tflops"], "traffic": traffic,
+                     "note": "algorithmic FP64 flops = %d per merged successor breakpoint (U per step, "
+                             "counted by the kernel); peak = measured FP64 FMA throughput of this GPU "
+                             "(ob_fp64_peak); traffic = DRAM bytes read + written by one k_tc_batched "
+                             "launch of this workload from the committed ncu record (null when the "
+                             "kernel's sources changed since)" % FLOPS_PER_MERGED_POINT,
+                     "fma_count": {"flops_per_step": fma_flops, "tflops": fma_flops / avg_step / 1e12,
+                                   "frac": fma_flops / avg_step / 1e12 / peak["tflops"],
+                                   "what": "2U + 4W + 2Z: the FMAs the kernel issues per merged point, "
+                                           "point of w and point of z"},
+                     "peak_measurement": peak},
         "breakpoints": {"u_points": stats["u_points"], "w_points": stats["w_points"],
                         "z_points": stats["z_points"], "max_level_points": stats["max_level_points"],
                         "retried": stats["retried"]},

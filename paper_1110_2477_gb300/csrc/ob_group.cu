@@ -1,0 +1,127 @@
+// ob_group.cu -- the whole-GPU form: one cooperative launch of a CTA per SM, each
+// option in turn with every level split over all CTAs (TcGroup), bounded grid barriers.
+#include "ob_kern.cuh"
+
+namespace obl {
+
+// Barrier of all CTAs of the grid.  Thread 0 publishes with a fence and an atomic
+// arrival, the last arrival releases the others by bumping the generation; a wait
+// longer than wait_ns (or 2^30 polls) sets err.  Returns false once err is set.
+__device__ bool grid_barrier(GroupState* gs, unsigned& gen, unsigned long long wait_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = *((volatile int*)&gs->err) == 0;
+    if (ok) {
+      const unsigned want = gen + 1u;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&gs->count, 1u) + 1u;
+      if (arrived == gridDim.x) {
+        atomicExch(&gs->count, 0u);
+        __threadfence();
+        atomicExch(&gs->gen, want);
+      } else {
+        const unsigned long long t0 = global_ns();
+        for (unsigned it = 0;; ++it) {
+          if (*((volatile unsigned*)&gs->gen) == want) break;
+          if (*((volatile int*)&gs->err) != 0) { ok = 0; break; }
+          if (it > (1u << 30) || global_ns() - t0 > wait_ns) {
+            atomicExch(&gs->err, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __threadfence();
+      gen = want;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
+    const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
+    size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds, unsigned long long wait_ns,
+    int skip_cta) {
+  __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
+  __shared__ int s_cnt[kGroupMax];
+  obk::BlockTeam<kGroupNW> bt{tbuf};
+  const int G = gridDim.x, c = blockIdx.x;
+  // test control: this CTA never arrives at any barrier, so the others' bounded waits
+  // run out and every option of the call reports OB_ERR_TIMEOUT
+  if (c == skip_cta) return;
+  char* mine = arena + shared_bytes + (size_t)c * cta_bytes;
+  unsigned gen = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const obk::Opt o = opts[oi];
+    int rc = check_option(o, true);
+    double ask = dnan(), bid = dnan();
+    obk::Stats st;
+    st.upts = st.wpts = st.zpts = 0;
+    st.zmax_level = 0;
+    obk::GroupLay S;
+    obk::Lay Lp;
+    if (rc == obk::ST_OK && (!obk::carve_group_shared(arena, shared_bytes, o.N, 2 * (o.N + 2), S) ||
+                             !obk::carve(mine, cta_bytes, o.N, 16, Lp)))
+      rc = obk::ST_CAPACITY;
+    if (rc == obk::ST_OK) {
+      obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
+      rc = g.begin();
+      if (rc == obk::ST_OK && !grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
+      for (int t = o.N; t >= 0 && rc == obk::ST_OK; --t) {
+        const bool ok = g.compute(t);
+        if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? g.ztot : -1;
+        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
+        int bad = 0;
+        for (int k = threadIdx.x; k < G; k += blockDim.x) {
+          s_cnt[k] = __ldcg(&gs->cnt[t & 1][k]);
+          if (s_cnt[k] < 0) bad = 1;
+        }
+        if (__syncthreads_or(bad)) { rc = obk::ST_CAPACITY; break; }
+        if (!g.publish(t, s_cnt)) { rc = obk::ST_CAPACITY; break; }
+        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
+      }
+      if (rc == obk::ST_OK && c == 0) g.root(ask, bid);
+      st = g.R.st;
+    }
+    if (threadIdx.x == 0) {
+      if (rc == obk::ST_OK) {
+        atomicAdd(&ds->upts, (unsigned long long)st.upts);
+        atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
+        atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
+      }
+      if (c == 0) {
+        out[2 * oi] = rc ? dnan() : ask;
+        out[2 * oi + 1] = rc ? dnan() : bid;
+        if (status) status[oi] = rc;
+        atomicAdd(&ds->options, 1ULL);
+        if (rc == obk::ST_OK) {
+          const unsigned long long N = (unsigned long long)o.N;
+          atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
+          atomicMax(&ds->max_level, st.zmax_level);
+        } else {
+          atomicAdd(&ds->failed, 1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t group_occupancy(int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tc_group, 32 * kGroupNW, 0);
+}
+
+cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
+                         char* arena, size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds,
+                         unsigned long long wait_ns, int skip_cta) {
+  void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
+                  (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds, (void*)&wait_ns,
+                  (void*)&skip_cta};
+  return cudaLaunchCooperativeKernel((const void*)k_tc_group, dim3(G), dim3(32 * kGroupNW), args, 0, s);
+}
+
+}  // namespace obl

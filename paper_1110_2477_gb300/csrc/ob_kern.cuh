@@ -1,0 +1,293 @@
+// ob_kern.cuh -- what the library's translation units share: constants, the
+// per-call counters, option checks, the per-option drivers of the kernels, the
+// batched and Greeks team kernels (templates, instantiated in the units that launch
+// them) and the launch functions each unit defines for the host code in ob_lib.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ob.h"
+#include "ob_adj.cuh"
+#include "ob_tc.cuh"
+
+namespace obl {
+
+constexpr int kBlock = 128;          // CTA of the plain kernel and of the CRR kernel (4 warps)
+constexpr int kNW = 8;               // warps of a CTA of the batched kernel
+constexpr int kTeamBlock = 32 * kNW;
+constexpr int kTiers = 3;            // launches per ob_price_ask_bid call
+constexpr int kTier1Ctas = 16;       // CTAs of the first follow-up launch
+constexpr int kSortMax = 8192;       // largest batch ordered by cost
+constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
+constexpr double kHeavyFactor = 0.0; // heavy: predicted cost > factor x (total / warps); 0: all
+// control words
+enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
+       C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
+
+constexpr int ST_TIMEOUT = -4;  // OB_ERR_TIMEOUT: a bounded device wait ran out
+
+struct DevStats {
+  unsigned long long options, node_updates, upts, wpts, zpts;
+  int max_level, retried, failed, tiers;
+};
+
+static_assert(sizeof(ob_option_t) == 64, "ob_option_t must be 64 bytes");
+static_assert(sizeof(obk::Opt) == 64, "Opt must be 64 bytes");
+
+__device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+__device__ __forceinline__ int check_option(const obk::Opt& o, bool need_k) {
+  if (!(o.N >= 1) || o.N > (1 << 26) || !(o.S0 > 0.0) || !(o.sigma > 0.0) || !(o.T > 0.0) ||
+      !(o.K >= 0.0) || !isfinite(o.R) || !isfinite(o.S0) || !isfinite(o.K) || !isfinite(o.sigma) ||
+      !isfinite(o.T) || o.payoff < 0 || o.payoff > 2)
+    return obk::ST_ARG;
+  if (need_k && !(o.k >= 0.0 && o.k < 1.0)) return obk::ST_ARG;
+  if (o.payoff == obk::PAY_SPREAD && !(o.K2 >= o.K && isfinite(o.K2))) return obk::ST_ARG;
+  return obk::ST_OK;
+}
+
+// ------------------------------------------------------------------ ordering
+// Predicted work of an option: node updates times an estimate of the
+// breakpoints per node (both parties).  Puts keep about one breakpoint per
+// node and party; calls and cash-settled spreads gather many once
+// x = k / (sigma sqrt(T/N)) exceeds ~1 (pieces whose slopes stay inside the
+// bid/ask window survive more levels).  Fitted to the oracle's counts on the
+// batched workload; only the ordering and the warp/CTA split depend on it.
+__device__ __forceinline__ double predicted_cost(const obk::Opt& o) {
+  const double N = o.N > 0 ? (double)o.N : 1.0;
+  const double nodes = (N + 1.0) * (N + 2.0) * 0.5;
+  const double sd = (o.sigma > 0.0 && o.T > 0.0) ? o.sigma * sqrt(o.T / N) : 1.0;
+  const double x = (o.k > 0.0) ? o.k / sd : 0.0;
+  double m = 2.0;
+  if (x > 1.0) {
+    if (o.payoff == obk::PAY_CALL) m += 1.5 * x;
+    else if (o.payoff == obk::PAY_SPREAD) m += x * x;
+  }
+  double c = nodes * m;
+  return c < 1e12 ? c : 1e12;
+}
+
+// ------------------------------------------------------------------ induction with costs
+template <class Team, bool CHIP = false>
+__device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
+                                          int& rc, double& ask, double& bid, obk::Stats& st,
+                                          const obk::WBuf* chip = nullptr) {
+  rc = check_option(o, true);
+  ask = dnan();
+  bid = dnan();
+  st.upts = st.wpts = st.zpts = 0;
+  st.zmax_level = 0;
+  if (rc != obk::ST_OK) return;
+  obk::Lay L;
+  if (!obk::carve(slice, bytes, o.N, 2 * (o.N + 2), L)) {
+    rc = obk::ST_CAPACITY;
+    return;
+  }
+  obk::TcRun<Team, CHIP> R(tm, o, L);
+  if (CHIP) R.chip = *chip;
+  rc = R.run(ask, bid);
+  st = R.st;
+}
+
+// Record an option's result (one thread); a capacity failure goes to the retry
+// list when a follow-up launch exists.
+__device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, const obk::Stats& st,
+                                       const obk::Opt& o, double* out, int* status, int* ovf_count,
+                                       int* ovf_list, bool retry, DevStats* ds) {
+  if (rc == obk::ST_CAPACITY && retry) {
+    const int pos = atomicAdd(ovf_count, 1);
+    ovf_list[pos] = oi;
+    atomicAdd(&ds->retried, 1);
+    return;
+  }
+  out[2 * oi] = rc ? dnan() : ask;
+  out[2 * oi + 1] = rc ? dnan() : bid;
+  if (status) status[oi] = rc;
+  atomicAdd(&ds->options, 1ULL);
+  if (rc == obk::ST_OK) {
+    const unsigned long long N = (unsigned long long)o.N;
+    atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
+    atomicAdd(&ds->upts, (unsigned long long)st.upts);
+    atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
+    atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
+    atomicMax(&ds->max_level, st.zmax_level);
+  } else {
+    atomicAdd(&ds->failed, 1);
+  }
+}
+
+// Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
+// one at a time as a whole-CTA team, then each of its warps takes the remaining
+// options one at a time from a second queue.  Both queues are device counters.
+// CHIP: the CTA's dynamic shared memory holds the w arrays of chip_points points (the
+// fused level step of CTA teams, TcRun::level_fused).
+template <int NW, bool WARPS, bool CHIP = false>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
+    const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
+    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds, int chip_points) {
+  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+  extern __shared__ __align__(16) char chip_smem[];
+  obk::BlockTeam<NW> bt{tbuf};
+  const obk::WBuf chip = obk::carve_wbuf(chip_smem, chip_points);
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  const int nh = order ? *((volatile int*)&ctl[C_NHEAVY]) : 0;
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_HEAVY_HEAD], 1);
+    const int idx = bt.bcast0(v);
+    if (idx >= nh) break;
+    const int oi = order[idx];
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one<obk::BlockTeam<NW>, CHIP>(bt, o, my, cta_bytes, rc, ask, bid, st, &chip);
+    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    bt.sync();
+  }
+  if (!WARPS) return;  // every option went to a CTA team
+  obk::WarpTeam wt;
+  const size_t wbytes = (cta_bytes / NW) & ~(size_t)255;
+  char* wmy = my + (size_t)(threadIdx.x >> 5) * wbytes;
+  for (;;) {
+    int v = 0;
+    if (wt.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int idx = wt.bcast0(v) + nh;
+    if (idx >= n) break;
+    const int oi = order ? order[idx] : idx;
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one(wt, o, wmy, wbytes, rc, ask, bid, st);
+    if (wt.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    wt.sync();
+  }
+}
+
+// ------------------------------------------------------------------ whole-GPU form
+// Each option in turn on every SM: the CTAs split each level's nodes (TcGroup) and
+// meet at two grid barriers per level.  Launched cooperatively, so all CTAs are
+// resident; every wait is bounded.
+constexpr int kGroupMax = 1024;                                    // CTAs of the grid at most
+constexpr unsigned long long kGroupWaitNs = 10000000000ULL;        // 10 s per barrier wait
+constexpr int kGroupNW = 16;                                       // warps per CTA
+
+struct GroupState {
+  unsigned int count;  // arrivals at the current barrier
+  unsigned int gen;    // barriers completed
+  int err;             // a wait ran out: every later barrier fails at once
+  int pad;
+  int cnt[2][kGroupMax];  // points of each CTA's share of a level (-1: overflow)
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ------------------------------------------------------------------ adjoint (Greeks)
+template <class Team>
+__device__ __forceinline__ void greeks_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
+                                           int& rc, double& ask, double& bid, double* gA, double* gB) {
+  rc = check_option(o, true);
+  ask = dnan();
+  bid = dnan();
+  if (rc != obk::ST_OK) return;
+  obk::Lay L;
+  obk::AdjLay A;
+  if (!obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A)) {
+    rc = obk::ST_CAPACITY;
+    return;
+  }
+  obk::TcRun<Team> R(tm, o, L);
+  obk::TcAdj<Team> G(R, A);
+  rc = G.run(ask, bid, gA, gB);
+}
+
+__device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double bid, const double* gA,
+                                              const double* gB, double* out, double* grad, int* status,
+                                              int* ovf_count, int* ovf_list, bool retry) {
+  if (rc == obk::ST_CAPACITY && retry) {
+    const int pos = atomicAdd(ovf_count, 1);
+    ovf_list[pos] = oi;
+    return;
+  }
+  out[2 * oi] = rc ? dnan() : ask;
+  out[2 * oi + 1] = rc ? dnan() : bid;
+  for (int k = 0; k < obk::NPAR; ++k) {
+    grad[12 * (size_t)oi + k] = rc ? dnan() : gA[k];
+    grad[12 * (size_t)oi + 6 + k] = rc ? dnan() : gB[k];
+  }
+  if (status) status[oi] = rc;
+}
+
+// Greeks on CTA teams: each CTA takes options from the queue over [0, n) as one team.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 8 / NW) k_greeks_team(
+    const obk::Opt* __restrict__ opts, int n, double* out, double* grad, int* status, char* arena,
+    size_t cta_bytes, int* ctl, int* ovf_list) {
+  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+  obk::BlockTeam<NW> bt{tbuf};
+  char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  for (;;) {
+    int v = 0;
+    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int oi = bt.bcast0(v);
+    if (oi >= n) break;
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
+    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
+    if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
+    bt.sync();
+  }
+}
+
+
+// ------------------------------------------------------------------ launch functions
+// Arguments of the batched kernel.
+struct BatchedArgs {
+  const obk::Opt* opts;
+  int n;
+  const int* order;
+  double* out;
+  int* status;
+  char* arena;
+  size_t cta_bytes;
+  int* ctl;
+  int* ovf_list;
+  DevStats* ds;
+  int chip_points;
+};
+
+// k_tc_batched<nw, warps, chip> on `grid` CTAs (ob_batched16.cu: nw 16, 12; ob_batched8.cu:
+// nw 8, 4 and the on-chip instantiations of nw 16, 8).
+cudaError_t launch_batched_wide(int nw, bool warps, int grid, cudaStream_t s, const BatchedArgs& a);
+cudaError_t launch_batched_narrow(int nw, bool warps, bool chip, int grid, size_t smem, cudaStream_t s,
+                                  const BatchedArgs& a);
+cudaError_t set_chip_smem(int bytes16, int bytes8);
+
+// ob_tiers.cu
+cudaError_t launch_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, int* status, char* arena,
+                         size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count,
+                         int* ovf_list, int last, DevStats* ds);
+cudaError_t launch_plain(int blocks, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
+                         char* arena, size_t wbytes, int nworkers, DevStats* ds);
+
+// ob_group.cu
+cudaError_t group_occupancy(int* per_sm);
+cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
+                         char* arena, size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds,
+                         unsigned long long wait_ns, int skip_cta);
+
+// ob_greeks8.cu (8-warp CTA teams) and ob_greeks.cu (the follow-up launches)
+cudaError_t launch_greeks_team8(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
+                                int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list);
+cudaError_t launch_greeks_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, double* grad,
+                                int* status, char* arena, size_t cta_bytes, const int* in_count,
+                                const int* in_list, int* head, int* ovf_count, int* ovf_list, int last);
+
+}  // namespace obl

@@ -1,17 +1,20 @@
-// ob_lib.cu -- kernels and the C ABI declared in include/ob.h.
-//
+// ob_lib.cu -- the host side of the C ABI declared in include/ob.h (scratch pool,
+// call ordering, CUDA graphs, entry points) and the small kernels:
 //  k_order        one CTA sorts the option indices by predicted cost (largest first)
-//  k_tc_batched   persistent CTAs: each takes options from a device queue and runs the
-//                 piecewise-linear induction (ob_tc.cuh) on a whole-CTA team in its own
-//                 slice of the scratch pool; an option that outgrows the slice goes to an
-//                 overflow list that the follow-up launches (k_tc_retry: 16 CTAs, then one,
-//                 larger slices) take over on the same stream
-//  k_tc_plain     one warp per option in index order (the comparison kernel)
-//  k_tc_group     one cooperative launch of a CTA per SM: each option in turn, every level
-//                 split over all CTAs (TcGroup), bounded grid barriers
-//  k_greeks_team  the adjoint (ob_adj.cuh) on CTA teams, with warp and retry variants
 //  k_crr          persistent warps: plain CRR recursion without costs, the level kept in
 //                 shared memory and updated in place
+//  k_gather, k_fp64_probe   the autotuner's sample; the FP64 throughput probe
+// The induction kernels live in their own translation units (compiled in parallel):
+//  ob_batched16.cu, ob_batched8.cu   k_tc_batched: persistent CTAs take options from a
+//                 device queue and run the piecewise-linear induction (ob_tc.cuh) on a
+//                 whole-CTA team in their slice of the scratch pool; an option that
+//                 outgrows its slice goes to an overflow list
+//  ob_tiers.cu    k_tc_retry (the follow-up launches: 16 CTAs, then one, larger slices)
+//                 and k_tc_plain (one warp per option in index order)
+//  ob_group.cu    k_tc_group: one cooperative launch of a CTA per SM, each option in
+//                 turn, every level split over all CTAs (TcGroup), bounded grid barriers
+//  ob_greeks8.cu, ob_greeks.cu   the adjoint (ob_adj.cuh) on CTA teams, single warps,
+//                 and its follow-up launches
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,66 +24,11 @@
 
 #include <mutex>
 
-#include "ob.h"
-#include "ob_adj.cuh"
-#include "ob_tc.cuh"
+#include "ob_kern.cuh"
+
+using namespace obl;
 
 namespace {
-
-constexpr int kBlock = 128;          // CTA of the plain kernel and of the CRR kernel (4 warps)
-constexpr int kNW = 8;               // warps of a CTA of the batched kernel
-constexpr int kTeamBlock = 32 * kNW;
-constexpr int kTiers = 3;            // launches per ob_price_ask_bid call
-constexpr int kTier1Ctas = 16;       // CTAs of the first follow-up launch
-constexpr int kSortMax = 8192;       // largest batch ordered by cost
-constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
-constexpr double kHeavyFactor = 0.0; // heavy: predicted cost > factor x (total / warps); 0: all
-// control words
-enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
-       C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
-
-constexpr int ST_TIMEOUT = -4;  // OB_ERR_TIMEOUT: a bounded device wait ran out
-
-struct DevStats {
-  unsigned long long options, node_updates, upts, wpts, zpts;
-  int max_level, retried, failed, tiers;
-};
-
-static_assert(sizeof(ob_option_t) == 64, "ob_option_t must be 64 bytes");
-static_assert(sizeof(obk::Opt) == 64, "Opt must be 64 bytes");
-
-__device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
-
-__device__ __forceinline__ int check_option(const obk::Opt& o, bool need_k) {
-  if (!(o.N >= 1) || o.N > (1 << 26) || !(o.S0 > 0.0) || !(o.sigma > 0.0) || !(o.T > 0.0) ||
-      !(o.K >= 0.0) || !isfinite(o.R) || !isfinite(o.S0) || !isfinite(o.K) || !isfinite(o.sigma) ||
-      !isfinite(o.T) || o.payoff < 0 || o.payoff > 2)
-    return obk::ST_ARG;
-  if (need_k && !(o.k >= 0.0 && o.k < 1.0)) return obk::ST_ARG;
-  if (o.payoff == obk::PAY_SPREAD && !(o.K2 >= o.K && isfinite(o.K2))) return obk::ST_ARG;
-  return obk::ST_OK;
-}
-
-// ------------------------------------------------------------------ ordering
-// Predicted work of an option: node updates times an estimate of the
-// breakpoints per node (both parties).  Puts keep about one breakpoint per
-// node and party; calls and cash-settled spreads gather many once
-// x = k / (sigma sqrt(T/N)) exceeds ~1 (pieces whose slopes stay inside the
-// bid/ask window survive more levels).  Fitted to the oracle's counts on the
-// batched workload; only the ordering and the warp/CTA split depend on it.
-__device__ __forceinline__ double predicted_cost(const obk::Opt& o) {
-  const double N = o.N > 0 ? (double)o.N : 1.0;
-  const double nodes = (N + 1.0) * (N + 2.0) * 0.5;
-  const double sd = (o.sigma > 0.0 && o.T > 0.0) ? o.sigma * sqrt(o.T / N) : 1.0;
-  const double x = (o.k > 0.0) ? o.k / sd : 0.0;
-  double m = 2.0;
-  if (x > 1.0) {
-    if (o.payoff == obk::PAY_CALL) m += 1.5 * x;
-    else if (o.payoff == obk::PAY_SPREAD) m += x * x;
-  }
-  double c = nodes * m;
-  return c < 1e12 ? c : 1e12;
-}
 
 // Bitonic sort of (cost, index) keys, descending, in one CTA; also decides how
 // many of the costliest options go to whole-CTA teams (ctl[C_NHEAVY]).
@@ -126,382 +74,6 @@ __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int*
       while (nh < n && (double)(keys[nh] >> 20) > thr) ++nh;
     }
     ctl[C_NHEAVY] = nh;
-  }
-}
-
-// ------------------------------------------------------------------ induction with costs
-template <class Team, bool CHIP = false>
-__device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
-                                          int& rc, double& ask, double& bid, obk::Stats& st,
-                                          const obk::WBuf* chip = nullptr) {
-  rc = check_option(o, true);
-  ask = dnan();
-  bid = dnan();
-  st.upts = st.wpts = st.zpts = 0;
-  st.zmax_level = 0;
-  if (rc != obk::ST_OK) return;
-  obk::Lay L;
-  if (!obk::carve(slice, bytes, o.N, 2 * (o.N + 2), L)) {
-    rc = obk::ST_CAPACITY;
-    return;
-  }
-  obk::TcRun<Team, CHIP> R(tm, o, L);
-  if (CHIP) R.chip = *chip;
-  rc = R.run(ask, bid);
-  st = R.st;
-}
-
-// Record an option's result (one thread); a capacity failure goes to the retry
-// list when a follow-up launch exists.
-__device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, const obk::Stats& st,
-                                       const obk::Opt& o, double* out, int* status, int* ovf_count,
-                                       int* ovf_list, bool retry, DevStats* ds) {
-  if (rc == obk::ST_CAPACITY && retry) {
-    const int pos = atomicAdd(ovf_count, 1);
-    ovf_list[pos] = oi;
-    atomicAdd(&ds->retried, 1);
-    return;
-  }
-  out[2 * oi] = rc ? dnan() : ask;
-  out[2 * oi + 1] = rc ? dnan() : bid;
-  if (status) status[oi] = rc;
-  atomicAdd(&ds->options, 1ULL);
-  if (rc == obk::ST_OK) {
-    const unsigned long long N = (unsigned long long)o.N;
-    atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
-    atomicAdd(&ds->upts, (unsigned long long)st.upts);
-    atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
-    atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
-    atomicMax(&ds->max_level, st.zmax_level);
-  } else {
-    atomicAdd(&ds->failed, 1);
-  }
-}
-
-// Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
-// one at a time as a whole-CTA team, then each of its warps takes the remaining
-// options one at a time from a second queue.  Both queues are device counters.
-// CHIP: the CTA's dynamic shared memory holds the w arrays of chip_points points (the
-// fused level step of CTA teams, TcRun::level_fused).
-template <int NW, bool WARPS, bool CHIP = false>
-__global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
-    const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
-    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds, int chip_points) {
-  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
-  extern __shared__ __align__(16) char chip_smem[];
-  obk::BlockTeam<NW> bt{tbuf};
-  const obk::WBuf chip = obk::carve_wbuf(chip_smem, chip_points);
-  char* my = arena + (size_t)blockIdx.x * cta_bytes;
-  const int nh = order ? *((volatile int*)&ctl[C_NHEAVY]) : 0;
-  for (;;) {
-    int v = 0;
-    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_HEAVY_HEAD], 1);
-    const int idx = bt.bcast0(v);
-    if (idx >= nh) break;
-    const int oi = order[idx];
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid;
-    obk::Stats st;
-    price_one<obk::BlockTeam<NW>, CHIP>(bt, o, my, cta_bytes, rc, ask, bid, st, &chip);
-    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
-    bt.sync();
-  }
-  if (!WARPS) return;  // every option went to a CTA team
-  obk::WarpTeam wt;
-  const size_t wbytes = (cta_bytes / NW) & ~(size_t)255;
-  char* wmy = my + (size_t)(threadIdx.x >> 5) * wbytes;
-  for (;;) {
-    int v = 0;
-    if (wt.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
-    const int idx = wt.bcast0(v) + nh;
-    if (idx >= n) break;
-    const int oi = order ? order[idx] : idx;
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid;
-    obk::Stats st;
-    price_one(wt, o, wmy, wbytes, rc, ask, bid, st);
-    if (wt.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
-    wt.sync();
-  }
-}
-
-// Follow-up launch: the options of in_list (count at *in_count), one per CTA,
-// with larger slices.
-__global__ void __launch_bounds__(kTeamBlock, 2) k_tc_retry(
-    const obk::Opt* __restrict__ opts, double* out, int* status, char* arena, size_t cta_bytes,
-    const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list, int last,
-    DevStats* ds) {
-  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
-  obk::BlockTeam<kNW> bt{tbuf};
-  char* my = arena + (size_t)blockIdx.x * cta_bytes;
-  const int cnt = *((volatile const int*)in_count);
-  for (;;) {
-    int v = 0;
-    if (threadIdx.x == 0) v = atomicAdd(head, 1);
-    const int idx = bt.bcast0(v);
-    if (idx >= cnt) break;
-    const int oi = in_list[idx];
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid;
-    obk::Stats st;
-    price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
-    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, ovf_count, ovf_list, !last, ds);
-    bt.sync();
-  }
-}
-
-// ------------------------------------------------------------------ whole-GPU form
-// Each option in turn on every SM: the CTAs split each level's nodes (TcGroup) and
-// meet at two grid barriers per level.  Launched cooperatively, so all CTAs are
-// resident; every wait is bounded.
-constexpr int kGroupMax = 1024;                                    // CTAs of the grid at most
-constexpr unsigned long long kGroupWaitNs = 10000000000ULL;        // 10 s per barrier wait
-constexpr int kGroupNW = 16;                                       // warps per CTA
-
-struct GroupState {
-  unsigned int count;  // arrivals at the current barrier
-  unsigned int gen;    // barriers completed
-  int err;             // a wait ran out: every later barrier fails at once
-  int pad;
-  int cnt[2][kGroupMax];  // points of each CTA's share of a level (-1: overflow)
-};
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Barrier of all CTAs of the grid.  Thread 0 publishes with a fence and an atomic
-// arrival, the last arrival releases the others by bumping the generation; a wait
-// longer than wait_ns (or 2^30 polls) sets err.  Returns false once err is set.
-__device__ bool grid_barrier(GroupState* gs, unsigned& gen, unsigned long long wait_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = *((volatile int*)&gs->err) == 0;
-    if (ok) {
-      const unsigned want = gen + 1u;
-      __threadfence();
-      const unsigned arrived = atomicAdd(&gs->count, 1u) + 1u;
-      if (arrived == gridDim.x) {
-        atomicExch(&gs->count, 0u);
-        __threadfence();
-        atomicExch(&gs->gen, want);
-      } else {
-        const unsigned long long t0 = global_ns();
-        for (unsigned it = 0;; ++it) {
-          if (*((volatile unsigned*)&gs->gen) == want) break;
-          if (*((volatile int*)&gs->err) != 0) { ok = 0; break; }
-          if (it > (1u << 30) || global_ns() - t0 > wait_ns) {
-            atomicExch(&gs->err, 1);
-            ok = 0;
-            break;
-          }
-          __nanosleep(128);
-        }
-      }
-      __threadfence();
-      gen = want;
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-__global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
-    const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
-    size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds, unsigned long long wait_ns,
-    int skip_cta) {
-  __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
-  __shared__ int s_cnt[kGroupMax];
-  obk::BlockTeam<kGroupNW> bt{tbuf};
-  const int G = gridDim.x, c = blockIdx.x;
-  // test control: this CTA never arrives at any barrier, so the others' bounded waits
-  // run out and every option of the call reports OB_ERR_TIMEOUT
-  if (c == skip_cta) return;
-  char* mine = arena + shared_bytes + (size_t)c * cta_bytes;
-  unsigned gen = 0;
-  for (int oi = 0; oi < n; ++oi) {
-    const obk::Opt o = opts[oi];
-    int rc = check_option(o, true);
-    double ask = dnan(), bid = dnan();
-    obk::Stats st;
-    st.upts = st.wpts = st.zpts = 0;
-    st.zmax_level = 0;
-    obk::GroupLay S;
-    obk::Lay Lp;
-    if (rc == obk::ST_OK && (!obk::carve_group_shared(arena, shared_bytes, o.N, 2 * (o.N + 2), S) ||
-                             !obk::carve(mine, cta_bytes, o.N, 16, Lp)))
-      rc = obk::ST_CAPACITY;
-    if (rc == obk::ST_OK) {
-      obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
-      rc = g.begin();
-      if (rc == obk::ST_OK && !grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
-      for (int t = o.N; t >= 0 && rc == obk::ST_OK; --t) {
-        const bool ok = g.compute(t);
-        if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? g.ztot : -1;
-        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
-        int bad = 0;
-        for (int k = threadIdx.x; k < G; k += blockDim.x) {
-          s_cnt[k] = __ldcg(&gs->cnt[t & 1][k]);
-          if (s_cnt[k] < 0) bad = 1;
-        }
-        if (__syncthreads_or(bad)) { rc = obk::ST_CAPACITY; break; }
-        if (!g.publish(t, s_cnt)) { rc = obk::ST_CAPACITY; break; }
-        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
-      }
-      if (rc == obk::ST_OK && c == 0) g.root(ask, bid);
-      st = g.R.st;
-    }
-    if (threadIdx.x == 0) {
-      if (rc == obk::ST_OK) {
-        atomicAdd(&ds->upts, (unsigned long long)st.upts);
-        atomicAdd(&ds->wpts, (unsigned long long)st.wpts);
-        atomicAdd(&ds->zpts, (unsigned long long)st.zpts);
-      }
-      if (c == 0) {
-        out[2 * oi] = rc ? dnan() : ask;
-        out[2 * oi + 1] = rc ? dnan() : bid;
-        if (status) status[oi] = rc;
-        atomicAdd(&ds->options, 1ULL);
-        if (rc == obk::ST_OK) {
-          const unsigned long long N = (unsigned long long)o.N;
-          atomicAdd(&ds->node_updates, (N + 1) * (N + 2) / 2);
-          atomicMax(&ds->max_level, st.zmax_level);
-        } else {
-          atomicAdd(&ds->failed, 1);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Plain form: one warp per option, static assignment in index order, no retry.
-__global__ void __launch_bounds__(kBlock) k_tc_plain(const obk::Opt* __restrict__ opts, int n,
-                                                     double* out, int* status, char* arena,
-                                                     size_t wbytes, int nworkers, DevStats* ds) {
-  obk::WarpTeam tm;
-  const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (wid >= nworkers) return;
-  char* my = arena + (size_t)wid * wbytes;
-  for (int oi = wid; oi < n; oi += nworkers) {
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid;
-    obk::Stats st;
-    price_one(tm, o, my, wbytes, rc, ask, bid, st);
-    if (tm.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, nullptr, nullptr, false, ds);
-    tm.sync();
-  }
-}
-
-// ------------------------------------------------------------------ adjoint (Greeks)
-template <class Team>
-__device__ __forceinline__ void greeks_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
-                                           int& rc, double& ask, double& bid, double* gA, double* gB) {
-  rc = check_option(o, true);
-  ask = dnan();
-  bid = dnan();
-  if (rc != obk::ST_OK) return;
-  obk::Lay L;
-  obk::AdjLay A;
-  if (!obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A)) {
-    rc = obk::ST_CAPACITY;
-    return;
-  }
-  obk::TcRun<Team> R(tm, o, L);
-  obk::TcAdj<Team> G(R, A);
-  rc = G.run(ask, bid, gA, gB);
-}
-
-__device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double bid, const double* gA,
-                                              const double* gB, double* out, double* grad, int* status,
-                                              int* ovf_count, int* ovf_list, bool retry) {
-  if (rc == obk::ST_CAPACITY && retry) {
-    const int pos = atomicAdd(ovf_count, 1);
-    ovf_list[pos] = oi;
-    return;
-  }
-  out[2 * oi] = rc ? dnan() : ask;
-  out[2 * oi + 1] = rc ? dnan() : bid;
-  for (int k = 0; k < obk::NPAR; ++k) {
-    grad[12 * (size_t)oi + k] = rc ? dnan() : gA[k];
-    grad[12 * (size_t)oi + 6 + k] = rc ? dnan() : gB[k];
-  }
-  if (status) status[oi] = rc;
-}
-
-// One warp per option from a device queue; an option that outgrows its slice is
-// handed to the CTA-team launch that follows.
-__global__ void __launch_bounds__(kBlock) k_greeks(const obk::Opt* __restrict__ opts, int n, double* out,
-                                                   double* grad, int* status, char* arena, size_t wbytes,
-                                                   int nworkers, int* ctl, int* ovf_list) {
-  obk::WarpTeam tm;
-  const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  if (wid >= nworkers) return;
-  char* my = arena + (size_t)wid * wbytes;
-  for (;;) {
-    int v = 0;
-    if (tm.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
-    const int oi = tm.bcast0(v);
-    if (oi >= n) break;
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
-    greeks_one(tm, o, my, wbytes, rc, ask, bid, gA, gB);
-    if (tm.lane() == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
-    tm.sync();
-  }
-}
-
-// Greeks on CTA teams: each CTA takes options from the queue over [0, n) as one team.
-template <int NW>
-__global__ void __launch_bounds__(32 * NW, 8 / NW) k_greeks_team(
-    const obk::Opt* __restrict__ opts, int n, double* out, double* grad, int* status, char* arena,
-    size_t cta_bytes, int* ctl, int* ovf_list) {
-  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
-  obk::BlockTeam<NW> bt{tbuf};
-  char* my = arena + (size_t)blockIdx.x * cta_bytes;
-  for (;;) {
-    int v = 0;
-    if (threadIdx.x == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
-    const int oi = bt.bcast0(v);
-    if (oi >= n) break;
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
-    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
-    if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
-    bt.sync();
-  }
-}
-
-__global__ void __launch_bounds__(kTeamBlock, 1) k_greeks_retry(
-    const obk::Opt* __restrict__ opts, double* out, double* grad, int* status, char* arena,
-    size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list,
-    int last) {
-  __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
-  obk::BlockTeam<kNW> bt{tbuf};
-  char* my = arena + (size_t)blockIdx.x * cta_bytes;
-  const int cnt = *((volatile const int*)in_count);
-  for (;;) {
-    int v = 0;
-    if (threadIdx.x == 0) v = atomicAdd(head, 1);
-    const int idx = bt.bcast0(v);
-    if (idx >= cnt) break;
-    const int oi = in_list[idx];
-    const obk::Opt o = opts[oi];
-    int rc;
-    double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
-    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
-    if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, ovf_count, ovf_list, !last);
-    bt.sync();
   }
 }
 
@@ -651,7 +223,6 @@ struct DevPool {
   size_t fixed_bytes = 0;         // OB_POOL_MB: the pool has exactly this size
   double heavy_factor = kHeavyFactor;
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
-  int greeks_team = 8;  // Greeks: warps per CTA team (4 or 8); 0: one warp per option
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -739,7 +310,6 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
       if (v == 4 || v == 8 || v == 12 || v == 16) P.team_warps = v;
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
-    if (const char* g = getenv("OB_GREEKS_TEAM")) P.greeks_team = atoi(g);
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
     if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
@@ -747,10 +317,8 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
             cudaSuccess ||
         (e = cudaDeviceGetAttribute(&P.smem_cta, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
       return cuda_fail(e);
-    if ((e = cudaFuncSetAttribute(k_tc_batched<16, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  chip_smem_cap(P.smem_sm, P.smem_cta, 16))) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_tc_batched<8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  chip_smem_cap(P.smem_sm, P.smem_cta, 8))) != cudaSuccess)
+    if ((e = set_chip_smem(chip_smem_cap(P.smem_sm, P.smem_cta, 16), chip_smem_cap(P.smem_sm, P.smem_cta, 8))) !=
+        cudaSuccess)
       return cuda_fail(e);
     if (cudaMalloc(&P.ctl, sizeof(int) * C_WORDS) != cudaSuccess ||
         cudaMalloc(&P.order, sizeof(int) * kSortMax) != cudaSuccess ||
@@ -877,8 +445,8 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
     if (wbytes > kPlainWarpBytes) wbytes = kPlainWarpBytes;
     wbytes &= ~(size_t)255;
     const int blocks = (workers * 32 + kBlock - 1) / kBlock;
-    k_tc_plain<<<blocks, kBlock, 0, s>>>(opts, n, out, status, P->arena, wbytes, workers, P->stats);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_plain(blocks, s, opts, n, out, status, P->arena, wbytes, workers, P->stats)) != cudaSuccess)
+      return cuda_fail(e);
     P->last_tiers = 1;
     P->last_graph = 0;
     return co.end();
@@ -926,36 +494,19 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
   // the on-chip w arrays of the fused level step (CTA teams of 16 or 8 warps only)
   const int chip = (warps || (P->team_warps != 16 && P->team_warps != 8)) ? 0 : chip_points(P, P->team_warps);
   const size_t chip_bytes = (size_t)chip * obk::WBUF_POINT_BYTES;
-#define OB_LAUNCH_BATCHED(NWV)                                                                      \
-  (warps ? k_tc_batched<NWV, true><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena,  \
-                                                              cta_bytes, P->ctl, list0, P->stats, 0) \
-         : k_tc_batched<NWV, false><<<nctas, 32 * NWV, 0, s>>>(opts, n, order, out, status, P->arena, \
-                                                               cta_bytes, P->ctl, list0, P->stats, 0))
-  if (chip > 0 && P->team_warps == 16)
-    k_tc_batched<16, false, true><<<nctas, 512, chip_bytes, s>>>(opts, n, order, out, status, P->arena,
-                                                                 cta_bytes, P->ctl, list0, P->stats, chip);
-  else if (chip > 0)
-    k_tc_batched<8, false, true><<<nctas, 256, chip_bytes, s>>>(opts, n, order, out, status, P->arena,
-                                                                cta_bytes, P->ctl, list0, P->stats, chip);
-  else if (P->team_warps == 4)
-    OB_LAUNCH_BATCHED(4);
-  else if (P->team_warps == 12)
-    OB_LAUNCH_BATCHED(12);
-  else if (P->team_warps == 16)
-    OB_LAUNCH_BATCHED(16);
+const BatchedArgs ba{opts, n, order, out, status, P->arena, cta_bytes, P->ctl, list0, P->stats, chip};
+  if (chip > 0 || P->team_warps == 8 || P->team_warps == 4)
+    e = launch_batched_narrow(P->team_warps, warps, chip > 0, nctas, chip_bytes, s, ba);
   else
-    OB_LAUNCH_BATCHED(8);
-#undef OB_LAUNCH_BATCHED
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    e = launch_batched_wide(P->team_warps, warps, nctas, s, ba);
+  if (e != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
-  k_tc_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF],
-                                               list0, &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0,
-                                               P->stats);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, P->arena, P->arena_bytes & ~(size_t)255,
-                                      &P->ctl[C_T1_OVF], list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF],
-                                      nullptr, 1, P->stats);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  e = launch_retry(kTier1Ctas, s, opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF], list0,
+                   &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0, P->stats);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_retry(1, s, opts, out, status, P->arena, P->arena_bytes & ~(size_t)255, &P->ctl[C_T1_OVF], list1,
+                   &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF], nullptr, 1, P->stats);
+  if (e != cudaSuccess) return cuda_fail(e);
   P->last_tiers = kTiers + (order ? 1 : 0);
   return OB_OK;
 }
@@ -1081,9 +632,7 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
     if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess)
       return cuda_fail(e);
     if (!coop) return OB_ERR_CUDA;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_group, 32 * kGroupNW, 0)) !=
-        cudaSuccess)
-      return cuda_fail(e);
+    if ((e = group_occupancy(&per_sm)) != cudaSuccess) return cuda_fail(e);
     if (per_sm < 1) return OB_ERR_CUDA;
     int G = P->sms;  // one CTA per SM
     if (G > kGroupMax) G = kGroupMax;
@@ -1113,11 +662,8 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
     --P->test_skip_calls;
     skip_cta = G - 1;
   }
-  void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
-                  (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds, (void*)&wait_ns,
-                  (void*)&skip_cta};
-  if ((e = cudaLaunchCooperativeKernel((const void*)k_tc_group, dim3(G), dim3(32 * kGroupNW), args, 0,
-                                       s)) != cudaSuccess)
+  if ((e = launch_group(G, s, opts, n, out, status, arena, shared_bytes, cta_bytes, gs, ds, wait_ns, skip_cta)) !=
+      cudaSuccess)
     return cuda_fail(e);
   P->last_tiers = 1;
   P->last_graph = 0;
@@ -1164,9 +710,7 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   int rc = pool_get(&P, &dev);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_call_mu[dev]);
-  const int gteam = P->greeks_team;
-  const bool teams = gteam == 4 || gteam == 8;
-  const int per_sm = teams ? 8 / gteam : 8;  // CTA teams, or warps of the one-warp form
+  const int per_sm = 1;  // one 8-warp CTA team per SM
   const int max_workers = P->sms * per_sm;
   const int workers = n < max_workers ? n : max_workers;
   if ((rc = pool_reserve(P, (size_t)n, (size_t)workers * (kGreeksSmBytes / per_sm)))) return rc;
@@ -1181,23 +725,15 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   size_t wbytes = P->arena_bytes / (size_t)workers;
   if (wbytes > kGreeksSmBytes / per_sm) wbytes = kGreeksSmBytes / per_sm;
   wbytes &= ~(size_t)255;
-  if (gteam == 4)
-    k_greeks_team<4><<<workers, 128, 0, s>>>(opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
-  else if (gteam == 8)
-    k_greeks_team<8><<<workers, 256, 0, s>>>(opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
-  else
-    k_greeks<<<(workers * 32 + kBlock - 1) / kBlock, kBlock, 0, s>>>(opts, n, out, grad, status, P->arena,
-                                                                     wbytes, workers, P->ctl, list0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  e = launch_greeks_team8(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
+  if (e != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
-  k_greeks_retry<<<kTier1Ctas, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, t1_bytes,
-                                                   &P->ctl[C_T0_OVF], list0, &P->ctl[C_T1_HEAD],
-                                                   &P->ctl[C_T1_OVF], list1, 0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  k_greeks_retry<<<1, kTeamBlock, 0, s>>>(opts, out, grad, status, P->arena, P->arena_bytes & ~(size_t)255,
-                                          &P->ctl[C_T1_OVF], list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF],
-                                          nullptr, 1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  e = launch_greeks_retry(kTier1Ctas, s, opts, out, grad, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF], list0,
+                          &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_greeks_retry(1, s, opts, out, grad, status, P->arena, P->arena_bytes & ~(size_t)255, &P->ctl[C_T1_OVF],
+                          list1, &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF], nullptr, 1);
+  if (e != cudaSuccess) return cuda_fail(e);
   return co.end();
 }
 
@@ -1467,12 +1003,13 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
   // every option goes to a CTA team (heavy factor 0), as in the pooled form
-  k_tc_batched<kNW, false><<<kNoAllocCtas, kTeamBlock, 0, s>>>(opts, n, order, out, status, arena, cta_bytes,
-                                                              ctl, list0, ds, 0);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
-  k_tc_retry<<<1, kTeamBlock, 0, s>>>(opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0,
-                                      &ctl[C_T1_HEAD], &ctl[C_T1_OVF], list1, 1, ds);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  {
+    const BatchedArgs ba{opts, n, order, out, status, arena, cta_bytes, ctl, list0, ds, 0};
+    if ((e = launch_batched_narrow(kNW, false, false, kNoAllocCtas, 0, s, ba)) != cudaSuccess) return cuda_fail(e);
+  }
+  if ((e = launch_retry(1, s, opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0, &ctl[C_T1_HEAD],
+                        &ctl[C_T1_OVF], list1, 1, ds)) != cudaSuccess)
+    return cuda_fail(e);
   return OB_OK;
 }
 
