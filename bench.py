@@ -301,11 +301,15 @@ def run_crr(args, rank, world, local):
     big = W.appendix_put(20000)
     bp = ob.to_device(big, dev)
     bo = torch.empty(1, dtype=torch.float64, device=dev)
+    bw = torch.empty(1, dtype=torch.float64, device=dev)
     ob.ob_crr_american(bp, 1, bo, None, stream)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ob.ob_crr_american_wide(bp, 1, bw, None, stream)
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     a.record(stream)
     ob.ob_crr_american(bp, 1, bo, None, stream)
     b.record(stream)
+    ob.ob_crr_american_wide(bp, 1, bw, None, stream)
+    c.record(stream)
     torch.cuda.synchronize(dev)
     if rank != 0:
         return
@@ -326,7 +330,10 @@ def run_crr(args, rank, world, local):
                      "frac": flops / peak["tflops"], "traffic": None,
                      "note": "3 FP64 flops per node (DFMA + DMUL) against the measured FP64 FMA peak "
                              "(ob_fp64_peak)", "peak_measurement": peak},
-        "put_n20000": {"price": float(bo.item()), "ms": a.elapsed_time(b)},
+        "put_n20000": {"price": float(bo.item()), "one_warp_ms": a.elapsed_time(b),
+                       "whole_gpu_price": float(bw.item()), "whole_gpu_ms": b.elapsed_time(c),
+                       "paper_context": {"serial_ms": 638.26, "p8_ms": 114.3,
+                                         "machine": "2 x Xeon E5405, 8 cores (Table 3)"}},
         "step_ms": step_ms, "clocks": clocks,
     }
     if not args.no_cpu_baseline:
@@ -463,9 +470,15 @@ def run_greeks(args, rank, world, local):
     pb.record(stream)
     torch.cuda.synchronize(dev)
     plain_s = pa.elapsed_time(pb) / 1e3
+    u_points = ob.ob_get_stats()["u_points"]
+    peak = measure_fp64_peak(local)
     if rank != 0:
         return
     value = world * n * args.steps / job_s
+    # every level is evaluated three times (forward, segment recompute, adjoint rerun), each
+    # counted as the pricing line counts one
+    g_flops = 3.0 * FLOPS_PER_MERGED_POINT * float(u_points)
+    g_achieved = g_flops / (job_s / args.steps) / 1e12
     line = {
         "metric": "options/s with Greeks (ask, bid and 12 derivatives), FP64", "value": value,
         "unit": "options/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -477,6 +490,12 @@ def run_greeks(args, rank, world, local):
         "plain": {"value": n / plain_s, "unit": "options/s", "call": "ob_price_ask_bid"},
         "greeks_over_plain_time": (job_s / args.steps) / plain_s,
         "gpu_launches": 3 * args.steps, "step_ms": step_ms, "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": g_achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": g_achieved / peak["tflops"], "traffic": None,
+                     "note": "algorithmic FP64 flops = 3 level evaluations (forward, recompute, adjoint "
+                             "rerun) x %d per merged successor breakpoint (U of the pricing pass); the "
+                             "adjoint's scatter work is not counted; peak = ob_fp64_peak" %
+                             FLOPS_PER_MERGED_POINT, "peak_measurement": peak},
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -533,8 +552,8 @@ def main():
     # sample of the batch, outside the timed region
     tuned = None
     if not args.no_autotune:
-        tw, tms = ob.ob_autotune(params, n, min(n, 1024), stream)
-        tuned = {"team_warps": tw, "sample": min(n, 1024),
+        tw, chip, tms = ob.ob_autotune(params, n, min(n, 1024), stream)
+        tuned = {"team_warps": tw, "chip_points": chip, "sample": min(n, 1024),
                  "sample_ms": {str(k): round(v, 2) for k, v in tms.items()}}
     for _ in range(args.warmup):
         ob.ob_price_ask_bid(params, n, out, st, stream)
@@ -634,7 +653,8 @@ def main():
                    "options": n, "node_updates_per_step": nodes_per_step,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas (one batch per GPU)",
-                   "team_warps": stats["team_warps"], "autotune": tuned,
+                   "team_warps": stats["team_warps"], "chip_points": stats["chip_points"],
+                   "autotune": tuned,
                    "launch": "CUDA graph replay" if stats["graph"] == 2 else
                              ("CUDA graph" if stats["graph"] == 1 else "direct")},
         "options_per_s": world * n * args.steps / job_s,

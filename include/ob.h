@@ -157,6 +157,19 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
 int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                     void* stream);
 
+/* Whole-GPU form of ob_crr_american, for large single options (N in the
+ * thousands and up): the options are priced one after another, each on every SM
+ * at once.  One cooperative launch of a CTA per SM; the levels advance in tiles
+ * of 64 levels: each CTA takes 192 nodes of the tile's last level together with
+ * the 64-node halo the recursion reaches from them, runs the 64 levels in shared
+ * memory, writes its nodes back, and all CTAs meet at a grid barrier.  The same
+ * node update as ob_crr_american, so the results agree bit for bit.  Arguments
+ * and statuses as ob_crr_american; a barrier wait longer than 10 s gives
+ * OB_ERR_TIMEOUT for the option in progress and the later ones; an option needs
+ * 4N+3 doubles of the scratch pool (OB_ERR_CAPACITY beyond). */
+int ob_crr_american_wide(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                         void* stream);
+
 /* Host-buffer convenience form of ob_price_ask_bid: params, out (2*n) and
  * status (n, may be NULL) are HOST pointers; the call copies the inputs to
  * the device, runs the batched form on an internal stream, copies the results
@@ -180,6 +193,8 @@ typedef struct {
   int32_t graph;          /* batched form: 0 direct launches, 1 captured into a new CUDA
                              graph and launched, 2 replay of a cached graph */
   int32_t team_warps;     /* warps per CTA team of the batched form */
+  int32_t chip_points;    /* batched form: points of w each CTA team keeps in shared memory
+                             (the fused level step; 0: w in the global scratch) */
 } ob_stats_t;
 int ob_get_stats(ob_stats_t* host_out);
 
@@ -191,19 +206,28 @@ int ob_get_stats(ob_stats_t* host_out);
  *               order, persistent kernel, two follow-up tiers) into a CUDA graph per
  *               (params, n, out, status) key, keeps the last 4, and replays a graph
  *               when the key repeats; 0: plain launches; -1 keeps (default 1).
+ *   chip_points the fused level step of 16- and 8-warp teams: passes 1-3 run per chunk
+ *               of whole nodes with w, the keys of g and h and their running minima in
+ *               shared memory (a chunk holds up to this many points of w, 60 bytes each;
+ *               nodes beyond it run on the global scratch); -1 as many as the CTA's
+ *               shared memory holds, 0 off (default; measured slower on the 4096-option
+ *               batch, since the shared memory is taken from the L1 cache), -2 keeps.
+ *               Results do not depend on it (bitwise).
  * Drops the cached graphs.  Returns OB_ERR_ARG for another team width. */
-int ob_configure(int32_t team_warps, int32_t use_graphs);
+int ob_configure(int32_t team_warps, int32_t use_graphs, int32_t chip_points);
 
-/* Autotuner of the batched form: times each team width (16, 12, 8, 4 warps; hence the
- * CTA size, the registers per thread and the per-CTA breakpoint capacity) on a sample
- * of the given options
- * (every (n_options / sample)-th option; sample <= 0 or >= n_options: all of them),
- * one warm-up run and one timed run each, with CUDA events on stream, and keeps the
- * fastest for later calls.  Synchronous.  params is a DEVICE pointer as in
- * ob_price_ask_bid.  team_warps_out (HOST, may be NULL) receives the choice; ms_out
- * (HOST, 4 floats, may be NULL) the timed milliseconds of 16, 12, 8 and 4 warps. */
+/* Autotuner of the batched form: times six configurations -- team widths 16, 12, 8, 4
+ * warps (hence the CTA size, the registers per thread and the per-CTA breakpoint
+ * capacity) with w in the global scratch, then the fused level step with w on chip
+ * (all the shared memory a CTA can take) for 16 and 8 warps -- on a sample of the given
+ * options (every (n_options / sample)-th option; sample <= 0 or >= n_options: all of
+ * them), one warm-up run and one timed run each, with CUDA events on stream, and keeps
+ * the fastest for later calls.  Synchronous.  params is a DEVICE pointer as in
+ * ob_price_ask_bid.  team_warps_out and chip_out (HOST, may be NULL) receive the
+ * choice (chip_out: on-chip points per CTA, 0 for none); ms_out (HOST, 6 floats, may
+ * be NULL) the timed milliseconds in the order above. */
 int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, void* stream,
-                int32_t* team_warps_out, float* ms_out);
+                int32_t* team_warps_out, int32_t* chip_out, float* ms_out);
 
 /* Release the current device's scratch pool (synchronises the device). */
 int ob_release(void);

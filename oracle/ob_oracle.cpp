@@ -493,9 +493,9 @@ int node_step(const PL<T>& zu, const PL<T>& zd, const T& r, const T& Sa, const T
 // two lines.  So the derivatives are carried on (c, s) of every piece.  At y*, between the
 // lines P (left) and Q (right) of F, the minimum value moves with
 //   dg = (1 - mu) dg_P(y*) + mu dg_Q(y*),   mu = (s_P + S^a) / (s_P - s_Q),
-// (y* held fixed in g_P, g_Q; mu lies in [0, 1] because the slopes of g on the two sides
-// bracket zero at a minimum), which is the derivative of g_P(y*) with y* = the crossing of
-// P and Q moving.  No breakpoint position enters a derivative: a crossing of two lines at
+// (y* held fixed in g_P, g_Q; at an interior minimum mu lies in [0, 1] because the slopes
+// of g on the two sides bracket zero), which is the derivative of g_P(y*) with y* = the
+// crossing of P and Q moving.  No breakpoint position enters a derivative: a crossing of two lines at
 // a shallow angle moves fast, but the functions do not, and carrying the positions would
 // cancel large terms in floating point.
 struct Line {
@@ -538,11 +538,11 @@ LPL lines_div(const LPL& X, const Dual& r) {
   return out;
 }
 
-// Line of slope -S through the breakpoint j of F where F + S y is least.  Breakpoints
+// Line of slope -S through the breakpoint j of F where g = F + S y is least.  Breakpoints
 // that coincide with y_j to within rounding (crossings that round to within a few ulps
 // of a kink) leave the choice among them to rounding noise in the values; the minimum
-// sits where the slopes of the lines, + S, change sign, so the search moves to the
-// breakpoint of the cluster where they do, and the weight is kept in [0, 1].
+// sits where the slopes of the lines, + S, change sign, so j moves through such a
+// cluster in the direction the lines say g keeps falling.
 Line flat_line(const LPL& F, int j, const Dual& S) {
   const int m = (int)F.F.y.size();
   const double tol = 1e-12 * std::max(1.0, std::fabs(F.F.y[j]));
@@ -552,8 +552,7 @@ Line flat_line(const LPL& F, int j, const Dual& S) {
   const Line& P = F.L[j];
   const Line& Q = F.L[j + 1];
   const double sp = P.s.v, sq = Q.s.v;
-  double mu = (sp == sq) ? 0.0 : (sp + S.v) / (sp - sq);
-  mu = std::min(1.0, std::max(0.0, mu));
+  const double mu = (sp == sq) ? 0.0 : (sp + S.v) / (sp - sq);
   const Dual gP = P.c + (P.s + S) * Dual(ys);
   const Dual gQ = Q.c + (Q.s + S) * Dual(ys);
   return Line{gP * Dual(1.0 - mu) + gQ * Dual(mu), -S};

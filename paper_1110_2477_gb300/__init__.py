@@ -29,7 +29,7 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
            "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune",
-           "ob_price_ask_bid_wide", "ob_fp64_peak")
+           "ob_price_ask_bid_wide", "ob_fp64_peak", "ob_crr_american_wide")
 
 
 class ObStats(ctypes.Structure):
@@ -38,7 +38,8 @@ class ObStats(ctypes.Structure):
                 ("z_points", ctypes.c_int64),
                 ("max_level_points", ctypes.c_int32), ("retried", ctypes.c_int32),
                 ("failed", ctypes.c_int32), ("tiers", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("team_warps", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("team_warps", ctypes.c_int32),
+                ("chip_points", ctypes.c_int32)]
 
 
 class ObError(RuntimeError):
@@ -54,7 +55,8 @@ def load():
         lib = ctypes.CDLL(LIB_PATH)
         P, i64 = ctypes.c_void_p, ctypes.c_int64
         for name in ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american",
-                     "ob_price_ask_bid_noalloc", "ob_greeks", "ob_price_ask_bid_wide"):
+                     "ob_price_ask_bid_noalloc", "ob_greeks", "ob_price_ask_bid_wide",
+                     "ob_crr_american_wide"):
             f = getattr(lib, name)
             f.argtypes = [P, i64, P, P, P]
             f.restype = ctypes.c_int
@@ -64,10 +66,10 @@ def load():
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
         lib.ob_get_stats.argtypes = [ctypes.POINTER(ObStats)]
         lib.ob_get_stats.restype = ctypes.c_int
-        lib.ob_configure.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.ob_configure.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         lib.ob_configure.restype = ctypes.c_int
         lib.ob_autotune.argtypes = [P, i64, i64, P, ctypes.POINTER(ctypes.c_int32),
-                                    ctypes.POINTER(ctypes.c_float)]
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
         lib.ob_autotune.restype = ctypes.c_int
         lib.ob_fp64_peak.argtypes = [i64, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.ob_fp64_peak.restype = ctypes.c_int
@@ -132,6 +134,11 @@ def ob_crr_american(params, n, out, status=None, stream=None):
     _check(load().ob_crr_american(_ptr(params), int(n), _ptr(out), _ptr(status), _stream(stream)))
 
 
+def ob_crr_american_wide(params, n, out, status=None, stream=None):
+    """Whole-GPU CRR form: each option in turn on every SM (large single options)."""
+    _check(load().ob_crr_american_wide(_ptr(params), int(n), _ptr(out), _ptr(status), _stream(stream)))
+
+
 def ob_price_ask_bid_noalloc(params, n, out, status=None, stream=None):
     """Fixed-scratch form: for callers that cannot allocate device memory when they price
     (the library's pool is never touched; scratch is a device array held since load time).
@@ -172,22 +179,28 @@ def ob_release():
     _check(load().ob_release())
 
 
-def ob_configure(team_warps=0, use_graphs=-1):
-    """Team width of the batched form (4, 8, 12, 16; 0 keeps) and CUDA-graph replay (1, 0; -1 keeps)."""
-    _check(load().ob_configure(int(team_warps), int(use_graphs)))
+def ob_configure(team_warps=0, use_graphs=-1, chip_points=-2):
+    """Team width of the batched form (4, 8, 12, 16; 0 keeps), CUDA-graph replay (1, 0; -1 keeps)
+    and the on-chip w points of the fused level step (-1 all that fit, 0 off, -2 keeps)."""
+    _check(load().ob_configure(int(team_warps), int(use_graphs), int(chip_points)))
+
+
+TUNE_CANDIDATES = ("16", "12", "8", "4", "16+chip", "8+chip")
 
 
 def ob_autotune(params, n, sample=0, stream=None):
-    """Time team widths 16, 12, 8, 4 on a sample of the device records and keep the fastest.
-    Returns (team_warps, {16: ms, 12: ms, 8: ms, 4: ms})."""
+    """Time the six configurations of TUNE_CANDIDATES on a sample of the device records and
+    keep the fastest.  Returns (team_warps, chip_points, {candidate: ms})."""
     tw = ctypes.c_int32(0)
-    ms = (ctypes.c_float * 4)()
-    _check(load().ob_autotune(_ptr(params), int(n), int(sample), _stream(stream), ctypes.byref(tw), ms))
-    return int(tw.value), {16: float(ms[0]), 12: float(ms[1]), 8: float(ms[2]), 4: float(ms[3])}
+    chip = ctypes.c_int32(0)
+    ms = (ctypes.c_float * len(TUNE_CANDIDATES))()
+    _check(load().ob_autotune(_ptr(params), int(n), int(sample), _stream(stream), ctypes.byref(tw),
+                              ctypes.byref(chip), ms))
+    return int(tw.value), int(chip.value), {k: float(v) for k, v in zip(TUNE_CANDIDATES, ms)}
 
 
 def autotune(table, sample=0):
-    """ob_autotune on a workloads table."""
+    """ob_autotune on a workloads table: (team_warps, chip_points, {candidate: ms})."""
     dev = to_device(table)
     return ob_autotune(dev, int(np.asarray(table).shape[0]), sample)
 
@@ -206,13 +219,15 @@ def price(table, plain=False, stream=None, wide=False):
     return out, st
 
 
-def crr(table, stream=None):
+def crr(table, stream=None, wide=False):
+    """Plain CRR prices of a workloads table: (out[n], status[n]) tensors; wide: each option
+    on the whole GPU."""
     import torch
     n = int(np.asarray(table).shape[0])
     dev = to_device(table)
     out = torch.empty(n, dtype=torch.float64, device=dev.device)
     st = torch.empty(n, dtype=torch.int32, device=dev.device)
-    ob_crr_american(dev, n, out, st, stream)
+    (ob_crr_american_wide if wide else ob_crr_american)(dev, n, out, st, stream)
     return out, st
 
 

@@ -1,25 +1,32 @@
 // ob_adj.cuh -- reverse-mode derivatives of ask and bid with respect to
 // (S0, K, sigma, R, T, k): the adjoint of the induction in ob_tc.cuh.
 //
-// The breakpoint structure is held fixed (the derivative of the piecewise
-// linear recursion on the branch the forward pass took).  Levels are swept
-// from the root (t = 0) back to the leaves (t = N+1); the adjoint of level t
-// needs level t+1's functions and the intermediate arrays of level t, so the
-// forward pass keeps level functions at checkpoints every s = ceil(sqrt(N+2))
-// levels and each segment between two checkpoints is recomputed once, its levels
-// kept, before its adjoint levels run.  In each adjoint level:
-//   - passes 1 and 2 are recomputed from level t+1 (pass 2 also records the
-//     index at which each running minimum is attained);
-//   - pass 3 is rerun in double to record its branch decisions and output
-//     positions, then replayed with LD values seeded on the piece's inputs, which
-//     yields the local Jacobian of every emitted point; the adjoints of the
-//     emitted points are pulled back to the points of w, to the points where the
-//     minima of g and h are attained, and to the node constants;
-//   - pass 2's g = w + S^a y, h = w + S^b y are pulled back to w;
-//   - pass 1 is rerun and its emitted points' adjoints are pulled back to the
-//     breakpoints of both successors (level t+1) and to their tail slopes.
-// Node constants (S^a lambda, S^b lambda, xi lambda of every node) are chained to
-// the six parameters in closed form as they are met.
+// The breakpoint structure is held fixed (the derivative of the piecewise linear
+// recursion on the branch the prices take).  Every piece of every node function is a
+// line c + s y (in the level's future-value units), and each step of the induction
+// takes the pieces of its result from the lines of its inputs or makes them from those
+// lines:
+//   - pass 1 (w = max of the successors): every piece of w is a piece of one successor;
+//   - pass 3 (restriction and exercise): every piece of z is a piece of w, a line of
+//     slope -S^a (-S^b) through the point of w where the running minimum of
+//     g = w + S^a y (h = w + S^b y) is attained, or a branch of the expense function u.
+// So the adjoint carries, per piece, the adjoints of (c, s) -- never of breakpoint
+// positions, which move fast where two lines cross at a shallow angle while the
+// functions do not.  At a running minimum, on point y* of w between the lines P and Q,
+//   g* = (1 - mu) (c_P + (s_P + S) y*) + mu (c_Q + (s_Q + S) y*),  mu = (s_P + S)/(s_P - s_Q),
+// is the derivative of the value with the crossing of P and Q moving; at an interior
+// minimum mu lies in [0, 1] because the slopes of g on the two sides bracket zero
+// (points that coincide with y* to within rounding are resolved by the lines' slopes).
+//
+// Levels are swept from the root (t = 0) back to the leaves (t = N+1).  The adjoint of
+// level t needs level t+1's functions, so the forward pass keeps the level functions at
+// checkpoints every s = ceil(sqrt(N+2)) levels and each segment between two checkpoints
+// is recomputed once, its levels kept, before its adjoint levels run.  An adjoint level
+// reruns passes 1-3 from level t+1 while recording, for every point of w and of z, which
+// line its piece follows (pass 2 records where each running minimum is attained); two
+// scatter loops then move the adjoints of z_t's lines onto w's lines and the node
+// constants, and those of w's lines onto level t+1's lines.  Node constants (S^a lambda,
+// S^b lambda, xi lambda of every node) are chained to the six parameters in closed form.
 #pragma once
 #include "ob_tc.cuh"
 
@@ -39,18 +46,28 @@ struct AdjLay {
   int* so;          // level store: node offsets
   long long so_cap;
   LvRef* ref;       // [N+2]
-  double *zbY[2], *zbF[2], *zbS[2];  // adjoints of two levels' points
-  double *wbY, *wbF, *wbS, *wbG, *wbH;
-  int *argA, *argB;
+  double *pc[2], *ps[2];  // adjoints of (c, s) of the piece right of each point, two levels [cap]
+  double *tc[2], *ts[2];  // ... and of each node's left tail [2(N+2)]
+  double *wc, *ws;        // adjoints of the pieces of w right of each point [cap]
+  double *wtc, *wts;      // ... and of w's left tails [2(N+1)]
+  double *nSa, *nSb, *nXi;  // adjoints of each node's S^a lambda, S^b lambda, xi lambda [2(N+1)]
+  int* wsrc;              // pass 1: the successor piece each piece of w follows [cap]
+  unsigned* zsrc;         // pass 3: the line each piece of z follows (KW..KU4 codes) [cap]
+  int* wtail;             // [2(N+1)] the same for the left tails
+  unsigned* ztail;
+  int *argA, *argB;       // pass 2: where the running minima of g and h are attained [cap]
   int cap;
 };
 
-// Split an arena between the pricing arrays (cap points each), the adjoint arrays
-// and the level store.  Returns false if it does not fit.
+// Split an arena between the pricing arrays (cap points each), the adjoint arrays and
+// the level store.  Returns false if it does not fit.
 OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, AdjLay& A) {
-  const size_t nb = node_bytes(N) + 32 * 256 + al256(sizeof(LvRef) * ((size_t)N + 2));
+  const size_t nodes = 2 * ((size_t)N + 2);
+  const size_t node_arrays = 4 * al256(sizeof(double) * nodes) + 5 * al256(sizeof(double) * nodes) +
+                             2 * al256(sizeof(int) * nodes);
+  const size_t nb = node_bytes(N) + 40 * 256 + al256(sizeof(LvRef) * ((size_t)N + 2)) + node_arrays;
   if (bytes < nb) return false;
-  const size_t per = ELEM_BYTES + 11 * sizeof(double) + 2 * sizeof(int);
+  const size_t per = ELEM_BYTES + 6 * sizeof(double) + 4 * sizeof(int);
   size_t cap = (size_t)((double)(bytes - nb) * 0.35) / per;
   if (cap > 0x3fffffff) cap = 0x3fffffff;
   if ((long long)cap < (long long)min_cap) return false;
@@ -58,15 +75,22 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   auto take = [&](size_t sz) { char* r = p; p += al256(sz); return r; };
   A.ref = (LvRef*)take(sizeof(LvRef) * ((size_t)N + 2));
   for (int b = 0; b < 2; ++b) {
-    A.zbY[b] = (double*)take(sizeof(double) * cap);
-    A.zbF[b] = (double*)take(sizeof(double) * cap);
-    A.zbS[b] = (double*)take(sizeof(double) * cap);
+    A.pc[b] = (double*)take(sizeof(double) * cap);
+    A.ps[b] = (double*)take(sizeof(double) * cap);
+    A.tc[b] = (double*)take(sizeof(double) * nodes);
+    A.ts[b] = (double*)take(sizeof(double) * nodes);
   }
-  A.wbY = (double*)take(sizeof(double) * cap);
-  A.wbF = (double*)take(sizeof(double) * cap);
-  A.wbS = (double*)take(sizeof(double) * cap);
-  A.wbG = (double*)take(sizeof(double) * cap);
-  A.wbH = (double*)take(sizeof(double) * cap);
+  A.wc = (double*)take(sizeof(double) * cap);
+  A.ws = (double*)take(sizeof(double) * cap);
+  A.wtc = (double*)take(sizeof(double) * nodes);
+  A.wts = (double*)take(sizeof(double) * nodes);
+  A.nSa = (double*)take(sizeof(double) * nodes);
+  A.nSb = (double*)take(sizeof(double) * nodes);
+  A.nXi = (double*)take(sizeof(double) * nodes);
+  A.wsrc = (int*)take(sizeof(int) * cap);
+  A.zsrc = (unsigned*)take(sizeof(unsigned) * cap);
+  A.wtail = (int*)take(sizeof(int) * nodes);
+  A.ztail = (unsigned*)take(sizeof(unsigned) * nodes);
   A.argA = (int*)take(sizeof(int) * cap);
   A.argB = (int*)take(sizeof(int) * cap);
   A.cap = (int)cap;
@@ -83,36 +107,12 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   return A.sd_cap > 0;
 }
 
-// Sink of the local-dual replay of a piece: every emitted point's local derivatives are
-// contracted with that point's adjoint as soon as the point is produced, in output order
-// (left tail, first point if it is part of the output, inside), so no array of LD points
-// is kept.
-struct PullOut {
-  const double *zbY, *zbF, *zbS;
-  int w;           // output position of the next emitted point
-  int emit_first;  // whether the candidate first point is part of the output
-  double adj[LDN];
-  double last_slope, tail_slope;
-  OB_HD void begin() {}
-  OB_HD void pull(const EmT<LD>& em) {
-    const double by = zbY[w], bf = zbF[w], bs = zbS[w];
-    for (int k = 0; k < LDN; ++k) adj[k] += by * em.y.d[k] + bf * em.f.d[k] + bs * em.s.d[k];
-    ++w;
-  }
-  OB_HD void add_tl(const EmT<LD>& e) { pull(e); }
-  OB_HD void set_first(const EmT<LD>& e) {
-    if (emit_first) pull(e);
-  }
-  OB_HD void add_m(const EmT<LD>& e) { pull(e); }
-};
-
 OB_HD void atomic_add(double* a, double v) {
 #if defined(__CUDA_ARCH__)
   if (v != 0.0) atomicAdd(a, v);
 #else
   if (v != 0.0) {  // host builds of this header: compare-and-swap loop
-    double old = __atomic_load_n((long long*)a, __ATOMIC_RELAXED) * 0.0 + *a;
-    long long expect = dbits(old);
+    long long expect = __atomic_load_n((long long*)a, __ATOMIC_RELAXED);
     for (;;) {
       const long long want = dbits(bitsd(expect) + v);
       if (__atomic_compare_exchange_n((long long*)a, &expect, want, false, __ATOMIC_RELAXED,
@@ -132,7 +132,8 @@ struct TcAdj {
   const AdjLay& A;
   int N;
   double g[2][NPAR];     // this lane's share of d ask / d theta (g[0]) and d bid / d theta (g[1])
-  long long sd_top, so_top, seg_sd, seg_so;
+  long long sd_top, so_top;
+  int wtot_cur = 0;      // points of w of the adjoint level in progress
 
   OB_HD TcAdj(TcRun<Team>& R_, const AdjLay& A_)
       : R(R_), tm(R_.tm), o(R_.o), L(R_.L), A(A_), N(R_.N) {
@@ -222,217 +223,105 @@ struct TcAdj {
   }
 
   // ---------------------------------------------------------------- adjoint of pass 3
-  OB_HD void pass3_adj(int t, int wtot, const double* zbY, const double* zbF, const double* zbS) {
-    const int lane = tm.lane();
-    const int W0 = t + 1;
-    double carry_slope = 0.0;
-    int zpos = 0;
-    for (int base = 0; base < wtot; base += Team::W) {
-      const int i = base + lane;
-      const bool ok = i < wtot;
-      PieceIn<double> in;
-      PieceOut<double> po;
-      po.ntl = po.nm = 0;
-      po.first = EmT<double>{0.0, 0.0, 0.0};
-      po.last_slope = po.tail_slope = 0.0;
-      RecDec rec;
-      int node = -1;
-      if (ok) {
-        R.load_piece(t, i, wtot, in, node);
-        piece(in, po, rec);
-      }
-      double tile_last;
-      double prev = tm.prev_last(po.last_slope, carry_slope, tile_last);
-      if (ok && in.head) prev = po.tail_slope;
-      const int emit_first = (ok && (in.anchor || !same_bits(prev, po.first.s))) ? 1 : 0;
-      const int nout = ok ? po.ntl + emit_first + po.nm : 0;
-      int total;
-      const int p0 = zpos + tm.excl_sum(nout, total);
-      if (ok && nout > 0) {
-        // seeds: 0 y0, 1 f0, 2 s0, 3 y1, 4 f1, 5 cA0, 6 cA1, 7 cB, 8 Sa, 9 Sb, 10 vu
-        PieceIn<LD> li;
-        const double vals[11] = {val(in.y0), val(in.f0), val(in.s0), val(in.y1), val(in.f1),
-                                 val(in.cA0), val(in.cA1), val(in.cB), val(in.Sa), val(in.Sb), val(in.vu)};
-        LD* dst[11] = {&li.y0, &li.f0, &li.s0, &li.y1, &li.f1, &li.cA0, &li.cA1, &li.cB, &li.Sa, &li.Sb, &li.vu};
-        for (int k = 0; k < 11; ++k) {
-          *dst[k] = mk<LD>(vals[k]);
-          dst[k]->d[k] = 1.0;
-        }
-        li.yu = in.yu; li.head = in.head; li.tail = in.tail; li.seller = in.seller;
-        li.anchor = in.anchor; li.Arel = in.Arel; li.Brel = in.Brel;
-        PullOut pl;
-        pl.zbY = zbY;
-        pl.zbF = zbF;
-        pl.zbS = zbS;
-        pl.w = p0;
-        pl.emit_first = emit_first;
-        for (int k = 0; k < LDN; ++k) pl.adj[k] = 0.0;
-        PlayDec pd{rec.d, 0};
-        piece(li, pl, pd);
-        const double* adj = pl.adj;
-        atomic_add(&A.wbY[i], adj[0]);
-        atomic_add(&A.wbF[i], adj[1]);
-        atomic_add(&A.wbS[i], adj[2]);
-        if (!in.tail) {
-          atomic_add(&A.wbY[i + 1], adj[3]);
-          atomic_add(&A.wbF[i + 1], adj[4]);
-          atomic_add(&A.wbG[A.argA[i + 1]], adj[6]);
-        }
-        if (in.head) atomic_add(&A.wbG[A.argA[i]], adj[5]);
-        atomic_add(&A.wbH[A.argB[i]], adj[7]);
-        const int p = node >= W0 ? 1 : 0;
-        const int j = node - p * W0;
-        acc_node(t, j, p, adj[8], adj[9], in.seller ? adj[10] : -adj[10]);
-      }
-      carry_slope = tile_last;
-      zpos += total;
-    }
-    tm.sync();
+  // The lines of w around point a (a point where a running minimum is attained): the
+  // piece left of it (the piece right of a - 1, or w's left tail if a starts its node)
+  // and the piece right of it.  Slopes: wS, or the tail's -S^a of the level-(t+1) node
+  // it comes from.
+  OB_HD double left_slope(int t, int a, int node, bool first) const {
+    if (!first) return L.wS[a - 1];
+    const int code = A.wtail[node];  // -1 - (level-(t+1) node)
+    const int n1 = -1 - code, W1 = t + 2;
+    const int j1 = n1 >= W1 ? n1 - W1 : n1;
+    return -L.nt[(t + 1) & 1][4 * j1];
   }
 
-  // ---------------------------------------------------------------- adjoint of pass 2
-  OB_HD void pass2_adj(int t, int wtot) {
+  // Line adjoint (cb, sb) of a piece of z at level t, following the line of `code`.
+  OB_HD void pull_z(int t, unsigned code, double cb, double sb) {
+    if (cb == 0.0 && sb == 0.0) return;
+    const int kind = (int)(code >> KSHIFT);
+    int a = (int)(code & KMASK);
     const int W0 = t + 1;
+    const int node = L.wN[a];
+    const int p = node >= W0 ? 1 : 0;
+    const int j = node - p * W0;
     const double* nt = L.nt[t & 1];
-    for (int i = tm.lane(); i < wtot; i += Team::W) {
-      const double gb = A.wbG[i], hb = A.wbH[i];
-      if (gb == 0.0 && hb == 0.0) continue;
-      const int n = L.wN[i];
-      const int p = n >= W0 ? 1 : 0;
-      const int j = n - p * W0;
-      const double y = L.wY[i];
-      A.wbF[i] += gb + hb;
-      A.wbY[i] += nt[4 * j] * gb + nt[4 * j + 1] * hb;
-      acc_node(t, j, p, y * gb, y * hb, 0.0);
+    if (kind == KW) {
+      atomic_add(&A.wc[a], cb);
+      atomic_add(&A.ws[a], sb);
+      return;
     }
-    tm.sync();
+    if (kind == KA || kind == KB) {
+      const double S = nt[4 * j + (kind == KA ? 0 : 1)];
+      // resolve points that coincide with y_a to within rounding by the lines' slopes
+      const double tol = 1e-12 * fmax(1.0, fabs(L.wY[a]));
+      for (int it = 0; it < 64; ++it) {
+        const bool last = (a + 1 >= wtot_cur) || L.wN[a + 1] != node;
+        if (last || !(L.wS[a + 1] + S < 0.0) || L.wY[a + 1] - L.wY[a] > tol) break;
+        ++a;
+      }
+      for (int it = 0; it < 64; ++it) {
+        const bool first = (a == 0) || L.wN[a - 1] != node;
+        if (first || !(L.wS[a - 1] + S > 0.0) || L.wY[a] - L.wY[a - 1] > tol) break;
+        --a;
+      }
+      const bool first = (a == 0) || L.wN[a - 1] != node;
+      const double sP = left_slope(t, a, node, first), sQ = L.wS[a];
+      const double mu = (sP == sQ) ? 0.0 : (sP + S) / (sP - sQ);
+      const double ys = L.wY[a];
+      if (first) {
+        atomic_add(&A.wtc[node], (1.0 - mu) * cb);
+        atomic_add(&A.wts[node], (1.0 - mu) * ys * cb);
+      } else {
+        atomic_add(&A.wc[a - 1], (1.0 - mu) * cb);
+        atomic_add(&A.ws[a - 1], (1.0 - mu) * ys * cb);
+      }
+      atomic_add(&A.wc[a], mu * cb);
+      atomic_add(&A.ws[a], mu * ys * cb);
+      // the S y* term of the minimum and the line's slope -S
+      atomic_add(kind == KA ? &A.nSa[node] : &A.nSb[node], ys * cb - sb);
+      return;
+    }
+    // a branch of u: c = vu + S yu, s = -S, vu = xi (seller) or -xi (buyer), yu = kink of u
+    const bool seller = (p == 0);
+    const double yu = seller ? (double)R.zeta : -(double)R.zeta;
+    atomic_add(&A.nXi[node], seller ? cb : -cb);
+    atomic_add(kind == KU3 ? &A.nSa[node] : &A.nSb[node], yu * cb - sb);
   }
 
-  // ---------------------------------------------------------------- adjoint of pass 1
-  OB_HD void pass1_adj(int t, double* zbY, double* zbF, double* zbS) {
-    const int lane = tm.lane();
-    const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
-    const int* o1 = R.inOff;
-    const double *Y1 = R.inY, *F1 = R.inF, *S1 = R.inS;
-    const double* nt1 = L.nt[(t + 1) & 1];
-    const int UB1 = R.ustart(o1, W1, 0, 0, W0);
-    const int Utot = R.ustart(o1, W1, UB1, 1, W0);
-    int ncur = 0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
-    for (int base = 0; base < Utot; base += Team::W) {
-      const int q = base + lane;
-      const int nl = ncur + lane;
-      int nend = 0x7fffffff;
-      if (nl < nNodes) {
-        const int p = nl >= W0 ? 1 : 0;
-        nend = R.ustart(o1, W1, UB1, p, nl - p * W0 + 1);
+  // z_t's line adjoints (pc, ps per point; tc, ts per node) onto w's lines and the node
+  // constants of level t
+  OB_HD void scatter_z(int t, int ztot, const double* pc, const double* ps, const double* tc, const double* ts) {
+    const int nNodes = 2 * (t + 1);
+    for (int i = tm.lane(); i < ztot; i += Team::W) pull_z(t, A.zsrc[i], pc[i], ps[i]);
+    for (int n = tm.lane(); n < nNodes; n += Team::W) pull_z(t, A.ztail[n], tc[n], ts[n]);
+    tm.sync();
+    const int W0 = t + 1;
+    for (int n = tm.lane(); n < nNodes; n += Team::W) {
+      const int p = n >= W0 ? 1 : 0;
+      acc_node(t, n - p * W0, p, A.nSa[n], A.nSb[n], A.nXi[n]);
+    }
+  }
+
+  // w's line adjoints onto the lines of level t+1 (pc1, ps1 per point; tc1, ts1 per node)
+  OB_HD void scatter_w(int t, int wtot, double* pc1, double* ps1, double* tc1, double* ts1) {
+    for (int i = tm.lane(); i < wtot; i += Team::W) {
+      const double cb = A.wc[i], sb = A.ws[i];
+      if (cb == 0.0 && sb == 0.0) continue;
+      const int code = A.wsrc[i];
+      if (code >= 0) {
+        atomic_add(&pc1[code], cb);
+        atomic_add(&ps1[code], sb);
+      } else {
+        atomic_add(&tc1[-1 - code], cb);
+        atomic_add(&ts1[-1 - code], sb);
       }
-      int pos, nend_le;
-      tm.count_le2(nend, q, base + Team::W, pos, nend_le);
-      const int ncur_next = ncur + nend_le;
-      P1 e;
-      e.dup = true;
-      int node = ncur + pos, ql = -1, p = 0, j = 0, aoff = 0, boff = 0, ma = 0, mb = 0;
-      if (q < Utot) {
-        p = node >= W0 ? 1 : 0;
-        j = node - p * W0;
-        ql = q - R.ustart(o1, W1, UB1, p, j);
-        const int* op = o1 + p * W1;
-        aoff = op[j + 1];
-        ma = op[j + 2] - aoff;
-        boff = op[j];
-        mb = aoff - boff;
-        p1_analyze(Y1 + aoff, F1 + aoff, S1 + aoff, ma, -nt1[4 * (j + 1)], Y1 + boff, F1 + boff,
-                   S1 + boff, mb, -nt1[4 * j], ql, e);
-      }
-      // owner of the segment ending at this point: that of the previous union point,
-      // looking past a duplicate (duplicates are never adjacent); encoded 2*own + dup
-      int m1, m2, l1, l2;
-      const int code = (q < Utot && e.dup) ? 1 : 2 * e.own;
-      tm.look2(code, carry_own, carry_own, m1, m2, l1, l2);
-      const int v2 = (m1 & 1) ? (m2 >> 1) : (m1 >> 1);
-      carry_own = (l1 & 1) ? l2 : l1;
-      int cnt = 0;
-      int wl = 0;
-      bool emit_pt = false;
-      if (q < Utot && !e.dup) {
-        wl = (ql == 0) ? e.wl_first : v2;
-        const double sLw = wl ? e.bL : e.aL, sRw = e.wr ? e.bR : e.aR;
-        emit_pt = !same_bits(sLw, sRw);
-        cnt = (e.lc ? 1 : 0) + (emit_pt ? 1 : 0) + (e.rc ? 1 : 0);
-      }
-      int total;
-      const int p0 = wpos + tm.excl_sum(cnt, total);
-      if (cnt > 0) {
-        // sources (seed k -> destination): 0 y; A: 1 value, 2 slope of the evaluated piece,
-        // 3 its anchor y, 4 left slope, 5 right slope; B: 6..10 alike
-        const double* Ay = Y1 + aoff; const double* Af = F1 + aoff; const double* As = S1 + aoff;
-        const double* By = Y1 + boff; const double* Bf = F1 + boff; const double* Bs = S1 + boff;
-        const double aTL = -nt1[4 * (j + 1)], bTL = -nt1[4 * j];
-        // destination encoding: >= 0: (array id 0 y / 1 f / 2 s) * 2^28 + index in level t+1;
-        // -1: A's tail slope, -2: B's tail slope, -3: none
-        long long dstk[11];
-        LD sy = mk<LD>(e.y);
-        sy.d[0] = 1.0;
-        dstk[0] = e.fromA ? (0LL << 28) + aoff + e.ia : (0LL << 28) + boff + e.ib;
-        auto side = [&](const double* Yv, const double* Fv, const double* Sv, int off, bool bp, int ib_,
-                        int kb_, double TL, int tailcode, int s0, LD& val_, LD& sl, LD& sr) {
-          long long* d = dstk + s0;
-          if (bp) {
-            val_ = mk<LD>(Fv[ib_]); val_.d[s0] = 1.0; d[0] = (1LL << 28) + off + ib_;
-            d[1] = -3; d[2] = -3;
-            sl = mk<LD>(ib_ > 0 ? Sv[ib_ - 1] : TL); sl.d[s0 + 3] = 1.0;
-            d[3] = ib_ > 0 ? (2LL << 28) + off + ib_ - 1 : tailcode;
-            sr = mk<LD>(Sv[ib_]); sr.d[s0 + 4] = 1.0; d[4] = (2LL << 28) + off + ib_;
-          } else {
-            const int a0 = kb_ >= 0 ? kb_ : 0;
-            LD f = mk<LD>(Fv[a0]); f.d[s0] = 1.0; d[0] = (1LL << 28) + off + a0;
-            LD s = mk<LD>(kb_ >= 0 ? Sv[kb_] : TL); s.d[s0 + 1] = 1.0;
-            d[1] = kb_ >= 0 ? (2LL << 28) + off + kb_ : tailcode;
-            LD ya = mk<LD>(Yv[a0]); ya.d[s0 + 2] = 1.0; d[2] = (0LL << 28) + off + a0;
-            val_ = f + s * (sy - ya);
-            sl = mk<LD>(val(s)); sl.d[s0 + 3] = 1.0; d[3] = d[1];
-            sr = mk<LD>(val(s)); sr.d[s0 + 4] = 1.0; d[4] = d[1];
-          }
-        };
-        LD a, aL, aR, b, bL, bR;
-        side(Ay, Af, As, aoff, e.aBp, e.ia, e.ka, aTL, -1, 1, a, aL, aR);
-        side(By, Bf, Bs, boff, e.bBp, e.ib, e.kb, bTL, -2, 6, b, bL, bR);
-        double adj[11];
-        for (int k = 0; k < 11; ++k) adj[k] = 0.0;
-        int w = p0;
-        auto pull = [&](const LD& ey, const LD& ef, const LD& es) {
-          const double by = A.wbY[w], bf = A.wbF[w], bs = A.wbS[w];
-          for (int k = 0; k < 11; ++k) adj[k] += by * ey.d[k] + bf * ef.d[k] + bs * es.d[k];
-          ++w;
-        };
-        if (e.lc) {
-          const int W_ = e.lc_w;
-          const LD vW = W_ ? b : a, vO = W_ ? a : b, sW = W_ ? bL : aL, sO = W_ ? aL : bL;
-          const LD x = sy + (vW - vO) / (sO - sW);
-          pull(x, vW + sW * (x - sy), sW);
-        }
-        if (emit_pt) {
-          const bool pickA = okey(e.a) >= okey(e.b);
-          pull(sy, pickA ? a : b, e.wr ? bR : aR);
-        }
-        if (e.rc) {
-          const int W_ = e.rc_w;
-          const LD vW = W_ ? b : a, vO = W_ ? a : b, sW = W_ ? bR : aR, sO = W_ ? aR : bR;
-          const LD x = sy + (vW - vO) / (sO - sW);
-          pull(x, vW + sW * (x - sy), sO);
-        }
-        for (int k = 0; k < 11; ++k) {
-          if (adj[k] == 0.0) continue;
-          const long long d = dstk[k];
-          if (d == -3) continue;
-          if (d == -1) { acc_node(t + 1, j + 1, p, -adj[k], 0.0, 0.0); continue; }
-          if (d == -2) { acc_node(t + 1, j, p, -adj[k], 0.0, 0.0); continue; }
-          const int arr = (int)(d >> 28), idx = (int)(d & ((1LL << 28) - 1));
-          atomic_add(arr == 0 ? &zbY[idx] : (arr == 1 ? &zbF[idx] : &zbS[idx]), adj[k]);
-        }
-      }
-      wpos += total;
-      ncur = ncur_next;
+    }
+    for (int n = tm.lane(); n < 2 * (t + 1); n += Team::W) {
+      const double cb = A.wtc[n], sb = A.wts[n];
+      if (cb == 0.0 && sb == 0.0) continue;
+      const int code = A.wtail[n];
+      atomic_add(&tc1[-1 - code], cb);
+      atomic_add(&ts1[-1 - code], sb);
     }
     tm.sync();
   }
@@ -494,14 +383,15 @@ struct TcAdj {
         in_from_store(t + 1);
         if (!level_to_bank(t) || !store_from_bank(t)) return ST_CAPACITY;
       }
-      if (!seeded && c > 0) {  // root: seed the adjoints of level 0
+      if (!seeded && c > 0) {  // root: the value at y = 0 of the piece right of every point <= 0
         seeded = true;
         const LvRef r0 = A.ref[0];
         const double* Y0 = A.sd + r0.d;
         const double* F0 = Y0 + r0.np;
         const double* S0v = F0 + r0.np;
         const int* off0 = A.so + r0.o;
-        zero(A.zbY[cur], r0.np); zero(A.zbF[cur], r0.np); zero(A.zbS[cur], r0.np);
+        zero(A.pc[cur], r0.np); zero(A.ps[cur], r0.np);
+        zero(A.tc[cur], 2); zero(A.ts[cur], 2);
         tm.sync();
         const double lam0 = L.lam[0];
         double vals[2];
@@ -511,15 +401,14 @@ struct TcAdj {
           const double tailL = -L.nt[0][0];
           double v;
           if (e <= b) { vals[p] = 0.0; continue; }
-          if (!klt(Y0[b], 0.0)) {
+          int k = b;  // first point right of 0
+          while (k < e && kle(Y0[k], 0.0)) ++k;
+          if (k == b) {
             v = F0[b] + tailL * (0.0 - Y0[b]);
-            if (lane == 0) { A.zbF[cur][b] += sc; A.zbY[cur][b] += sc * (-tailL); }
-            acc_node(0, 0, p, lane == 0 ? sc * Y0[b] : 0.0, 0.0, 0.0);
+            if (lane == 0) A.tc[cur][p] += sc;
           } else {
-            int k = b;
-            while (k + 1 < e && kle(Y0[k + 1], 0.0)) ++k;
-            v = F0[k] + S0v[k] * (0.0 - Y0[k]);
-            if (lane == 0) { A.zbF[cur][k] += sc; A.zbS[cur][k] += sc * (-Y0[k]); A.zbY[cur][k] += sc * (-S0v[k]); }
+            v = F0[k - 1] + S0v[k - 1] * (0.0 - Y0[k - 1]);
+            if (lane == 0) A.pc[cur][k - 1] += sc;
           }
           vals[p] = (p == 0) ? v / lam0 : -v / lam0;  // ask, then bid (as the pricing path)
         }
@@ -534,36 +423,42 @@ struct TcAdj {
       }
       // adjoint levels lo .. c-1 (each needs level t+1 <= c)
       for (int t = lo; t <= c - 1; ++t) {
+        R.use_banks(t);  // pass 3's rerun writes level t into its bank (scratch)
         in_from_store(t + 1);
         R.node_table(t + 1);
         R.node_table(t);
         tm.sync();
-        int wtot, utot;
-        if (!R.pass1(t, wtot, utot)) return ST_CAPACITY;
+        int wtot, utot, ztot;
+        if (!R.template pass1<true>(t, wtot, utot, 0, -1, A.wsrc, A.wtail)) return ST_CAPACITY;
         if (wtot > A.cap) return ST_CAPACITY;
         R.template pass2<true>(t, wtot, A.argA, A.argB);
-        zero(A.wbY, wtot); zero(A.wbF, wtot); zero(A.wbS, wtot); zero(A.wbG, wtot); zero(A.wbH, wtot);
-        tm.sync();
-        pass3_adj(t, wtot, A.zbY[cur], A.zbF[cur], A.zbS[cur]);
-        pass2_adj(t, wtot);
+        wtot_cur = wtot;
+        if (!R.template pass3<true>(t, wtot, ztot, 0, A.zsrc, A.ztail, A.argA, A.argB)) return ST_CAPACITY;
+        if (ztot != A.ref[t].np) return ST_CAPACITY;  // the rerun reproduces the stored level
+        const int nNodes = 2 * (t + 1), nNodes1 = 2 * (t + 2);
         const int nxt = cur ^ 1;
         const int np1 = A.ref[t + 1].np;
         if (np1 > A.cap) return ST_CAPACITY;
-        zero(A.zbY[nxt], np1); zero(A.zbF[nxt], np1); zero(A.zbS[nxt], np1);
+        zero(A.wc, wtot); zero(A.ws, wtot);
+        zero(A.wtc, nNodes); zero(A.wts, nNodes);
+        zero(A.nSa, nNodes); zero(A.nSb, nNodes); zero(A.nXi, nNodes);
+        zero(A.pc[nxt], np1); zero(A.ps[nxt], np1);
+        zero(A.tc[nxt], nNodes1); zero(A.ts[nxt], nNodes1);
         tm.sync();
-        pass1_adj(t, A.zbY[nxt], A.zbF[nxt], A.zbS[nxt]);
+        scatter_z(t, ztot, A.pc[cur], A.ps[cur], A.tc[cur], A.ts[cur]);
+        tm.sync();
+        scatter_w(t, wtot, A.pc[nxt], A.ps[nxt], A.tc[nxt], A.ts[nxt]);
         cur = nxt;
       }
       lo = c;
     }
-    // leaves: only their slopes -S^b_{N+1,j} depend on the parameters
+    // leaves: their lines are c = 0 with slopes -S^a (tail) and -S^b (the point's piece)
     {
-      const LvRef rl = A.ref[N + 1];
       const int W = N + 2;
-      for (int n = lane; n < rl.np; n += Team::W) {
+      for (int n = lane; n < 2 * W; n += Team::W) {
         const int p = n >= W ? 1 : 0;
         const int j = n - p * W;
-        acc_node(N + 1, j, p, 0.0, -A.zbS[cur][n], 0.0);
+        acc_node(N + 1, j, p, -A.ts[cur][n], -A.ps[cur][n], 0.0);
       }
     }
     for (int p = 0; p < 2; ++p)

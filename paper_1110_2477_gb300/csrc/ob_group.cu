@@ -1,5 +1,6 @@
-// ob_group.cu -- the whole-GPU form: one cooperative launch of a CTA per SM, each
-// option in turn with every level split over all CTAs (TcGroup), bounded grid barriers.
+// ob_group.cu -- the whole-GPU forms: one cooperative launch of a CTA per SM, each
+// option in turn with every level split over all CTAs (TcGroup for the induction with
+// costs, trapezoid tiles of levels for the plain CRR recursion), bounded grid barriers.
 #include "ob_kern.cuh"
 
 namespace obl {
@@ -109,6 +110,93 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     }
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ CRR on the whole GPU
+// Each option in turn on every SM.  The levels advance in tiles of kCrrD levels: CTA c
+// takes the tiles of kCrrLen nodes of level T - D from level T's nodes [a, a + kCrrLen + D]
+// (its own nodes plus the D-node halo to the right that the recursion reaches), runs the
+// D levels in shared memory (the valid region shrinks by one node a level), writes its
+// kCrrLen nodes, and all CTAs meet at a grid barrier before the next tile of levels.  The
+// exercise table and the leaves are laid out by all CTAs first.
+constexpr int kCrrThreads = 256;
+constexpr int kCrrD = 64;                       // levels per tile
+constexpr int kCrrLen = kCrrThreads - kCrrD;    // nodes a CTA finishes per tile
+
+__global__ void __launch_bounds__(kCrrThreads, 1) k_crr_group(
+    const obk::Opt* __restrict__ opts, int n, double* out, int* status, double* buf, size_t buf_doubles,
+    GroupState* gs, unsigned long long wait_ns) {
+  __shared__ double X[2][kCrrThreads + 1];
+  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
+  unsigned gen = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const obk::Opt o = opts[oi];
+    int rc = check_option(o, false);
+    double res = dnan();
+    const int N = o.N;
+    if (rc == obk::ST_OK && 4 * (size_t)N + 3 > buf_doubles) rc = obk::ST_CAPACITY;
+    const double dt = o.T / N;
+    const double u = exp(o.sigma * sqrt(dt));
+    const double d = 1.0 / u;
+    const double r = exp(o.R * dt);
+    if (rc == obk::ST_OK && !(d < r && r < u)) rc = obk::ST_ARBITRAGE;
+    if (rc == obk::ST_OK) {
+      const double p = (r - d) / (u - d);
+      const double pu = p / r, pd = (1.0 - p) / r;
+      double* P = buf;  // P[e + N], e = -N..N
+      double* Vin = buf + 2 * (size_t)N + 1;
+      double* Vout = Vin + N + 1;
+      const int stride = G * kCrrThreads;
+      for (int e = c * kCrrThreads + tid; e <= 2 * N; e += stride) P[e] = crr_payoff(o, o.S0 * pow(u, (double)(e - N)));
+      if (!grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
+      if (rc == obk::ST_OK) {
+        for (int j = c * kCrrThreads + tid; j <= N; j += stride) Vin[j] = P[2 * j];
+        if (!grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
+      }
+      int T = N;
+      while (rc == obk::ST_OK && T > 0) {
+        const int D = T < kCrrD ? T : kCrrD;
+        const int Wt = T - D + 1;  // nodes of level T - D
+        const int tiles = (Wt + kCrrLen - 1) / kCrrLen;
+        for (int tile = c; tile < tiles; tile += G) {
+          const int a = tile * kCrrLen;
+          for (int k = tid; k <= kCrrThreads; k += kCrrThreads) X[0][k] = (a + k <= T) ? __ldcg(&Vin[a + k]) : 0.0;
+          __syncthreads();
+          int cur = 0;
+          for (int l = 1; l <= D; ++l) {
+            const int t = T - l;
+            if (tid < kCrrLen + D - l && a + tid <= t)
+              X[cur ^ 1][tid] = crr_step(pu, pd, X[cur][tid + 1], X[cur][tid], P[2 * (a + tid) - t + N]);
+            __syncthreads();
+            cur ^= 1;
+          }
+          if (tid < kCrrLen && a + tid < Wt) Vout[a + tid] = X[cur][tid];
+          __syncthreads();
+        }
+        if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
+        double* tmp = Vin; Vin = Vout; Vout = tmp;
+        T -= D;
+      }
+      if (rc == obk::ST_OK) res = __ldcg(&Vin[0]);
+    }
+    if (c == 0 && tid == 0) {
+      out[oi] = res;
+      if (status) status[oi] = rc;
+    }
+    // every CTA is done with buf before the next option lays out its table
+    if (!grid_barrier(gs, gen, wait_ns) && c == 0 && tid == 0 && rc == obk::ST_OK && status) status[oi] = ST_TIMEOUT;
+  }
+}
+
+cudaError_t crr_group_occupancy(int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_crr_group, kCrrThreads, 0);
+}
+
+cudaError_t launch_crr_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
+                             double* buf, size_t buf_doubles, GroupState* gs, unsigned long long wait_ns) {
+  void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&buf, (void*)&buf_doubles,
+                  (void*)&gs, (void*)&wait_ns};
+  return cudaLaunchCooperativeKernel((const void*)k_crr_group, dim3(G), dim3(kCrrThreads), args, 0, s);
 }
 
 cudaError_t group_occupancy(int* per_sm) {

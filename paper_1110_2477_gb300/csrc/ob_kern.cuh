@@ -226,7 +226,7 @@ __device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double
 
 // Greeks on CTA teams: each CTA takes options from the queue over [0, n) as one team.
 template <int NW>
-__global__ void __launch_bounds__(32 * NW, 8 / NW) k_greeks_team(
+__global__ void __launch_bounds__(32 * NW, NW >= 16 ? 1 : 8 / NW) k_greeks_team(
     const obk::Opt* __restrict__ opts, int n, double* out, double* grad, int* status, char* arena,
     size_t cta_bytes, int* ctl, int* ovf_list) {
   __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
@@ -246,6 +246,24 @@ __global__ void __launch_bounds__(32 * NW, 8 / NW) k_greeks_team(
   }
 }
 
+
+// ------------------------------------------------------------------ plain CRR (no costs)
+// c_{t,j} = max(P_{t,j}, pu c_{t+1,j+1} + pd c_{t+1,j}), pu = p/r, pd = (1-p)/r, with the
+// exercise value P = max(payoff, 0) tabulated per option by stock exponent 2j - t.
+__device__ __forceinline__ double crr_payoff(const obk::Opt& o, double S) {
+  double v;
+  if (o.payoff == obk::PAY_PUT) v = o.K - S;
+  else if (o.payoff == obk::PAY_CALL) v = S - o.K;
+  else v = fmax(S - o.K, 0.0) - fmax(S - o.K2, 0.0);
+  return fmax(v, 0.0);
+}
+
+// One node update; both CRR kernels use it, so their results agree bit for bit.  The
+// values are >= 0, so their bit patterns order like the values.
+__device__ __forceinline__ double crr_step(double pu, double pd, double up, double cur, double ex) {
+  const double cont = fma(pu, up, pd * cur);
+  return (__double_as_longlong(cont) > __double_as_longlong(ex)) ? cont : ex;
+}
 
 // ------------------------------------------------------------------ launch functions
 // Arguments of the batched kernel.
@@ -279,13 +297,18 @@ cudaError_t launch_plain(int blocks, cudaStream_t s, const obk::Opt* opts, int n
 
 // ob_group.cu
 cudaError_t group_occupancy(int* per_sm);
+cudaError_t crr_group_occupancy(int* per_sm);
+cudaError_t launch_crr_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
+                             double* buf, size_t buf_doubles, GroupState* gs, unsigned long long wait_ns);
 cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
                          char* arena, size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds,
                          unsigned long long wait_ns, int skip_cta);
 
-// ob_greeks8.cu (8-warp CTA teams) and ob_greeks.cu (the follow-up launches)
+// ob_greeks8.cu (8- and 16-warp CTA teams) and ob_greeks.cu (the follow-up launches)
 cudaError_t launch_greeks_team8(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list);
+cudaError_t launch_greeks_team16(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
+                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list);
 cudaError_t launch_greeks_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, double* grad,
                                 int* status, char* arena, size_t cta_bytes, const int* in_count,
                                 const int* in_list, int* head, int* ovf_count, int* ovf_list, int last);

@@ -82,13 +82,6 @@ __global__ void k_order(const obk::Opt* __restrict__ opts, int n, int npad, int*
 // P is tabulated per option by stock exponent e = 2j - t (max(payoff, 0)).
 // Lanes take interleaved nodes so that shared-memory and table accesses are
 // unit-stride; the up-successor value comes from the neighbour lane.
-__device__ __forceinline__ double crr_payoff(const obk::Opt& o, double S) {
-  double v;
-  if (o.payoff == obk::PAY_PUT) v = o.K - S;
-  else if (o.payoff == obk::PAY_CALL) v = S - o.K;
-  else v = fmax(S - o.K, 0.0) - fmax(S - o.K2, 0.0);
-  return fmax(v, 0.0);
-}
 
 __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opts, int n, double* out,
                                                 int* status, char* arena, size_t wbytes, int nworkers,
@@ -141,9 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_crr(const obk::Opt* __restrict__ opt
             if (lane == 31) up = extra;
             tm.sync();
             if (i < width) {
-              const double cont = pu * up + pd * cur;
-              const double ex = Pt[2 * i];
-              V[i] = (__double_as_longlong(cont) > __double_as_longlong(ex)) ? cont : ex;
+              V[i] = crr_step(pu, pd, up, cur, Pt[2 * i]);
             }
             tm.sync();
           }
@@ -201,9 +192,11 @@ struct GraphEntry {
   void* status = nullptr;
   int n = 0;
   int team_warps = 0;
+  int chip = 0;
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kGraphCache = 4;
+constexpr int kTuneCands = 6;  // configurations the autotuner times
 
 // Scratch budgets.  The pool is one device allocation that grows to the largest
 // need of any call so far (never shrinks before ob_release); OB_POOL_MB fixes its size.
@@ -223,6 +216,7 @@ struct DevPool {
   size_t fixed_bytes = 0;         // OB_POOL_MB: the pool has exactly this size
   double heavy_factor = kHeavyFactor;
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
+  int greeks_warps = 8; // warps of a Greeks CTA team (8 or 16)
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -303,6 +297,7 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
     if (e != cudaSuccess) return cuda_fail(e);
     P.warps_per_sm = (int)env_size("OB_WARPS_PER_SM", 16);
     P.sm_bytes = (env_size("OB_ARENA_MB", 2) << 20) * 16;  // OB_ARENA_MB: MiB per warp slot
+    if (const size_t kb = env_size("OB_SM_KB", 0)) P.sm_bytes = kb << 10;  // or KiB per SM
     P.fixed_bytes = env_size("OB_POOL_MB", 0) << 20;
     if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
     if (const char* tw = getenv("OB_TEAM_WARPS")) {
@@ -310,6 +305,7 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
       if (v == 4 || v == 8 || v == 12 || v == 16) P.team_warps = v;
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
+    if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 16 ? 16 : 8;
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
     if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
@@ -519,7 +515,7 @@ int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* 
   cudaError_t e;
   for (GraphEntry& g : P->graphs) {
     if (g.exec && g.params == opts && g.n == n && g.out == out && g.status == status &&
-        g.team_warps == P->team_warps) {
+        g.team_warps == P->team_warps && g.chip == P->chip_req) {
       if ((e = cudaGraphLaunch(g.exec, s)) != cudaSuccess) return cuda_fail(e);
       P->last_graph = 2;
       P->last_tiers = kTiers + (n <= kSortMax ? 1 : 0);
@@ -552,6 +548,7 @@ int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* 
   g.out = out;
   g.status = status;
   g.team_warps = P->team_warps;
+  g.chip = P->chip_req;
   if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(e);
   P->last_graph = 1;
   return OB_OK;
@@ -699,6 +696,41 @@ int ob_crr_american(const ob_option_t* params, int64_t n_options, double* out, i
   return co.end();
 }
 
+int ob_crr_american_wide(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                         void* stream) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out) return OB_ERR_ARG;
+  DevPool* P = nullptr;
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
+  cudaError_t e;
+  if (!P->gstate) {
+    if (cudaMalloc(&P->gstate, sizeof(GroupState)) != cudaSuccess) {
+      cudaGetLastError();
+      return OB_ERR_NOMEM;
+    }
+  }
+  int per_sm = 0, coop = 0;
+  if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return cuda_fail(e);
+  if (!coop) return OB_ERR_CUDA;
+  if ((e = crr_group_occupancy(&per_sm)) != cudaSuccess) return cuda_fail(e);
+  if (per_sm < 1) return OB_ERR_CUDA;
+  int G = P->sms;  // one CTA per SM
+  if (G > kGroupMax) G = kGroupMax;
+  if ((rc = pool_reserve(P, 1, 0))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
+  if ((e = cudaMemsetAsync(P->gstate, 0, sizeof(GroupState), s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_crr_group(G, s, (const obk::Opt*)params, (int)n_options, out, status, (double*)P->arena,
+                            P->arena_bytes / sizeof(double), P->gstate, P->wide_wait_ns)) != cudaSuccess)
+    return cuda_fail(e);
+  return co.end();
+}
+
 int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad, int32_t* status,
               void* stream) {
   if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
@@ -710,7 +742,7 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   int rc = pool_get(&P, &dev);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_call_mu[dev]);
-  const int per_sm = 1;  // one 8-warp CTA team per SM
+  const int per_sm = 1;  // one CTA team per SM (8 or 16 warps, OB_GREEKS_WARPS)
   const int max_workers = P->sms * per_sm;
   const int workers = n < max_workers ? n : max_workers;
   if ((rc = pool_reserve(P, (size_t)n, (size_t)workers * (kGreeksSmBytes / per_sm)))) return rc;
@@ -725,7 +757,9 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   size_t wbytes = P->arena_bytes / (size_t)workers;
   if (wbytes > kGreeksSmBytes / per_sm) wbytes = kGreeksSmBytes / per_sm;
   wbytes &= ~(size_t)255;
-  e = launch_greeks_team8(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
+  e = P->greeks_warps == 16
+          ? launch_greeks_team16(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0)
+          : launch_greeks_team8(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   e = launch_greeks_retry(kTier1Ctas, s, opts, out, grad, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF], list0,
@@ -803,12 +837,14 @@ int ob_get_stats(ob_stats_t* host_out) {
   host_out->tiers = P->last_tiers;
   host_out->graph = P->last_graph;
   host_out->team_warps = P->team_warps;
+  host_out->chip_points = (P->team_warps == 16 || P->team_warps == 8) ? chip_points(P, P->team_warps) : 0;
   return OB_OK;
 }
 
-int ob_configure(int32_t team_warps, int32_t use_graphs) {
+int ob_configure(int32_t team_warps, int32_t use_graphs, int32_t chip_points) {
   if (team_warps != 0 && team_warps != 4 && team_warps != 8 && team_warps != 12 && team_warps != 16)
     return OB_ERR_ARG;
+  if (chip_points < -2) return OB_ERR_ARG;
   DevPool* P = nullptr;
   int dev = 0;
   int rc = pool_get(&P, &dev);
@@ -816,12 +852,13 @@ int ob_configure(int32_t team_warps, int32_t use_graphs) {
   std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   if (team_warps) P->team_warps = team_warps;
   if (use_graphs >= 0) P->use_graphs = use_graphs != 0;
+  if (chip_points != -2) P->chip_req = chip_points;
   drop_graphs(P);
   return OB_OK;
 }
 
 int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, void* stream,
-                int32_t* team_warps_out, float* ms_out) {
+                int32_t* team_warps_out, int32_t* chip_out, float* ms_out) {
   if (n_options <= 0 || n_options > (1 << 30) || !params) return OB_ERR_ARG;
   const int n = (int)n_options;
   int m = (int)(sample > 0 && sample < n_options ? sample : n_options);
@@ -864,11 +901,15 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     if (a) cudaEventDestroy(a);
     return cuda_fail(e);
   }
-  const int cands[4] = {16, 12, 8, 4};
-  int best = keep;
+  // candidates: team width, and on-chip w points per CTA (0: w in the global scratch;
+  // -1: the fused level step with all the shared memory a CTA can take)
+  const int cands[kTuneCands][2] = {{16, 0}, {12, 0}, {8, 0}, {4, 0}, {16, -1}, {8, -1}};
+  const int keep_chip = P->chip_req;
+  int best = keep, best_chip = keep_chip;
   float best_ms = 0.0f;
-  for (int c = 0; c < 4 && rc == OB_OK; ++c) {
-    P->team_warps = cands[c];
+  for (int c = 0; c < kTuneCands && rc == OB_OK; ++c) {
+    P->team_warps = cands[c][0];
+    P->chip_req = cands[c][1];
     float ms = 0.0f;
     for (int rep = 0; rep < 2 && rc == OB_OK; ++rep) {  // one warm-up run, one timed run
       if ((e = cudaEventRecord(a, s)) != cudaSuccess) { rc = cuda_fail(e); break; }
@@ -882,13 +923,15 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     }
     if (rc) break;
     if (ms_out) ms_out[c] = ms;
-    if (c == 0 || ms < best_ms) { best_ms = ms; best = cands[c]; }
+    if (c == 0 || ms < best_ms) { best_ms = ms; best = cands[c][0]; best_chip = cands[c][1]; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   P->team_warps = rc ? keep : best;
+  P->chip_req = rc ? keep_chip : best_chip;
   drop_graphs(P);
   if (team_warps_out) *team_warps_out = P->team_warps;
+  if (chip_out) *chip_out = chip_points(P, P->team_warps);
   if (rc) return rc;
   return co.end();
 }

@@ -32,6 +32,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "ob_team.cuh"
 
 namespace obk {
@@ -175,6 +177,7 @@ struct P1 {
   int wr;             // owner just right of y
   int own;            // owner just left of the next union point
   int wl_first;       // owner just left of y, first union point only
+  int farL;           // owner of the far left (first union point only)
   bool dup, rc, lc;
   // provenance, for the adjoint: breakpoint indices used, the successors whose lines
   // meet at the crossings
@@ -258,6 +261,7 @@ OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int 
   if (q == 0) {  // the far left belongs to the successor with the smaller left slope
     int wl = (kA != kB) ? (kA > kB ? 0 : 1) : (klt(aL, bL) ? 0 : (klt(bL, aL) ? 1 : 0));
     const int farL = klt(aL, bL) ? 0 : (klt(bL, aL) ? 1 : wl);
+    e.farL = farL;
     if (farL != wl) {
       const double vW = wl ? b : a, vO = wl ? a : b, sW = wl ? bL : aL, sO = wl ? aL : bL;
       const double x = y + (vW - vO) / (sO - sW);
@@ -305,6 +309,32 @@ OB_HD void p1_analyze(const double* Ay, const double* Af, const double* As, int 
   e.own = own;
 }
 
+// The piece of one successor right (left = false) or left of the union point y: with a
+// breakpoint i at y, the piece right of it (or of i - 1; the tail if i = 0); else the
+// piece right of its breakpoint k before y (the tail if k = -1).  Codes: a point of level
+// t+1, >= 0 (the piece right of it), or -1 - (node of level t+1) for a left tail.
+OB_HD int p1_side_piece(bool bp, int i, int k, int off, int tail, bool left) {
+  if (bp) return left ? (i > 0 ? off + i - 1 : tail) : off + i;
+  return k >= 0 ? off + k : tail;
+}
+
+// For each emission of p1_emit (same order), the successor piece whose line w follows
+// right of the emitted point: after a left-tail crossing the winner's piece left of y,
+// after y the winner's piece right of y, after a crossing the other side's piece right of y.
+OB_HD int p1_emit_src(const P1& e, int wl, int aoff, int boff, int tailA, int tailB, int* src) {
+  int n = 0;
+  if (e.dup) return 0;
+  if (e.lc) src[n++] = e.lc_w ? p1_side_piece(e.bBp, e.ib, e.kb, boff, tailB, true)
+                              : p1_side_piece(e.aBp, e.ia, e.ka, aoff, tailA, true);
+  const double sLw = wl ? e.bL : e.aL, sRw = e.wr ? e.bR : e.aR;
+  if (!same_bits(sLw, sRw))
+    src[n++] = e.wr ? p1_side_piece(e.bBp, e.ib, e.kb, boff, tailB, false)
+                    : p1_side_piece(e.aBp, e.ia, e.ka, aoff, tailA, false);
+  if (e.rc) src[n++] = e.rc_w ? p1_side_piece(e.aBp, e.ia, e.ka, aoff, tailA, false)
+                              : p1_side_piece(e.bBp, e.ib, e.kb, boff, tailB, false);
+  return n;
+}
+
 // Emissions of an analysed union point, given the owner just left of it.
 OB_HD int p1_emit(const P1& e, int wl, Em* em) {
   int n = 0;
@@ -317,88 +347,16 @@ OB_HD int p1_emit(const P1& e, int wl, Em* em) {
 }
 
 // ------------------------------------------------------------------ scalars
-// The per-piece logic below is written once for two scalar types: double (the
-// pricing passes) and LD, a value with a few local derivatives used by the
-// adjoint passes.  All branch decisions are taken on values; in the adjoint they
-// are replayed from a recording made by the double run, so both runs follow the
-// same path even where rounding of the two differs.
-constexpr int LDN = 11;
-struct LD {
-  double v;
-  double d[LDN];
-};
+// The per-piece logic below is written for a scalar type T (double in every run) and
+// a decision policy D (NoDec: decisions are taken on the values as they come).
 OB_HD double val(double x) { return x; }
-OB_HD double val(const LD& x) { return x.v; }
 template <class T>
 OB_HD T mk(double x);
 template <>
 OB_HD double mk<double>(double x) { return x; }
-template <>
-OB_HD LD mk<LD>(double x) {
-  LD r;
-  r.v = x;
-  for (int i = 0; i < LDN; ++i) r.d[i] = 0.0;
-  return r;
-}
-OB_HD LD operator+(const LD& a, const LD& b) {
-  LD r; r.v = a.v + b.v;
-  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] + b.d[i];
-  return r;
-}
-OB_HD LD operator-(const LD& a, const LD& b) {
-  LD r; r.v = a.v - b.v;
-  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] - b.d[i];
-  return r;
-}
-OB_HD LD operator-(const LD& a) {
-  LD r; r.v = -a.v;
-  for (int i = 0; i < LDN; ++i) r.d[i] = -a.d[i];
-  return r;
-}
-OB_HD LD operator*(const LD& a, const LD& b) {
-  LD r; r.v = a.v * b.v;
-  for (int i = 0; i < LDN; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
-  return r;
-}
-OB_HD LD operator/(const LD& a, const LD& b) {
-  LD r; r.v = a.v / b.v;
-  for (int i = 0; i < LDN; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
-  return r;
-}
-OB_HD LD operator+(const LD& a, double b) { return a + mk<LD>(b); }
-OB_HD LD operator-(const LD& a, double b) { return a - mk<LD>(b); }
-OB_HD LD operator-(double a, const LD& b) { return mk<LD>(a) - b; }
-OB_HD LD operator*(double a, const LD& b) { return mk<LD>(a) * b; }
 
-// Decisions: the pricing run computes them (NoDec); the adjoint records them with
-// a double run (RecDec) and replays them with an LD run (PlayDec).
-//
-// Bound on the decisions of one piece() call.  Left tail (head only): the split (1)
-// and, per part (at most 2), comb1 (2) and the slope tests of its at most 2 sub-pieces
-// (2): 9.  The fast-path test (1), then either the fast outcome (1) or, on the
-// general path, the cB combination (2), the cA combination of at most 2 sub-pieces (4), then
-// per sub-piece of v (at most 4) the split at yu (1) and, per part (at most 2), comb1
-// (2) and at most 2 slope tests: 4 * 9.  Counting both paths bounds it by
-// 9 + 1 + 1 + 2 + 4 + 36 = 53.
-constexpr int MAXDEC = 9 + 1 + 1 + 2 + 4 + 4 * (1 + 2 * (2 + 2));
-constexpr int DECCAP = 96;
-static_assert(MAXDEC <= DECCAP, "decision record too small for one piece");
 struct NoDec {
   OB_HD int take(int c) { return c; }
-};
-struct RecDec {
-  unsigned char d[DECCAP];
-  int n = 0;
-  OB_HD int take(int c) {
-    if (n < DECCAP) d[n] = (unsigned char)c;
-    ++n;
-    return c;
-  }
-};
-struct PlayDec {
-  const unsigned char* d;
-  int n = 0;
-  OB_HD int take(int) { return d[n < DECCAP ? n++ : DECCAP - 1]; }
 };
 
 // ------------------------------------------------------------------ pass 3 helpers
@@ -509,12 +467,33 @@ struct PieceOut {
   EmT<T> m[MAXSUB];      // emissions inside the piece
   int nm;
   double last_slope, tail_slope;
-  // piece() hands its emissions over in output order: left tail, first, inside
+  // piece() hands its emissions over in output order: left tail, first, inside, each
+  // with the line (0..4 of piece()) the function follows right of the point; set_tail
+  // gives the line of the far left (head only).  The pricing run keeps no lines.
   OB_HD void begin() { ntl = nm = 0; }
-  OB_HD void add_tl(const EmT<T>& e) { tl[ntl++] = e; }
-  OB_HD void set_first(const EmT<T>& e) { first = e; }
-  OB_HD void add_m(const EmT<T>& e) { m[nm++] = e; }
+  OB_HD void add_tl(const EmT<T>& e, int) { tl[ntl++] = e; }
+  OB_HD void set_first(const EmT<T>& e, int) { first = e; }
+  OB_HD void add_m(const EmT<T>& e, int) { m[nm++] = e; }
+  OB_HD void set_tail(int) {}
 };
+
+// PieceOut that also keeps the line of every emission (the adjoint's rerun of pass 3).
+template <class T>
+struct PieceOutL : PieceOut<T> {
+  unsigned char tl_line[3], first_line, m_line[MAXSUB], tail_line;
+  OB_HD void add_tl(const EmT<T>& e, int l) { tl_line[this->ntl] = (unsigned char)l; this->tl[this->ntl++] = e; }
+  OB_HD void set_first(const EmT<T>& e, int l) { first_line = (unsigned char)l; this->first = e; }
+  OB_HD void add_m(const EmT<T>& e, int l) { m_line[this->nm] = (unsigned char)l; this->m[this->nm++] = e; }
+  OB_HD void set_tail(int l) { tail_line = (unsigned char)l; }
+};
+
+// Kinds of the line a piece of z follows (the adjoint's record of pass 3), in the top
+// four bits of a code whose low 28 bits give a point of w: KW the piece of w starting at
+// that point; KA, KB the line of slope -S^a (-S^b) through the point where the running
+// minimum of g (h) is attained; KU3, KU4 the left and right branch of u (the point is
+// the piece of w, which names the node).
+enum { KW = 0, KA = 1, KB = 2, KU3 = 3, KU4 = 4 };
+constexpr unsigned KSHIFT = 28, KMASK = (1u << KSHIFT) - 1;
 
 // The restriction and the exercise step on one piece (and, for the first point
 // of a node, on the left tail).
@@ -541,18 +520,20 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
       for (int c = 0; c < n; ++c) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
-        if (prev_l >= 0 && dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1))
-          out.add_tl(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s});
+        if (prev_l < 0) out.set_tail(l);  // the far left
+        else if (dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1))
+          out.add_tl(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s}, l);
         prev_l = l;
       }
     }
-    out.tail_slope = val(lines[prev_l].s);
+    out.tail_slope = val(lines[prev_l].s);  // just left of y0
   }
   const bool fast = dec.take((!in.tail && !in.Arel && !in.Brel &&
                               !(klt(val(in.y0), in.yu) && klt(in.yu, val(in.y1)))) ? 1 : 0);
   if (fast) {
     // common case: v = w on the piece and one branch of u covers it
     const bool leftside = klt(val(in.y0), in.yu);
+    const int uq = leftside ? 3 : 4;  // the branch of u over the piece
     const T sQ = leftside ? -in.Sa : -in.Sb;
     const T q0 = in.vu + sQ * (in.y0 - yu), q1 = in.vu + sQ * (in.y1 - yu);
     const long long ks0 = okey(val(in.s0)), ksQ = okey(val(sQ));
@@ -577,20 +558,20 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
     }
     outcome = dec.take(outcome);
     if (outcome == 0) {
-      out.set_first(EmT<T>{in.y0, in.f0, in.s0});
+      out.set_first(EmT<T>{in.y0, in.f0, in.s0}, 0);
       out.last_slope = val(in.s0);
     } else if (outcome == 1) {
-      out.set_first(EmT<T>{in.y0, q0, sQ});
+      out.set_first(EmT<T>{in.y0, q0, sQ}, uq);
       out.last_slope = val(sQ);
     } else {
       const T x = in.y0 + (in.f0 - q0) / (sQ - in.s0);
       if (outcome == 2) {  // w, then u from x
-        out.set_first(EmT<T>{in.y0, in.f0, in.s0});
-        out.add_m(EmT<T>{x, in.vu + sQ * (x - yu), sQ});
+        out.set_first(EmT<T>{in.y0, in.f0, in.s0}, 0);
+        out.add_m(EmT<T>{x, in.vu + sQ * (x - yu), sQ}, uq);
         out.last_slope = val(sQ);
       } else {  // u, then w from x
-        out.set_first(EmT<T>{in.y0, q0, sQ});
-        out.add_m(EmT<T>{x, in.f0 + in.s0 * (x - in.y0), in.s0});
+        out.set_first(EmT<T>{in.y0, q0, sQ}, uq);
+        out.add_m(EmT<T>{x, in.f0 + in.s0 * (x - in.y0), in.s0}, 0);
         out.last_slope = val(in.s0);
       }
     }
@@ -650,9 +631,9 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
         const int l = c ? lb : la;
         const T x = c ? xb : x0;
         if (prev_l < 0) {
-          out.set_first(EmT<T>{in.y0, ln_eval(lines[l], in.y0, in.y1, in.f1), lines[l].s});
+          out.set_first(EmT<T>{in.y0, ln_eval(lines[l], in.y0, in.y1, in.f1), lines[l].s}, l);
         } else if (dec.take(same_bits(val(lines[l].s), val(lines[prev_l].s)) ? 0 : 1)) {
-          out.add_m(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s});
+          out.add_m(EmT<T>{x, ln_eval(lines[l], x, in.y1, in.f1), lines[l].s}, l);
         }
         prev_l = l;
       }
@@ -748,7 +729,11 @@ struct TcRun {
 
   // pass 1: w = max(z_up, z_down) for the nodes n0 <= n < n1 of level t (n1 < 0: all
   // nodes); w of node n0 starts at position 0.  Returns false on overflow.
-  OB_HD bool pass1(int t, int& wtot, int& utot, int n0 = 0, int n1 = -1) {
+  // PROV (the adjoint's rerun): wsrc[i] receives the successor piece whose line w follows
+  // right of point i of w, wtail[node] that of w's left tail (p1_side_piece codes).
+  template <bool PROV = false>
+  OB_HD bool pass1(int t, int& wtot, int& utot, int n0 = 0, int n1 = -1, int* wsrc = nullptr,
+                   int* wtail = nullptr) {
     const int lane = tm.lane();
     const int b1 = (t + 1) & 1;
     const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
@@ -779,13 +764,18 @@ struct TcRun {
       e.dup = true;
       e.own = 0;  // lanes past the end hand a defined code on
       int cnt = 0, node = ncur + pos, ql = -1;
+      int aoff = 0, boff = 0, tailA = 0, tailB = 0;
       if (q < Utot) {
         const int p = node >= W0 ? 1 : 0;
         const int j = node - p * W0;
         ql = q - ustart(o1, W1, UB1, p, j);
         const int* op = o1 + p * W1;
-        const int aoff = op[j + 1], ma = op[j + 2] - aoff;
-        const int boff = op[j], mb = aoff - boff;
+        aoff = op[j + 1];
+        const int ma = op[j + 2] - aoff;
+        boff = op[j];
+        const int mb = aoff - boff;
+        tailA = -1 - (p * W1 + j + 1);
+        tailB = -1 - (p * W1 + j);
         p1_analyze(Y1 + aoff, F1 + aoff, S1 + aoff, ma, -nt1[4 * (j + 1)], Y1 + boff, F1 + boff,
                    S1 + boff, mb, -nt1[4 * j], ql, e);
       }
@@ -797,6 +787,11 @@ struct TcRun {
       const int v2 = (m1 & 1) ? (m2 >> 1) : (m1 >> 1);
       carry_own = (l1 & 1) ? l2 : l1;
       if (q < Utot) cnt = p1_emit(e, ql == 0 ? e.wl_first : v2, em);
+      int src[3];
+      if (PROV && q < Utot) {
+        p1_emit_src(e, ql == 0 ? e.wl_first : v2, aoff, boff, tailA, tailB, src);
+        if (ql == 0) wtail[node] = e.farL ? tailB : tailA;
+      }
       int total;
       const int pre = tm.excl_sum(cnt, total);
       const int p0 = wpos + pre;
@@ -806,6 +801,7 @@ struct TcRun {
           wF()[p0 + c] = em[c].f;
           wS()[p0 + c] = em[c].s;
           wN()[p0 + c] = node;
+          if (PROV) wsrc[p0 + c] = src[c];
         }
       } else if (cnt > 0) {
         ovf = true;
@@ -912,7 +908,12 @@ struct TcRun {
 
   // pass 3: restriction and exercise for every piece of w; writes level t, the
   // points from position zbase on (w of a chunk of nodes: its first node's points)
-  OB_HD bool pass3(int t, int wtot, int& ztot, int zbase = 0) {
+  // PROV (the adjoint's rerun): zsrc[p] receives the line (KW..KU4 code) the function
+  // follows right of emitted point p, ztail[node] that of its left tail; argA, argB are the
+  // points where pass 2's running minima are attained.
+  template <bool PROV = false>
+  OB_HD bool pass3(int t, int wtot, int& ztot, int zbase = 0, unsigned* zsrc = nullptr,
+                   unsigned* ztail = nullptr, const int* argA = nullptr, const int* argB = nullptr) {
     const int lane = tm.lane();
     const int nNodes = 2 * (t + 1);
     int* off = outOff;
@@ -925,7 +926,7 @@ struct TcRun {
     for (int base = 0; base < wtot; base += Team::W) {
       const int i = base + lane;
       const bool ok = i < wtot;
-      PieceOut<double> po;
+      typename std::conditional<PROV, PieceOutL<double>, PieceOut<double>>::type po;
       po.ntl = po.nm = 0;
       po.first = EmT<double>{0.0, 0.0, 0.0};
       po.last_slope = po.tail_slope = 0.0;
@@ -956,6 +957,21 @@ struct TcRun {
           for (int c = 0; c < po.ntl; ++c, ++w) { Yz[w] = po.tl[c].y; Fz[w] = po.tl[c].f; Sz[w] = po.tl[c].s; }
           if (emit_first) { Yz[w] = po.first.y; Fz[w] = po.first.f; Sz[w] = po.first.s; ++w; }
           for (int c = 0; c < po.nm; ++c, ++w) { Yz[w] = po.m[c].y; Fz[w] = po.m[c].f; Sz[w] = po.m[c].s; }
+          if constexpr (PROV) {
+            // lines 0..4 of piece(): the piece of w, the cA line (cA_i in the left tail,
+            // cA_{i+1} inside the piece), the cB line, the two branches of u
+            auto code = [&](int l, bool left_tail) -> unsigned {
+              if (l == 0) return ((unsigned)KW << KSHIFT) | (unsigned)i;
+              if (l == 1) return ((unsigned)KA << KSHIFT) | (unsigned)(left_tail ? argA[i] : argA[i + 1]);
+              if (l == 2) return ((unsigned)KB << KSHIFT) | (unsigned)argB[i];
+              return ((unsigned)(l == 3 ? KU3 : KU4) << KSHIFT) | (unsigned)i;
+            };
+            int v = p0;
+            for (int c = 0; c < po.ntl; ++c, ++v) zsrc[v] = code(po.tl_line[c], true);
+            if (emit_first) zsrc[v++] = code(po.first_line, false);
+            for (int c = 0; c < po.nm; ++c, ++v) zsrc[v] = code(po.m_line[c], false);
+            if (head) ztail[node] = code(po.tail_line, true);
+          }
         } else if (nout > 0) {
           ovf = true;
         }

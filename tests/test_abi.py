@@ -58,4 +58,5 @@ def test_stats_record_matches_header():
     fields = re.findall(r"^\s*(int64_t|int32_t)\s+(\w+);", body, re.M)
     assert [n for _, n in fields] == [n for n, _ in ObStats._fields_]
     sizes = {"int64_t": 8, "int32_t": 4}
-    assert ctypes.sizeof(ObStats) == sum(sizes[t] for t, _ in fields)
+    packed = sum(sizes[t] for t, _ in fields)
+    assert ctypes.sizeof(ObStats) == (packed + 7) // 8 * 8  # tail padding to the int64 alignment

@@ -253,7 +253,7 @@ def test_capacity_retry_and_exhaustion():
     """Small per-warp slices force follow-up launches with larger slices (same results);
     a pool too small for an option yields OB_ERR_CAPACITY for it, the others complete."""
     base = _child({})
-    small = _child({"OB_ARENA_MB": "1", "OB_WARPS_PER_SM": "2"})
+    small = _child({"OB_SM_KB": "2048"})  # 2 MiB of first-tier scratch per CTA
     assert small["stats"]["retried"] > 0
     assert small["st"] == base["st"] == [0] * len(base["st"])
     assert np.array_equal(np.array(small["out"]).view(np.int64), np.array(base["out"]).view(np.int64))
@@ -266,21 +266,27 @@ def test_capacity_retry_and_exhaustion():
 
 
 # ---------------------------------------------------------------- graphs, team widths, autotuner
-def test_team_widths_give_bitwise_equal_prices():
+def test_team_widths_and_on_chip_step_give_bitwise_equal_prices():
+    """Every team width, and the fused level step with w in shared memory (all that fits,
+    and a small chunk so that nodes and chunks fall back to the global scratch), price the
+    same bits."""
     ob = _ob()
-    t = W.random_table(96, 4711, N_lo=20, N_hi=400)
+    t = W.concat(W.random_table(96, 4711, N_lo=20, N_hi=400),
+                 W.make(S0=100, K=100, sigma=0.1, T=0.1, k=0.02, N=300, payoff=W.CALL))
     try:
         res = []
-        for tw in (16, 12, 8, 4):
-            ob.ob_configure(team_warps=tw, use_graphs=0)
+        for tw, chip in ((16, 0), (12, 0), (8, 0), (4, 0), (16, -1), (8, -1), (16, 300)):
+            ob.ob_configure(team_warps=tw, use_graphs=0, chip_points=chip)
             out, st = _gpu(t)
-            assert ob.ob_get_stats()["team_warps"] == tw
+            s = ob.ob_get_stats()
+            assert s["team_warps"] == tw
+            assert (s["chip_points"] > 0) == (chip != 0)
             res.append((out, st))
         for out, st in res[1:]:
             assert np.array_equal(st, res[0][1])
             assert np.array_equal(out.view(np.int64), res[0][0].view(np.int64))
     finally:
-        ob.ob_configure(team_warps=16, use_graphs=1)
+        ob.ob_configure(team_warps=16, use_graphs=1, chip_points=0)
 
 
 def test_graph_capture_then_replay_reads_current_inputs():
@@ -312,22 +318,27 @@ def test_graph_capture_then_replay_reads_current_inputs():
         assert np.array_equal(r1.view(np.int64), d1.view(np.int64))
         assert np.array_equal(r2.view(np.int64), d2.view(np.int64))
     finally:
-        ob.ob_configure(team_warps=16, use_graphs=1)
+        ob.ob_configure(team_warps=16, use_graphs=1, chip_points=0)
 
 
-def test_autotune_keeps_a_valid_width():
+def test_autotune_keeps_a_valid_configuration_and_prices_match_oracle():
     ob = _ob()
     t = W.random_table(200, 2024, N_lo=50, N_hi=500)
     before, _ = _gpu(t)
     try:
-        tw, ms = ob.autotune(t, sample=100)
+        tw, chip, ms = ob.autotune(t, sample=100)
         assert tw in (4, 8, 12, 16) and all(v > 0 for v in ms.values())
-        assert ms[tw] == min(ms.values())
-        after, _ = _gpu(t)
-        assert ob.ob_get_stats()["team_warps"] == tw
+        chosen = "%d+chip" % tw if chip else "%d" % tw
+        assert len(ms) == 6 and ms[chosen] == min(ms.values())
+        after, st = _gpu(t)
+        s = ob.ob_get_stats()
+        assert s["team_warps"] == tw and s["chip_points"] == chip
         assert np.array_equal(before.view(np.int64), after.view(np.int64))
+        idx = np.arange(0, len(t), 25)
+        ref, rst = oracle.price_ask_bid(t[idx], nthreads=8)
+        _assert_parity(t[idx], after[idx], st[idx], ref, rst)
     finally:
-        ob.ob_configure(team_warps=16, use_graphs=1)
+        ob.ob_configure(team_warps=16, use_graphs=1, chip_points=0)
 
 
 # ---------------------------------------------------------------- whole-GPU form (large single options)
@@ -386,3 +397,31 @@ def test_price_curves_ordering_at_scale():
     idx = np.array([1, 5, 61, 119, 122])
     ref, rst = oracle.price_ask_bid(t[idx], nthreads=5)
     _assert_parity(t[idx], out[idx], st[idx], ref, rst)
+
+
+# ---------------------------------------------------------------- CRR on the whole GPU
+def test_crr_wide_equals_crr_kernel_bitwise():
+    """Trapezoid tiles of 64 levels over every SM give the same bits as the warp kernel,
+    for N below and above a tile, above the warp kernel's shared-memory size, and for the
+    invalid and arbitrage records."""
+    t = W.concat(W.random_table(40, 6100, N_lo=1, N_hi=3000, k_zero=True), W.make(k=0.0, N=1),
+                 W.make(k=0.0, N=64), W.make(k=0.0, N=65), W.make(N=0), W.make(R=5.0, N=2, T=1.0),
+                 W.make(k=0.0, N=2400, payoff=W.SPREAD, K=95.0, K2=105.0))
+    a, sa = _ob().crr(t)
+    b, sb = _ob().crr(t, wide=True)
+    a, sa, b, sb = a.cpu().numpy(), sa.cpu().numpy(), b.cpu().numpy(), sb.cpu().numpy()
+    assert np.array_equal(sa, sb)
+    ok = sa == 0
+    assert np.array_equal(a[ok].view(np.int64), b[ok].view(np.int64))
+    assert np.all(np.isnan(b[~ok]))
+
+
+def test_crr_wide_appendix_put_large_n():
+    """The Appendix put at N = 20000 and 40000 on the whole GPU: 13.906, and the oracle."""
+    t = W.concat(W.appendix_put(20000), W.appendix_put(40000))
+    g, s = _ob().crr(t, wide=True)
+    g, s = g.cpu().numpy(), s.cpu().numpy()
+    ref, _ = oracle.crr_price(t, nthreads=2)
+    assert np.all(s == 0)
+    assert np.all(np.abs(g - ref) <= RTOL * ref)
+    assert [round(float(x), 3) for x in g] == [13.906, 13.906]

@@ -98,10 +98,14 @@ def test_fused_level_step_is_bitwise_equal(cap):
             assert np.array_equal(pts1, pts2)
 
 
-def test_host_adjoint_matches_dual_gradient():
-    t = W.random_table(6, 31500, N_lo=2, N_hi=50)
+@pytest.mark.parametrize("payoff", [W.PUT, W.CALL, W.SPREAD])
+def test_host_adjoint_matches_oracle_gradient(payoff):
+    """The adjoint (line adjoints per piece) against the oracle's gradient on 40 options of
+    one payoff, N in [2, 160]: exercise branches in the left tails, running minima at the
+    ends of their range, and the crossings of nearly parallel pieces of calls and spreads."""
+    t = W.random_table(40, 31500 + payoff, N_lo=2, N_hi=160, payoffs=(payoff,))
     t["k"] = np.maximum(t["k"], 1e-4)
-    rout, rgrad, rst = oracle.greeks(t, nthreads=3)
+    rout, rgrad, rst = oracle.greeks(t, nthreads=8)
     P = ctypes.c_void_p
     for i in range(len(t)):
         a = _rec(t[i])
