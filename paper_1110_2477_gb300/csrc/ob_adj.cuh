@@ -40,6 +40,13 @@ struct LvRef {
   int np;       // points
 };
 
+// Where the record of one level lies in the record store: rd + d (wY, then wS; wtot each)
+// and ri + i (wN, wsrc: wtot each; zsrc: ztot; wtail, ztail: 2(t+1) each).
+struct LvRec {
+  long long d, i;
+  int wtot, ztot;
+};
+
 struct AdjLay {
   double* sd;       // level store: points
   long long sd_cap;
@@ -57,6 +64,13 @@ struct AdjLay {
   unsigned* ztail;
   int *argA, *argB;       // pass 2: where the running minima of g and h are attained [cap]
   int cap;
+  // record store: per level of the segment being swept, what its adjoint needs of the
+  // forward level step (y, slope and node of every point of w, and the four codes)
+  LvRec* rec;             // [N+2]
+  double* rd;             // wY, wS per level
+  long long rd_cap;
+  int* ri;                // wN, wsrc, zsrc, wtail, ztail per level
+  long long ri_cap;
 };
 
 // Split an arena between the pricing arrays (cap points each), the adjoint arrays and
@@ -65,7 +79,8 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   const size_t nodes = 2 * ((size_t)N + 2);
   const size_t node_arrays = 4 * al256(sizeof(double) * nodes) + 5 * al256(sizeof(double) * nodes) +
                              2 * al256(sizeof(int) * nodes);
-  const size_t nb = node_bytes(N) + 40 * 256 + al256(sizeof(LvRef) * ((size_t)N + 2)) + node_arrays;
+  const size_t nb = node_bytes(N) + 40 * 256 + al256(sizeof(LvRef) * ((size_t)N + 2)) +
+                    al256(sizeof(LvRec) * ((size_t)N + 2)) + node_arrays;
   if (bytes < nb) return false;
   const size_t per = ELEM_BYTES + 6 * sizeof(double) + 4 * sizeof(int);
   size_t cap = (size_t)((double)(bytes - nb) * 0.35) / per;
@@ -74,6 +89,7 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   char* p = carve_cap(base, N, cap, L);
   auto take = [&](size_t sz) { char* r = p; p += al256(sz); return r; };
   A.ref = (LvRef*)take(sizeof(LvRef) * ((size_t)N + 2));
+  A.rec = (LvRec*)take(sizeof(LvRec) * ((size_t)N + 2));
   for (int b = 0; b < 2; ++b) {
     A.pc[b] = (double*)take(sizeof(double) * cap);
     A.ps[b] = (double*)take(sizeof(double) * cap);
@@ -102,9 +118,18 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   if (rest < so_ints * sizeof(int) + 4096) return false;
   A.so = (int*)take(sizeof(int) * so_ints);
   A.so_cap = (long long)so_ints;
-  A.sd = (double*)p;
-  A.sd_cap = (long long)((bytes - (size_t)(p - base)) / sizeof(double)) - 64;
-  return A.sd_cap > 0;
+  // the rest: 45 % level store (checkpoints and the segment's levels, 24 bytes a point),
+  // 55 % record store (the segment's records, 16 + 12 bytes a point of w, 4 of z)
+  const size_t left = bytes - (size_t)(p - base) - 1024;
+  const size_t lv = (size_t)((double)left * 0.45) & ~(size_t)255;
+  A.sd = (double*)take(lv);
+  A.sd_cap = (long long)(lv / sizeof(double));
+  const size_t rdb = ((left - lv) * 4 / 7) & ~(size_t)255;  // doubles: 16 of every 28 bytes
+  A.rd = (double*)take(rdb);
+  A.rd_cap = (long long)(rdb / sizeof(double));
+  A.ri = (int*)p;
+  A.ri_cap = (long long)((bytes - (size_t)(p - base)) / sizeof(int)) - 64;
+  return A.sd_cap > 0 && A.ri_cap > 0;
 }
 
 OB_HD void atomic_add(double* a, double v) {
@@ -133,7 +158,77 @@ struct TcAdj {
   int N;
   double g[2][NPAR];     // this lane's share of d ask / d theta (g[0]) and d bid / d theta (g[1])
   long long sd_top, so_top;
-  int wtot_cur = 0;      // points of w of the adjoint level in progress
+  long long rd_top = 0, ri_top = 0;
+
+  // the record of one level (see LvRec)
+  struct RecView {
+    const double *wY, *wS;
+    const int *wN, *wsrc;
+    const unsigned* zsrc;
+    const int* wtail;
+    const unsigned* ztail;
+    int wtot, ztot;
+  };
+  OB_HD RecView view(int t) const {
+    const LvRec r = A.rec[t];
+    const int nodes = 2 * (t + 1);
+    RecView v;
+    v.wY = A.rd + r.d;
+    v.wS = v.wY + r.wtot;
+    v.wN = A.ri + r.i;
+    v.wsrc = v.wN + r.wtot;
+    v.zsrc = (const unsigned*)(v.wsrc + r.wtot);
+    v.wtail = (const int*)(v.zsrc + r.ztot);
+    v.ztail = (const unsigned*)(v.wtail + nodes);
+    v.wtot = r.wtot;
+    v.ztot = r.ztot;
+    return v;
+  }
+  // keep what the adjoint of level t needs from the level step just run
+  OB_HD bool rec_store(int t, int wtot, int ztot) {
+    const int nodes = 2 * (t + 1);
+    const long long nd = 2LL * wtot, ni = 2LL * wtot + ztot + 2LL * nodes;
+    if (rd_top + nd > A.rd_cap || ri_top + ni > A.ri_cap) return false;
+    A.rec[t] = LvRec{rd_top, ri_top, wtot, ztot};
+    rd_top += nd;
+    ri_top += ni;
+    double* wY = A.rd + A.rec[t].d;
+    double* wS = wY + wtot;
+    int* wN = A.ri + A.rec[t].i;
+    int* wsrc = wN + wtot;
+    unsigned* zsrc = (unsigned*)(wsrc + wtot);
+    int* wtail = (int*)(zsrc + ztot);
+    unsigned* ztail = (unsigned*)(wtail + nodes);
+    for (int i = tm.lane(); i < wtot; i += Team::W) {
+      wY[i] = L.wY[i];
+      wS[i] = L.wS[i];
+      wN[i] = L.wN[i];
+      wsrc[i] = A.wsrc[i];
+    }
+    for (int i = tm.lane(); i < ztot; i += Team::W) zsrc[i] = A.zsrc[i];
+    for (int n = tm.lane(); n < nodes; n += Team::W) {
+      wtail[n] = A.wtail[n];
+      ztail[n] = A.ztail[n];
+    }
+    tm.sync();
+    return true;
+  }
+  // level t from level t+1 (the in-views) into its bank, recording for its adjoint
+  OB_HD bool level_recorded(int t) {
+    const int bt = t & 1;
+    R.outY = L.zY[bt]; R.outF = L.zF[bt]; R.outS = L.zS[bt]; R.outOff = L.off[bt];
+    R.outCap = L.capZ;
+    R.node_table(t + 1);
+    R.node_table(t);
+    tm.sync();
+    int wtot, utot, ztot;
+    if (!R.template pass1<true>(t, wtot, utot, 0, -1, A.wsrc, A.wtail)) return false;
+    if (wtot > A.cap) return false;
+    R.template pass2<true>(t, wtot, A.argA, A.argB);
+    if (!R.template pass3<true>(t, wtot, ztot, 0, A.zsrc, A.ztail, A.argA, A.argB)) return false;
+    tm.sync();
+    return rec_store(t, wtot, ztot);
+  }
 
   OB_HD TcAdj(TcRun<Team>& R_, const AdjLay& A_)
       : R(R_), tm(R_.tm), o(R_.o), L(R_.L), A(A_), N(R_.N) {
@@ -227,21 +322,21 @@ struct TcAdj {
   // piece left of it (the piece right of a - 1, or w's left tail if a starts its node)
   // and the piece right of it.  Slopes: wS, or the tail's -S^a of the level-(t+1) node
   // it comes from.
-  OB_HD double left_slope(int t, int a, int node, bool first) const {
-    if (!first) return L.wS[a - 1];
-    const int code = A.wtail[node];  // -1 - (level-(t+1) node)
+  OB_HD double left_slope(int t, const RecView& V, int a, int node, bool first) const {
+    if (!first) return V.wS[a - 1];
+    const int code = V.wtail[node];  // -1 - (level-(t+1) node)
     const int n1 = -1 - code, W1 = t + 2;
     const int j1 = n1 >= W1 ? n1 - W1 : n1;
     return -L.nt[(t + 1) & 1][4 * j1];
   }
 
   // Line adjoint (cb, sb) of a piece of z at level t, following the line of `code`.
-  OB_HD void pull_z(int t, unsigned code, double cb, double sb) {
+  OB_HD void pull_z(int t, const RecView& V, unsigned code, double cb, double sb) {
     if (cb == 0.0 && sb == 0.0) return;
     const int kind = (int)(code >> KSHIFT);
     int a = (int)(code & KMASK);
     const int W0 = t + 1;
-    const int node = L.wN[a];
+    const int node = V.wN[a];
     const int p = node >= W0 ? 1 : 0;
     const int j = node - p * W0;
     const double* nt = L.nt[t & 1];
@@ -253,21 +348,21 @@ struct TcAdj {
     if (kind == KA || kind == KB) {
       const double S = nt[4 * j + (kind == KA ? 0 : 1)];
       // resolve points that coincide with y_a to within rounding by the lines' slopes
-      const double tol = 1e-12 * fmax(1.0, fabs(L.wY[a]));
+      const double tol = 1e-12 * fmax(1.0, fabs(V.wY[a]));
       for (int it = 0; it < 64; ++it) {
-        const bool last = (a + 1 >= wtot_cur) || L.wN[a + 1] != node;
-        if (last || !(L.wS[a + 1] + S < 0.0) || L.wY[a + 1] - L.wY[a] > tol) break;
+        const bool last = (a + 1 >= V.wtot) || V.wN[a + 1] != node;
+        if (last || !(V.wS[a + 1] + S < 0.0) || V.wY[a + 1] - V.wY[a] > tol) break;
         ++a;
       }
       for (int it = 0; it < 64; ++it) {
-        const bool first = (a == 0) || L.wN[a - 1] != node;
-        if (first || !(L.wS[a - 1] + S > 0.0) || L.wY[a] - L.wY[a - 1] > tol) break;
+        const bool first = (a == 0) || V.wN[a - 1] != node;
+        if (first || !(V.wS[a - 1] + S > 0.0) || V.wY[a] - V.wY[a - 1] > tol) break;
         --a;
       }
-      const bool first = (a == 0) || L.wN[a - 1] != node;
-      const double sP = left_slope(t, a, node, first), sQ = L.wS[a];
+      const bool first = (a == 0) || V.wN[a - 1] != node;
+      const double sP = left_slope(t, V, a, node, first), sQ = V.wS[a];
       const double mu = (sP == sQ) ? 0.0 : (sP + S) / (sP - sQ);
-      const double ys = L.wY[a];
+      const double ys = V.wY[a];
       if (first) {
         atomic_add(&A.wtc[node], (1.0 - mu) * cb);
         atomic_add(&A.wts[node], (1.0 - mu) * ys * cb);
@@ -290,10 +385,11 @@ struct TcAdj {
 
   // z_t's line adjoints (pc, ps per point; tc, ts per node) onto w's lines and the node
   // constants of level t
-  OB_HD void scatter_z(int t, int ztot, const double* pc, const double* ps, const double* tc, const double* ts) {
+  OB_HD void scatter_z(int t, const RecView& V, const double* pc, const double* ps, const double* tc,
+                       const double* ts) {
     const int nNodes = 2 * (t + 1);
-    for (int i = tm.lane(); i < ztot; i += Team::W) pull_z(t, A.zsrc[i], pc[i], ps[i]);
-    for (int n = tm.lane(); n < nNodes; n += Team::W) pull_z(t, A.ztail[n], tc[n], ts[n]);
+    for (int i = tm.lane(); i < V.ztot; i += Team::W) pull_z(t, V, V.zsrc[i], pc[i], ps[i]);
+    for (int n = tm.lane(); n < nNodes; n += Team::W) pull_z(t, V, V.ztail[n], tc[n], ts[n]);
     tm.sync();
     const int W0 = t + 1;
     for (int n = tm.lane(); n < nNodes; n += Team::W) {
@@ -303,11 +399,11 @@ struct TcAdj {
   }
 
   // w's line adjoints onto the lines of level t+1 (pc1, ps1 per point; tc1, ts1 per node)
-  OB_HD void scatter_w(int t, int wtot, double* pc1, double* ps1, double* tc1, double* ts1) {
-    for (int i = tm.lane(); i < wtot; i += Team::W) {
+  OB_HD void scatter_w(int t, const RecView& V, double* pc1, double* ps1, double* tc1, double* ts1) {
+    for (int i = tm.lane(); i < V.wtot; i += Team::W) {
       const double cb = A.wc[i], sb = A.ws[i];
       if (cb == 0.0 && sb == 0.0) continue;
-      const int code = A.wsrc[i];
+      const int code = V.wsrc[i];
       if (code >= 0) {
         atomic_add(&pc1[code], cb);
         atomic_add(&ps1[code], sb);
@@ -319,7 +415,7 @@ struct TcAdj {
     for (int n = tm.lane(); n < 2 * (t + 1); n += Team::W) {
       const double cb = A.wtc[n], sb = A.wts[n];
       if (cb == 0.0 && sb == 0.0) continue;
-      const int code = A.wtail[n];
+      const int code = V.wtail[n];
       atomic_add(&tc1[-1 - code], cb);
       atomic_add(&ts1[-1 - code], sb);
     }
@@ -379,9 +475,10 @@ struct TcAdj {
       // recompute levels c-1 .. lo from the checkpoint c (kept in the store after the checkpoints)
       sd_top = ckpt_sd;
       so_top = ckpt_so;
+      rd_top = ri_top = 0;
       for (int t = c - 1; t >= lo; --t) {
         in_from_store(t + 1);
-        if (!level_to_bank(t) || !store_from_bank(t)) return ST_CAPACITY;
+        if (!level_recorded(t) || !store_from_bank(t)) return ST_CAPACITY;
       }
       if (!seeded && c > 0) {  // root: the value at y = 0 of the piece right of every point <= 0
         seeded = true;
@@ -421,33 +518,25 @@ struct TcAdj {
           g[1][P_R] -= bid * dl_R; g[1][P_T] -= bid * dl_T;
         }
       }
-      // adjoint levels lo .. c-1 (each needs level t+1 <= c)
+      // adjoint levels lo .. c-1 (each needs level t+1 <= c), from the records
       for (int t = lo; t <= c - 1; ++t) {
-        R.use_banks(t);  // pass 3's rerun writes level t into its bank (scratch)
-        in_from_store(t + 1);
         R.node_table(t + 1);
         R.node_table(t);
         tm.sync();
-        int wtot, utot, ztot;
-        if (!R.template pass1<true>(t, wtot, utot, 0, -1, A.wsrc, A.wtail)) return ST_CAPACITY;
-        if (wtot > A.cap) return ST_CAPACITY;
-        R.template pass2<true>(t, wtot, A.argA, A.argB);
-        wtot_cur = wtot;
-        if (!R.template pass3<true>(t, wtot, ztot, 0, A.zsrc, A.ztail, A.argA, A.argB)) return ST_CAPACITY;
-        if (ztot != A.ref[t].np) return ST_CAPACITY;  // the rerun reproduces the stored level
+        const RecView V = view(t);
         const int nNodes = 2 * (t + 1), nNodes1 = 2 * (t + 2);
         const int nxt = cur ^ 1;
         const int np1 = A.ref[t + 1].np;
-        if (np1 > A.cap) return ST_CAPACITY;
-        zero(A.wc, wtot); zero(A.ws, wtot);
+        if (np1 > A.cap || V.wtot > A.cap) return ST_CAPACITY;
+        zero(A.wc, V.wtot); zero(A.ws, V.wtot);
         zero(A.wtc, nNodes); zero(A.wts, nNodes);
         zero(A.nSa, nNodes); zero(A.nSb, nNodes); zero(A.nXi, nNodes);
         zero(A.pc[nxt], np1); zero(A.ps[nxt], np1);
         zero(A.tc[nxt], nNodes1); zero(A.ts[nxt], nNodes1);
         tm.sync();
-        scatter_z(t, ztot, A.pc[cur], A.ps[cur], A.tc[cur], A.ts[cur]);
+        scatter_z(t, V, A.pc[cur], A.ps[cur], A.tc[cur], A.ts[cur]);
         tm.sync();
-        scatter_w(t, wtot, A.pc[nxt], A.ps[nxt], A.tc[nxt], A.ts[nxt]);
+        scatter_w(t, V, A.pc[nxt], A.ps[nxt], A.tc[nxt], A.ts[nxt]);
         cur = nxt;
       }
       lo = c;
