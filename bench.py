@@ -424,9 +424,34 @@ def run_paper(args, rank, world, local):
         oracle.price_ask_bid(one, nthreads=1)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": float(nodes[2]) / dt, "unit": "node updates/s", "cores": 1,
-                                "kind": "oracle", "sample": "the N=1500 put at k=0.005, one thread, "
-                                "%.2f s" % dt}
+                                "kind": "oracle", "cpu_model": cpu_model(),
+                                "sample": "the N=1500 put at k=0.005, one thread, %.2f s" % dt,
+                                "alg1": alg1_speedups(one, dt, crr=False)}
+        crr_one = W.appendix_put(20000)
+        t0 = time.perf_counter()
+        oracle.crr_price(crr_one)
+        line["cpu_baseline"]["alg1_crr"] = alg1_speedups(crr_one, time.perf_counter() - t0, crr=True)
     print(json.dumps(line), flush=True)
+
+
+def alg1_speedups(opt, serial_s, crr):
+    """The paper's parallel scheme (Section 4.2, Algorithm 1) over the oracle's node steps on
+    the host cores: time and speedup over the serial oracle for 1, 2, 4, 8, ... threads and
+    blocks of L = 5 and 50 levels (the paper's Tables 2 and 3 shape)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    threads = sorted({p for p in (1, 2, 4, 8, 16, cores) if p <= cores})
+    ref = oracle.crr_price(opt)[0] if crr else oracle.price_ask_bid(opt)[0][0]
+    rows = []
+    for p in threads:
+        for L in (5, 50):
+            t0 = time.perf_counter()
+            out, st, _ = oracle.alg1_price(opt, p, L, crr=crr)
+            dt = time.perf_counter() - t0
+            rows.append({"threads": p, "L": L, "s": round(dt, 3), "speedup": round(serial_s / dt, 2),
+                         "status": st, "bitwise_equal": bool(np.array_equal(out, ref))})
+    return {"option": "N=%d %s, k=%g" % (int(opt["N"][0]), "CRR put" if crr else "put", float(opt["k"][0])),
+            "serial_s": round(serial_s, 3), "cores": cores, "rows": rows}
 
 
 def run_greeks(args, rank, world, local):
@@ -475,9 +500,9 @@ def run_greeks(args, rank, world, local):
     if rank != 0:
         return
     value = world * n * args.steps / job_s
-    # every level is evaluated three times (forward, segment recompute, adjoint rerun), each
-    # counted as the pricing line counts one
-    g_flops = 3.0 * FLOPS_PER_MERGED_POINT * float(u_points)
+    # every level is evaluated twice (forward, segment recompute with its records), each
+    # counted as the pricing line counts one; the reverse sweep's scatter is not counted
+    g_flops = 2.0 * FLOPS_PER_MERGED_POINT * float(u_points)
     g_achieved = g_flops / (job_s / args.steps) / 1e12
     line = {
         "metric": "options/s with Greeks (ask, bid and 12 derivatives), FP64", "value": value,
@@ -492,9 +517,9 @@ def run_greeks(args, rank, world, local):
         "gpu_launches": 3 * args.steps, "step_ms": step_ms, "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": g_achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
                      "frac": g_achieved / peak["tflops"], "traffic": None,
-                     "note": "algorithmic FP64 flops = 3 level evaluations (forward, recompute, adjoint "
-                             "rerun) x %d per merged successor breakpoint (U of the pricing pass); the "
-                             "adjoint's scatter work is not counted; peak = ob_fp64_peak" %
+                     "note": "algorithmic FP64 flops = 2 level evaluations (forward, segment "
+                             "recompute) x %d per merged successor breakpoint (U of the pricing pass); "
+                             "the reverse sweep's scatter is not counted; peak = ob_fp64_peak" %
                              FLOPS_PER_MERGED_POINT, "peak_measurement": peak},
     }
     if not args.no_cpu_baseline:

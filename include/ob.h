@@ -18,10 +18,17 @@
  *     recursion pi_t = max(P_t, (p pi^u + (1-p) pi^d)/r) over N levels.
  * All arithmetic is IEEE binary64.
  *
- * Threading: calls may come from any host thread; a call that needs the
- * library's scratch pool on a device serialises on an internal mutex only
- * while the pool is (re)allocated.  Kernels run asynchronously on the given
- * stream.
+ * Threading and ordering: calls may come from any host thread and on any
+ * stream.  A call that uses the library's scratch pool on a device enqueues
+ * under that device's mutex and orders its device work behind the previous
+ * pooled call's (it waits on an event the previous call recorded, then
+ * records its own), so calls on different streams never overlap in the pool.
+ * While the caller's stream is being captured into a CUDA graph this ordering
+ * is skipped (an event recorded outside a capture cannot be waited on inside
+ * it); such callers order their calls themselves.  Kernels run
+ * asynchronously on the given stream.  Growing the pool synchronises the
+ * device.  ob_price_ask_bid_noalloc uses a fixed array of its own instead of
+ * the pool: overlapping calls of it race.
  */
 #ifndef OB_H_
 #define OB_H_

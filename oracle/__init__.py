@@ -11,6 +11,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 library: the C++ source here (``ob_oracle.cpp``) is compiled by ``gcc`` into
 ``liboboracle.so`` and loaded with ctypes.
 
+``alg1_price`` runs the paper's own parallel scheme (Section 4.2, Algorithm 1: blocks of
+levels split into regions A and B, signals between neighbouring threads, a barrier per
+round, fewer threads near the root) over the same node steps, as a CPU comparator.
+
 Sub-modules:
   * ``exact``      -- the same recursion in exact rational arithmetic.
   * ``hedging_lp`` -- brute-force superhedging / stopping-time linear programs
@@ -64,8 +68,12 @@ def _load():
             lib.or_pl_eval.argtypes = [P, P, i32, d, d, P, i32, P]
             lib.or_node_step.argtypes = [P, P, i32, d, d, P, P, i32, d, d, d, d, d, d, d, i32,
                                          P, P, i32, P, P]
+            lib.or_alg1_tc.argtypes = [P, i32, i32, P, P, P]
+            lib.or_alg1_crr.argtypes = [P, i32, i32, P, P, P]
+            lib.or_alg1_rounds.argtypes = [i32, i32, i32, P, i32]
             for f in (lib.or_price_tc, lib.or_tc_stats, lib.or_greeks_tc, lib.or_price_crr,
-                      lib.or_pl_envelope, lib.or_pl_restrict, lib.or_pl_eval, lib.or_node_step):
+                      lib.or_pl_envelope, lib.or_pl_restrict, lib.or_pl_eval, lib.or_node_step,
+                      lib.or_alg1_tc, lib.or_alg1_crr, lib.or_alg1_rounds):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -130,6 +138,29 @@ def tc_stats(opt):
     return {"nodes": int(counts[0]), "bp_seller": int(counts[1]), "bp_buyer": int(counts[2]),
             "max_seller": int(counts[3]), "max_buyer": int(counts[4]),
             "per_level_seller": per[0::2].copy(), "per_level_buyer": per[1::2].copy()}
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def alg1_price(opt, threads: int, L: int, crr: bool = False):
+    """One option by the paper's parallel scheme (Section 4.2, Algorithm 1) on `threads`
+    threads with blocks of at most L levels, over the same node steps as price_ask_bid
+    (crr=False: returns ([ask, bid], status, nodes per thread)) or crr_price (crr=True:
+    returns ([price], status, nodes per thread))."""
+    a = _as_table(opt)[:1]
+    out = np.empty(1 if crr else 2, np.float64)
+    st = np.zeros(1, np.int32)
+    per = np.zeros(max(int(threads), 1), np.int64)
+    f = _load().or_alg1_crr if crr else _load().or_alg1_tc
+    f(_ptr(a), int(threads), int(L), _ptr(out), _ptr(st), _ptr(per))
+    return out, int(st[0]), per
+
+
+def alg1_rounds(top: int, threads: int, L: int):
+    """The rounds of Algorithm 1 from base level `top`: a list of (B, D, active threads)."""
+    cap = 4 * (top + 2)
+    buf = np.zeros(3 * cap, np.int32)
+    n = _load().or_alg1_rounds(int(top), int(threads), int(L), _ptr(buf), cap)
+    return [tuple(int(v) for v in buf[3 * k:3 * k + 3]) for k in range(n)]
 
 
 # ---------------------------------------------------------------- PL primitives

@@ -23,6 +23,10 @@
 //    level, and its European counterpart (no early exercise).
 //  * Forward-mode dual numbers through the same induction give the
 //    derivatives of ask and bid with respect to (S0, K, sigma, R, T, k).
+//  * Section 4.2, Algorithm 1: the paper's own parallel scheme (blocks of
+//    levels, regions A and B, signals between neighbouring threads, a barrier
+//    per round) driving the same node steps on host threads, as a CPU
+//    comparator; its results are bitwise the serial ones.
 //
 // Readings of the paper taken here:
 //  * "restricting the slopes" of w_t/r to [-S^a_t, -S^b_t] is the
@@ -48,8 +52,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -803,6 +809,187 @@ int pl_to(const PL<double>& F, double* y, double* f, int cap, double* sL, double
   return m;
 }
 
+// ---------------------------------------------------------------- Algorithm 1 (Section 4.2)
+// The paper's parallel scheme for one option on p threads, driving the node steps above
+// (price_tc's and price_crr's arithmetic, node for node, so the results are bitwise the
+// serial ones).  The tree is processed in rounds.  A round starts at a base level B whose
+// B+1 nodes were finished in the previous round; it computes the levels B-1 .. B-D.
+//   * Threads: while B+1 < 2p, p drops by one (every thread gets at least two nodes), so a
+//     retired thread takes no further part.
+//   * Blocks: thread i takes the columns [i q, (i+1) q) of every level of the round,
+//     q = floor((B+1)/p); the last thread takes the rest.  D = min(L, q - 1) >= 1.
+//   * Regions: the nodes of a block at level B-o whose two successors lie in the block's
+//     columns, [s, e-o), form region A (no dependence on other threads).  The remaining
+//     columns [e-o, e) form region B: node (B-o, e-1) needs column e = the next thread's
+//     first column at level B-o+1.
+//   * Synchronisation: thread i > 0 signals thread i-1 once it has finished the node of its
+//     first column at level B-D+1 (B-1 when D = 1); region A goes level by level, so by
+//     then every node of that column that thread i-1 reads is done.  Thread i-1 computes its
+//     region B after its region A and that signal.  All active threads meet at a barrier at
+//     the end of the round.
+//   * Storage: (L+1) rows of N+2 cells per party; level t lives in row t mod (L+1) (a round
+//     touches D+1 <= L+1 consecutive levels, so no two of them share a row).
+// Reading: the paper's listing uses n for a base level's index in one place and for its
+// node count in another, and gives the last block's size two ways; the node count B+1 and
+// the contiguous split above are taken.
+
+struct Alg1Round {
+  int B, D, p;
+};
+
+std::vector<Alg1Round> alg1_rounds(int top, int p, int L) {
+  std::vector<Alg1Round> r;
+  if (p < 1) p = 1;
+  if (L < 1) L = 1;
+  for (int B = top; B > 0;) {
+    while (p > 1 && B + 1 < 2 * p) --p;
+    const int q = (B + 1) / p;
+    const int D = std::min(L, q - 1);
+    r.push_back({B, D, p});
+    B -= D;
+  }
+  return r;
+}
+
+// A barrier for the threads of one round (their count is the same for all of them).
+struct RoundBarrier {
+  std::mutex mu;
+  std::condition_variable cv;
+  int arrived = 0;
+  int64_t gen = 0;
+  void arrive(int count) {
+    std::unique_lock<std::mutex> lk(mu);
+    const int64_t g = gen;
+    if (++arrived == count) {
+      arrived = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return gen != g; });
+    }
+  }
+};
+
+// Runs the rounds on p threads.  node(t, j) computes node (t, j) from level t+1 and returns
+// an error code (0 = OK); init(j) sets leaf j of level top.  nodes_per_thread (may be null)
+// receives the number of nodes each thread computed.
+template <class Node, class Init>
+int alg1_run(int top, int p, int L, Node node, Init init, int64_t* nodes_per_thread) {
+  const std::vector<Alg1Round> rounds = alg1_rounds(top, p, L);
+  if (p < 1) p = 1;
+  if (L < 1) L = 1;
+  std::vector<std::atomic<int>> sig(p);
+  for (auto& g : sig) g.store(0);
+  std::atomic<int> err(0);
+  RoundBarrier bar;
+  std::vector<int64_t> count(p, 0);
+  auto body = [&](int i) {
+    int64_t done = 0;  // nodes computed by this thread (kept local: no shared cache line)
+    {  // leaves, split as in the first round
+      const int P0 = rounds.empty() ? 1 : rounds[0].p;
+      if (i >= P0) return;
+      const int n = top + 1, q = n / P0;
+      const int s = i * q, e = (i == P0 - 1) ? n : (i + 1) * q;
+      for (int j = s; j < e; ++j) init(j);
+      bar.arrive(P0);
+    }
+    for (size_t k = 0; k < rounds.size(); ++k) {
+      const Alg1Round& R = rounds[k];
+      if (i >= R.p) break;
+      const int n = R.B + 1, q = n / R.p;
+      const int s = i * q, e = (i == R.p - 1) ? n : (i + 1) * q;
+      const int sig_level = (R.D > 1) ? R.B - R.D + 1 : R.B - 1;
+      auto compute = [&](int t, int j) {
+        if (err.load(std::memory_order_relaxed)) return;
+        const int rc = node(t, j);
+        if (rc) err.store(rc);
+        ++done;
+      };
+      for (int o = 1; o <= R.D; ++o) {  // region A, level by level
+        const int t = R.B - o;
+        const int m = std::min(e - o, t + 1);
+        for (int j = s; j < m; ++j) {
+          compute(t, j);
+          if (i > 0 && t == sig_level && j == s) sig[i].store((int)k + 1, std::memory_order_release);
+        }
+      }
+      if (i + 1 < R.p) {  // region B, after the next thread's signal
+        while (sig[i + 1].load(std::memory_order_acquire) < (int)k + 1) std::this_thread::yield();
+        for (int o = 1; o <= R.D; ++o) {
+          const int t = R.B - o;
+          for (int j = std::max(s, e - o); j < e && j <= t; ++j) compute(t, j);
+        }
+      }
+      bar.arrive(R.p);
+    }
+    count[i] = done;
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < p; ++i) pool.emplace_back(body, i);
+  body(0);
+  for (auto& th : pool) th.join();
+  if (nodes_per_thread)
+    for (int i = 0; i < p; ++i) nodes_per_thread[i] = count[i];
+  return err.load();
+}
+
+// ask and bid of one option (the model of price_tc) by Algorithm 1.
+int alg1_tc(const or_option_t& o, int p, int L, double& ask, double& bid, int64_t* per_thread) {
+  const Model<double> m = make_model<double>(o, o.S0, o.K, o.sigma, o.R, o.T, o.k);
+  const int N = m.N, rows = std::max(L, 1) + 1;
+  std::vector<PL<double>> zs((size_t)rows * (N + 2)), zb((size_t)rows * (N + 2));
+  auto cell = [&](std::vector<PL<double>>& z, int t, int j) -> PL<double>& {
+    return z[(size_t)(t % rows) * (N + 2) + j];
+  };
+  auto init = [&](int j) {
+    const double S = stock(m, N + 1, j);
+    const double Sa = (1.0 + m.k) * S, Sb = (1.0 - m.k) * S;
+    cell(zs, N + 1, j) = pl_expense(0.0, 0.0, Sa, Sb, false);
+    cell(zb, N + 1, j) = pl_expense(0.0, 0.0, Sa, Sb, true);
+  };
+  auto node = [&](int t, int j) -> int {
+    const double S = stock(m, t, j);
+    const double kt = (t == 0) ? 0.0 : m.k;
+    const double Sa = (1.0 + kt) * S, Sb = (1.0 - kt) * S;
+    double xi, zeta;
+    payoff_at(m, S, xi, zeta);
+    int rc = node_step(cell(zs, t + 1, j + 1), cell(zs, t + 1, j), m.r, Sa, Sb, xi, zeta, false,
+                       cell(zs, t, j));
+    if (rc) return rc;
+    return node_step(cell(zb, t + 1, j + 1), cell(zb, t + 1, j), m.r, Sa, Sb, xi, zeta, true,
+                     cell(zb, t, j));
+  };
+  const int rc = alg1_run(N + 1, p, L, node, init, per_thread);
+  if (rc) return rc;
+  ask = pl_eval(cell(zs, 0, 0), 0.0);
+  bid = -pl_eval(cell(zb, 0, 0), 0.0);
+  return OR_OK;
+}
+
+// The American CRR price (the recursion of price_crr) by Algorithm 1.
+int alg1_crr(const or_option_t& o, int p, int L, double& price, int64_t* per_thread) {
+  const int N = o.N, rows = std::max(L, 1) + 1;
+  const double dt = o.T / N;
+  const double u = std::exp(o.sigma * std::sqrt(dt));
+  const double d = 1.0 / u;
+  const double r = std::exp(o.R * dt);
+  const double pu = (r - d) / (u - d);
+  std::vector<double> c((size_t)rows * (N + 1));
+  auto cell = [&](int t, int j) -> double& { return c[(size_t)(t % rows) * (N + 1) + j]; };
+  auto init = [&](int j) {
+    cell(N, j) = std::max(crr_payoff(o.payoff, o.S0 * std::pow(u, 2 * j - N), o.K, o.K2), 0.0);
+  };
+  auto node = [&](int t, int j) -> int {
+    const double cont = (pu * cell(t + 1, j + 1) + (1.0 - pu) * cell(t + 1, j)) / r;
+    cell(t, j) = std::max(crr_payoff(o.payoff, o.S0 * std::pow(u, 2 * j - t), o.K, o.K2), cont);
+    return OR_OK;
+  };
+  const int rc = alg1_run(N, p, L, node, init, per_thread);
+  if (rc) return rc;
+  price = cell(0, 0);
+  return OR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -923,6 +1110,44 @@ int or_node_step(const double* yu, const double* fu, int mu, double sLu, double 
   int rc = node_step(U, D, r, Sa, Sb, xi, zeta, buyer != 0, z);
   if (rc) return rc;
   return pl_to(z, yo, fo, cap, sLo, sRo);
+}
+
+
+// ---- Algorithm 1 (Section 4.2) on p threads with blocks of at most L levels ----
+// One option; out[0] = ask, out[1] = bid (or_alg1_tc) or out[0] = the American CRR price
+// (or_alg1_crr); per_thread (may be NULL) receives the nodes each of the p threads computed.
+// Returns 0 or an error code (also in *status).
+int or_alg1_tc(const or_option_t* o, int p, int L, double* out, int32_t* status,
+               int64_t* per_thread) {
+  int rc = check_option(*o);
+  double ask = NAN, bid = NAN;
+  if (rc == OR_OK) rc = alg1_tc(*o, p, L, ask, bid, per_thread);
+  out[0] = rc ? NAN : ask;
+  out[1] = rc ? NAN : bid;
+  if (status) *status = rc;
+  return rc;
+}
+
+int or_alg1_crr(const or_option_t* o, int p, int L, double* out, int32_t* status,
+                int64_t* per_thread) {
+  int rc = check_option(*o);
+  double c = NAN;
+  if (rc == OR_OK) rc = alg1_crr(*o, p, L, c, per_thread);
+  out[0] = rc ? NAN : c;
+  if (status) *status = rc;
+  return rc;
+}
+
+// The rounds of Algorithm 1 from base level `top`: (B, D, p) per round into out (3 ints a
+// round, at most cap rounds).  Returns the number of rounds.
+int or_alg1_rounds(int top, int p, int L, int32_t* out, int cap) {
+  const std::vector<Alg1Round> r = alg1_rounds(top, p, L);
+  for (size_t k = 0; k < r.size() && (int)k < cap; ++k) {
+    out[3 * k] = r[k].B;
+    out[3 * k + 1] = r[k].D;
+    out[3 * k + 2] = r[k].p;
+  }
+  return (int)r.size();
 }
 
 }  // extern "C"
