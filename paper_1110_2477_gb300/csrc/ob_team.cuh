@@ -275,14 +275,16 @@ struct BlockTeam {
     }
     if (l == 31) h[W + w] = x;
     __syncthreads();
-    int off = 0, tot = 0;
-    for (int k = 0; k < NW; ++k) {
-      const int c = (int)h[W + k];
-      if (k < w) off += c;
-      tot += c;
+    // across warps: lane k of every warp takes warp k's total and the warp scans them with
+    // shuffles; warp w's offset is the inclusive sum of warps 0..w-1
+    int c = (l < NW) ? (int)h[W + l] : 0;
+    for (int d = 1; d < NW; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, c, d);
+      if (l >= d) c += y;
     }
-    total = tot;
-    return off + x - v;
+    const int before = __shfl_sync(0xffffffffu, c, (w + 31) & 31);
+    total = __shfl_sync(0xffffffffu, c, NW - 1);
+    return (w ? before : 0) + x - v;
   }
   __device__ __forceinline__ long long seg_min(long long v, bool head, long long& carry) const {
     long long* h = half();
