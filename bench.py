@@ -500,9 +500,10 @@ def run_greeks(args, rank, world, local):
     if rank != 0:
         return
     value = world * n * args.steps / job_s
-    # every level is evaluated twice (forward, segment recompute with its records), each
-    # counted as the pricing line counts one; the reverse sweep's scatter is not counted
-    g_flops = 2.0 * FLOPS_PER_MERGED_POINT * float(u_points)
+    # every level is evaluated once (the forward pass keeps the records of every level: each
+    # option of this workload fits), counted as the pricing line counts it; the recording and
+    # the reverse sweep's scatter are not counted
+    g_flops = 1.0 * FLOPS_PER_MERGED_POINT * float(u_points)
     g_achieved = g_flops / (job_s / args.steps) / 1e12
     line = {
         "metric": "options/s with Greeks (ask, bid and 12 derivatives), FP64", "value": value,
@@ -517,9 +518,10 @@ def run_greeks(args, rank, world, local):
         "gpu_launches": 3 * args.steps, "step_ms": step_ms, "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": g_achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
                      "frac": g_achieved / peak["tflops"], "traffic": None,
-                     "note": "algorithmic FP64 flops = 2 level evaluations (forward, segment "
-                             "recompute) x %d per merged successor breakpoint (U of the pricing pass); "
-                             "the reverse sweep's scatter is not counted; peak = ob_fp64_peak" %
+                     "note": "algorithmic FP64 flops = 1 level evaluation (the forward pass, which "
+                             "keeps the records of every level) x %d per merged successor breakpoint "
+                             "(U of the pricing pass); recording and the reverse sweep are not "
+                             "counted; peak = ob_fp64_peak" %
                              FLOPS_PER_MERGED_POINT, "peak_measurement": peak},
     }
     if not args.no_cpu_baseline:

@@ -77,7 +77,10 @@ enum {
  *   stream  cudaStream_t (NULL = legacy default stream).
  * Batched form: one persistent launch whose CTAs take options from a device
  * queue, costliest first (work stealing), each option on a whole-CTA team (one
- * 512-thread CTA per SM by default, see ob_configure); options whose functions
+ * 512-thread CTA per SM by default, see ob_configure); once the options left
+ * are predicted to cost less than 4 % of the mean work per SM
+ * (OB_SPLIT_FACTOR), each 16-warp CTA splits into two 8-warp teams that take
+ * options independently (two options per SM); options whose functions
  * outgrow a CTA's scratch are retried by follow-up launches with larger
  * scratch, on the same stream, without returning to the host.  The launch
  * sequence is captured in a CUDA graph per (params, n_options, out, status)
@@ -89,6 +92,27 @@ enum {
  * until ob_release(). */
 int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                      void* stream);
+
+/* ob_price_ask_bid plus the hedge at the root of each option (Section 3: the
+ * rebalancing at t = 0, where there are no costs).  A portfolio covers the
+ * seller from t = 1 on iff, after moving its stock holding to y', its cash
+ * lies above w_0/r at y'; v_0(0) = min over y' of w_0(y')/r + S0 y'.
+ *   hedge   DEVICE pointer, 4*n_options doubles:
+ *           hedge[4i]   the seller's stock holding y* after rebalancing at t = 0
+ *                       from no stock (the y' attaining v_0(0); the rightmost
+ *                       among equal minima),
+ *           hedge[4i+1] the buyer's (the same for the buyer's functions),
+ *           hedge[4i+2] 1 when immediate exercise sets the ask (u_0(0) > v_0(0)),
+ *                       else 0,
+ *           hedge[4i+3] 1 when the buyer does better exercising at once
+ *                       (u_0(0) < v_0(0)), else 0;
+ *           NaN for an option whose status is not OB_OK.
+ * Without costs (k = 0) y* is the CRR delta at t = 0 for the seller and its
+ * negative for the buyer.  Same launch sequence, graph caching and ordering as
+ * ob_price_ask_bid (hedge joins the graph key); the fused on-chip level step is
+ * not used by this call.  Returns OB_ERR_ARG when hedge is NULL. */
+int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                           double* hedge, void* stream);
 
 /* The plain form of the same computation: one warp per option, options taken
  * in index order with a static assignment, no queue and no retry (an option
@@ -137,11 +161,14 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
  * parameter (an exercise boundary, a breakpoint appearing) it is one of the
  * one-sided derivatives.  d/dK of the bull spread moves both strikes (fixed
  * width); d/dT changes the step T/N with N fixed; at k = 0, d/dk is the
- * right-hand derivative.  Method: reverse mode over the levels, root to leaves,
- * with the level functions kept at checkpoints every ceil(sqrt(N+2)) levels and
- * each segment recomputed once.  One 8-warp CTA team per option, one CTA per SM,
- * options taken from a device queue; follow-up launches with larger scratch for
- * options that outgrow a CTA's share of the pool.  Asynchronous on stream. */
+ * right-hand derivative.  Method: reverse mode over the levels, root to leaves.
+ * The forward pass keeps a record of every level step (which line each piece
+ * follows) when the option's predicted records fit its scratch; otherwise it
+ * keeps the level functions at checkpoints every ceil(sqrt(N+2)) levels and
+ * recomputes each segment once, with its records.  One 16-warp CTA team per
+ * option (OB_GREEKS_WARPS=8 for 8-warp teams), one CTA per SM, options taken
+ * from a device queue; follow-up launches with larger scratch (and checkpoints)
+ * for options that outgrow a CTA's share of the pool.  Asynchronous on stream. */
 int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double* grad,
               int32_t* status, void* stream);
 

@@ -68,12 +68,16 @@ def _load():
             lib.or_pl_eval.argtypes = [P, P, i32, d, d, P, i32, P]
             lib.or_node_step.argtypes = [P, P, i32, d, d, P, P, i32, d, d, d, d, d, d, d, i32,
                                          P, P, i32, P, P]
+            lib.or_initial_hedge.argtypes = [P, i64, P, P, i32]
+            lib.or_pl_rebalance.argtypes = [P, P, i32, d, d, d, d, d, P, P]
+            lib.or_root_objective.argtypes = [P, i32, P, i32, P]
             lib.or_alg1_tc.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_crr.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_rounds.argtypes = [i32, i32, i32, P, i32]
             for f in (lib.or_price_tc, lib.or_tc_stats, lib.or_greeks_tc, lib.or_price_crr,
                       lib.or_pl_envelope, lib.or_pl_restrict, lib.or_pl_eval, lib.or_node_step,
-                      lib.or_alg1_tc, lib.or_alg1_crr, lib.or_alg1_rounds):
+                      lib.or_alg1_tc, lib.or_alg1_crr, lib.or_alg1_rounds, lib.or_initial_hedge,
+                      lib.or_pl_rebalance, lib.or_root_objective):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -138,6 +142,30 @@ def tc_stats(opt):
     return {"nodes": int(counts[0]), "bp_seller": int(counts[1]), "bp_buyer": int(counts[2]),
             "max_seller": int(counts[3]), "max_buyer": int(counts[4]),
             "per_level_seller": per[0::2].copy(), "per_level_buyer": per[1::2].copy()}
+
+
+def initial_hedge(opts, nthreads: int = 1):
+    """The hedge at the root (Section 3's rebalancing at t = 0): out[n, 4] = (seller's stock
+    holding y*, buyer's y*, 1 if immediate exercise sets the ask, 1 if the buyer exercises at
+    once), status[n]."""
+    a = _as_table(opts)
+    n = a.shape[0]
+    out = np.empty((n, 4), np.float64)
+    st = np.empty(n, np.int32)
+    _load().or_initial_hedge(_ptr(a), n, _ptr(out), _ptr(st), _threads(nthreads))
+    return out, st
+
+
+def root_objective(opt, party: int, ys):
+    """F(y) + S0 y at the root (F = w_0/r of the seller, party 0, or the buyer, party 1): the
+    value a hedge to holding y attains."""
+    a = _as_table(opt)[:1]
+    y = np.ascontiguousarray(np.atleast_1d(ys), np.float64)
+    out = np.empty_like(y)
+    rc = _load().or_root_objective(_ptr(a), int(party), _ptr(y), len(y), _ptr(out))
+    if rc:
+        raise ValueError("oracle error %d" % rc)
+    return out
 
 
 # ---------------------------------------------------------------- Algorithm 1
@@ -212,6 +240,17 @@ def restrict(F: PL, Sa: float, Sb: float) -> PL:
     rc = _load().or_pl_restrict(_ptr(F.y), _ptr(F.f), len(F.y), F.sL, F.sR, float(Sa), float(Sb),
                                 _ptr(yo), _ptr(fo), cap, ctypes.byref(sL), ctypes.byref(sR))
     return _result(rc, yo, fo, sL, sR)
+
+
+def rebalance(F: PL, Sa, Sb, y0=0.0):
+    """The holding y' that attains inf_y' [F(y') + theta(y' - y0)] (theta: buy at Sa, sell at
+    Sb; the rightmost among equal minima) and that infimum."""
+    yo, vo = ctypes.c_double(), ctypes.c_double()
+    rc = _load().or_pl_rebalance(_ptr(F.y), _ptr(F.f), len(F.y), F.sL, F.sR, float(Sa), float(Sb),
+                                 float(y0), ctypes.byref(yo), ctypes.byref(vo))
+    if rc:
+        raise ValueError("oracle error %d" % rc)
+    return yo.value, vo.value
 
 
 def node_step(zu: PL, zd: PL, r, Sa, Sb, xi, zeta, buyer: bool) -> PL:

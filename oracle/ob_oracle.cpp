@@ -660,8 +660,9 @@ struct Stats {
   std::vector<int64_t>* per_level = nullptr;  // optional: [2*(N+2)] sums by level
 };
 
+// z1 (may be null) receives level 1's functions: seller j = 0, 1, then buyer j = 0, 1.
 template <class T>
-int price_tc(const Model<T>& m, T& ask, T& bid, Stats* st) {
+int price_tc(const Model<T>& m, T& ask, T& bid, Stats* st, PL<T>* z1 = nullptr) {
   const int N = m.N;
   std::vector<PL<T>> zs(N + 2), zb(N + 2);
   // level N+1: payoff (0, 0) for both parties; costs apply there.
@@ -697,6 +698,10 @@ int price_tc(const Model<T>& m, T& ask, T& bid, Stats* st) {
           (*st->per_level)[2 * t + 1] += mb;
         }
       }
+    }
+    if (t == 1 && z1) {
+      z1[0] = zs[0]; z1[1] = zs[1];
+      z1[2] = zb[0]; z1[3] = zb[1];
     }
   }
   ask = pl_eval(zs[0], T(0.0));
@@ -807,6 +812,57 @@ int pl_to(const PL<double>& F, double* y, double* f, int cap, double* sL, double
   *sL = F.sL;
   *sR = F.sR;
   return m;
+}
+
+// ---------------------------------------------------------------- the initial hedge
+// Section 3: a portfolio (x, y) at time t covers the seller from t+1 on iff, after
+// rebalancing the stock holding from y to some y' (buying at S^a, selling at S^b), the
+// cash left lies above w_t/r at y'; v_t(y) = inf_{y'} [F(y') + theta(y' - y)], F = w_t/r.
+// The y' that attains it is the holding the hedger moves to.  F + theta(. - y) is piecewise
+// linear with kinks at F's breakpoints and at y, so the infimum is attained at one of them
+// (the tails rise away from them when the restriction is bounded).  Among equal minima the
+// rightmost is taken.  Returns OR_ERR_UNBOUNDED when a tail falls.
+template <class T>
+int pl_rebalance(const PL<T>& F, double Sa, double Sb, double y, double& yopt, double& vopt) {
+  if (val(F.sR) + Sa < 0 || val(F.sL) + Sb > 0) return OR_ERR_UNBOUNDED;
+  std::vector<double> cand;
+  for (const T& b : F.y) cand.push_back(val(b));
+  cand.push_back(y);
+  std::sort(cand.begin(), cand.end());
+  bool have = false;
+  for (double c : cand) {
+    const double v = val(pl_eval(F, T(c))) + (c >= y ? Sa : Sb) * (c - y);
+    if (!have || v <= vopt) {
+      vopt = v;
+      yopt = c;
+      have = true;
+    }
+  }
+  return OR_OK;
+}
+
+// The hedge at the root: for the seller (p = 0) and the buyer (p = 1), the stock holding y*
+// that a hedger starting from no stock moves to at t = 0 (no costs there: theta(x) = S0 x),
+// v_0(0) = F(y*) + S0 y*, and whether immediate exercise sets the price (seller:
+// u_0(0) > v_0(0)) or is the buyer's choice (u_0(0) < v_0(0)).
+int initial_hedge(const Model<double>& m, double* out) {
+  PL<double> z1[4];
+  double ask, bid;
+  int rc = price_tc(m, ask, bid, nullptr, z1);
+  if (rc) return rc;
+  double xi, zeta;
+  payoff_at(m, m.S0, xi, zeta);
+  for (int p = 0; p < 2; ++p) {
+    PL<double> w = pl_envelope(z1[2 * p + 1], z1[2 * p], true);  // up successor j = 1
+    PL<double> f = pl_div(w, m.r);
+    double ys = 0.0, vs = 0.0;
+    rc = pl_rebalance(f, m.S0, m.S0, 0.0, ys, vs);
+    if (rc) return rc;
+    const double u0 = pl_eval(pl_expense(xi, zeta, m.S0, m.S0, p == 1), 0.0);
+    out[p] = ys;
+    out[2 + p] = (p == 0) ? (u0 > vs ? 1.0 : 0.0) : (u0 < vs ? 1.0 : 0.0);
+  }
+  return OR_OK;
 }
 
 // ---------------------------------------------------------------- Algorithm 1 (Section 4.2)
@@ -1148,6 +1204,48 @@ int or_alg1_rounds(int top, int p, int L, int32_t* out, int cap) {
     out[3 * k + 2] = r[k].p;
   }
   return (int)r.size();
+}
+
+
+// The hedge at the root of each option (initial_hedge): out[4i] = the seller's stock
+// holding after rebalancing at t = 0, out[4i+1] the buyer's, out[4i+2] = 1 when immediate
+// exercise sets the ask, out[4i+3] = 1 when the buyer exercises at once.
+int or_initial_hedge(const or_option_t* opts, int64_t n, double* out, int32_t* status, int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    const or_option_t& o = opts[i];
+    int rc = check_option(o);
+    if (rc == OR_OK) {
+      Model<double> m = make_model<double>(o, o.S0, o.K, o.sigma, o.R, o.T, o.k);
+      rc = initial_hedge(m, out + 4 * i);
+    }
+    if (rc)
+      for (int c = 0; c < 4; ++c) out[4 * i + c] = NAN;
+    if (status) status[i] = rc;
+  });
+  return OR_OK;
+}
+
+// The objective of the root's rebalancing, F(y) + S0 y with F = w_0/r of party p (0 seller,
+// 1 buyer), at ny holdings y (for checking a hedge that another minimiser of equal value
+// chose).
+int or_root_objective(const or_option_t* o, int p, const double* y, int ny, double* out) {
+  int rc = check_option(*o);
+  if (rc) return rc;
+  Model<double> m = make_model<double>(*o, o->S0, o->K, o->sigma, o->R, o->T, o->k);
+  PL<double> z1[4];
+  double ask, bid;
+  if ((rc = price_tc(m, ask, bid, nullptr, z1))) return rc;
+  const PL<double> f = pl_div(pl_envelope(z1[2 * p + 1], z1[2 * p], true), m.r);
+  for (int i = 0; i < ny; ++i) out[i] = pl_eval(f, y[i]) + m.S0 * y[i];
+  return OR_OK;
+}
+
+// The rebalancing target of pl_rebalance on an explicit PL function (for unit tests).
+int or_pl_rebalance(const double* y, const double* f, int m, double sL, double sR, double Sa,
+                    double Sb, double y0, double* yopt, double* vopt) {
+  if (m < 1) return OR_ERR_ARG;
+  PL<double> F = pl_from<double>(y, f, m, sL, sR);
+  return pl_rebalance(F, Sa, Sb, y0, *yopt, *vopt);
 }
 
 }  // extern "C"

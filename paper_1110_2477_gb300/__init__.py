@@ -29,7 +29,7 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
            "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune",
-           "ob_price_ask_bid_wide", "ob_fp64_peak", "ob_crr_american_wide")
+           "ob_price_ask_bid_wide", "ob_fp64_peak", "ob_crr_american_wide", "ob_price_ask_bid_hedge")
 
 
 class ObStats(ctypes.Structure):
@@ -62,6 +62,8 @@ def load():
             f.restype = ctypes.c_int
         lib.ob_greeks.argtypes = [P, i64, P, P, P, P]
         lib.ob_greeks.restype = ctypes.c_int
+        lib.ob_price_ask_bid_hedge.argtypes = [P, i64, P, P, P, P]
+        lib.ob_price_ask_bid_hedge.restype = ctypes.c_int
         lib.ob_price_ask_bid_host.argtypes = [P, i64, P, P]
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
         lib.ob_get_stats.argtypes = [ctypes.POINTER(ObStats)]
@@ -117,6 +119,13 @@ def to_device(table, device="cuda"):
 
 def ob_price_ask_bid(params, n, out, status=None, stream=None):
     _check(load().ob_price_ask_bid(_ptr(params), int(n), _ptr(out), _ptr(status), _stream(stream)))
+
+
+def ob_price_ask_bid_hedge(params, n, out, status, hedge, stream=None):
+    """ob_price_ask_bid plus the hedge at the root: hedge[n, 4] = (seller's stock holding after
+    rebalancing at t = 0, buyer's, immediate exercise sets the ask, buyer exercises at once)."""
+    _check(load().ob_price_ask_bid_hedge(_ptr(params), int(n), _ptr(out), _ptr(status), _ptr(hedge),
+                                         _stream(stream)))
 
 
 def ob_price_ask_bid_plain(params, n, out, status=None, stream=None):
@@ -217,6 +226,18 @@ def price(table, plain=False, stream=None, wide=False):
     f = ob_price_ask_bid_wide if wide else (ob_price_ask_bid_plain if plain else ob_price_ask_bid)
     f(dev, n, out, st, stream)
     return out, st
+
+
+def hedge(table, stream=None):
+    """ask/bid and the hedge at the root of a workloads table: (out[n,2], hedge[n,4], status[n])."""
+    import torch
+    n = int(np.asarray(table).shape[0])
+    dev = to_device(table)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev.device)
+    hg = torch.empty((n, 4), dtype=torch.float64, device=dev.device)
+    st = torch.empty(n, dtype=torch.int32, device=dev.device)
+    ob_price_ask_bid_hedge(dev, n, out, st, hg, stream)
+    return out, hg, st
 
 
 def crr(table, stream=None, wide=False):

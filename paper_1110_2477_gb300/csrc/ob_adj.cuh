@@ -19,14 +19,16 @@
 // (points that coincide with y* to within rounding are resolved by the lines' slopes).
 //
 // Levels are swept from the root (t = 0) back to the leaves (t = N+1).  The adjoint of
-// level t needs level t+1's functions, so the forward pass keeps the level functions at
-// checkpoints every s = ceil(sqrt(N+2)) levels and each segment between two checkpoints
-// is recomputed once, its levels kept, before its adjoint levels run.  An adjoint level
-// reruns passes 1-3 from level t+1 while recording, for every point of w and of z, which
-// line its piece follows (pass 2 records where each running minimum is attained); two
-// scatter loops then move the adjoints of z_t's lines onto w's lines and the node
-// constants, and those of w's lines onto level t+1's lines.  Node constants (S^a lambda,
-// S^b lambda, xi lambda of every node) are chained to the six parameters in closed form.
+// level t needs a record of the forward level step t: for every point of w its y, slope,
+// node and the successor piece it follows, for every point of z the line it follows
+// (pass 2 notes where each running minimum is attained).  When the records of all levels
+// fit the scratch, the forward pass keeps them (full mode).  Otherwise it keeps the level
+// functions at checkpoints every s = ceil(sqrt(N+2)) levels, and each segment between two
+// checkpoints is recomputed once with its records before its adjoint levels run.  An
+// adjoint level is two scatter loops: the adjoints of z_t's lines go onto w's lines and
+// the node constants, then those of w's lines onto level t+1's lines.  Node constants
+// (S^a lambda, S^b lambda, xi lambda of every node) are chained to the six parameters in
+// closed form.
 #pragma once
 #include "ob_tc.cuh"
 
@@ -73,9 +75,11 @@ struct AdjLay {
   long long ri_cap;
 };
 
-// Split an arena between the pricing arrays (cap points each), the adjoint arrays and
-// the level store.  Returns false if it does not fit.
-OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, AdjLay& A) {
+// Split an arena between the pricing arrays (cap points each), the adjoint arrays, the
+// level store and the record store (full: records of every level, and a level store for
+// the leaves and the root only).  Returns false if it does not fit.
+OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, AdjLay& A,
+                        bool full = false) {
   const size_t nodes = 2 * ((size_t)N + 2);
   const size_t node_arrays = 4 * al256(sizeof(double) * nodes) + 5 * al256(sizeof(double) * nodes) +
                              2 * al256(sizeof(int) * nodes);
@@ -119,9 +123,10 @@ OB_HD bool carve_greeks(char* base, size_t bytes, int N, int min_cap, Lay& L, Ad
   A.so = (int*)take(sizeof(int) * so_ints);
   A.so_cap = (long long)so_ints;
   // the rest: 45 % level store (checkpoints and the segment's levels, 24 bytes a point),
-  // 55 % record store (the segment's records, 16 + 12 bytes a point of w, 4 of z)
+  // 55 % record store (the segment's records, 16 + 12 bytes a point of w, 4 of z); in full
+  // mode 10 % and 90 %
   const size_t left = bytes - (size_t)(p - base) - 1024;
-  const size_t lv = (size_t)((double)left * 0.45) & ~(size_t)255;
+  const size_t lv = (size_t)((double)left * (full ? 0.10 : 0.45)) & ~(size_t)255;
   A.sd = (double*)take(lv);
   A.sd_cap = (long long)(lv / sizeof(double));
   const size_t rdb = ((left - lv) * 4 / 7) & ~(size_t)255;  // doubles: 16 of every 28 bytes
@@ -428,7 +433,7 @@ struct TcAdj {
 
   // ---------------------------------------------------------------- driver
   // Returns a status; on success lane 0's gA / gB hold d ask / d theta and d bid / d theta.
-  OB_HD int run(double& ask, double& bid, double* gA, double* gB) {
+  OB_HD int run(double& ask, double& bid, double* gA, double* gB, bool full = false) {
     const int lane = tm.lane();
     ask = bid = 0.0;
     const double dt = o.T / N;
@@ -457,28 +462,39 @@ struct TcAdj {
       tm.sync();
       if (!store_from_bank(N + 1)) return ST_CAPACITY;
     }
-    // forward, keeping checkpoints
-    for (int t = N; t >= 0; --t) {
+    // forward, keeping checkpoints (full mode: none; its one segment below is the forward)
+    for (int t = N; !full && t >= 0; --t) {
       const int b1 = (t + 1) & 1;
       R.inY = L.zY[b1]; R.inF = L.zF[b1]; R.inS = L.zS[b1]; R.inOff = L.off[b1];
       if (!level_to_bank(t)) return ST_CAPACITY;
       if (is_ckpt(t) && !store_from_bank(t)) return ST_CAPACITY;
     }
     const long long ckpt_sd = sd_top, ckpt_so = so_top;
-    // reverse sweep, one segment per checkpoint, from the root upward
+    // reverse sweep, one segment per checkpoint, from the root upward (full mode: one
+    // segment from the leaves, whose levels are not stored, only counted, but the root)
     int cur = 0;  // adjoint bank of the current level
     int lo = 0;   // lowest level whose functions the next segment must provide
     bool seeded = false;
     for (int c = 0; c <= N + 1; ++c) {
-      if (!is_ckpt(c)) continue;
+      if (full ? c != N + 1 : !is_ckpt(c)) continue;
       if (c < lo) continue;
       // recompute levels c-1 .. lo from the checkpoint c (kept in the store after the checkpoints)
       sd_top = ckpt_sd;
       so_top = ckpt_so;
       rd_top = ri_top = 0;
       for (int t = c - 1; t >= lo; --t) {
-        in_from_store(t + 1);
-        if (!level_recorded(t) || !store_from_bank(t)) return ST_CAPACITY;
+        if (full) {
+          const int b1 = (t + 1) & 1;
+          R.inY = L.zY[b1]; R.inF = L.zF[b1]; R.inS = L.zS[b1]; R.inOff = L.off[b1];
+        } else {
+          in_from_store(t + 1);
+        }
+        if (!level_recorded(t)) return ST_CAPACITY;
+        if (full && t > 0) {
+          if (lane == 0) A.ref[t] = LvRef{0, 0, L.off[t & 1][2 * (t + 1)]};  // its point count only
+        } else if (!store_from_bank(t)) {
+          return ST_CAPACITY;
+        }
       }
       if (!seeded && c > 0) {  // root: the value at y = 0 of the piece right of every point <= 0
         seeded = true;

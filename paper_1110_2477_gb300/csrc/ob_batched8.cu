@@ -4,7 +4,7 @@
 
 namespace obl {
 
-#define OB_ARGS a.opts, a.n, a.order, a.out, a.status, a.arena, a.cta_bytes, a.ctl, a.ovf_list, a.ds, a.chip_points
+#define OB_ARGS a.opts, a.n, a.order, a.out, a.status, a.arena, a.cta_bytes, a.ctl, a.ovf_list, a.ds, a.chip_points, a.hedge
 
 cudaError_t launch_batched_narrow(int nw, bool warps, bool chip, int grid, size_t smem, cudaStream_t s,
                                   const BatchedArgs& a) {

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kTeamBlock, 1) k_greeks_retry(
     const obk::Opt o = opts[oi];
     int rc;
     double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
-    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
+    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB, false);
     if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, ovf_count, ovf_list, !last);
     bt.sync();
   }

@@ -21,6 +21,7 @@ constexpr int kTier1Ctas = 16;       // CTAs of the first follow-up launch
 constexpr int kSortMax = 8192;       // largest batch ordered by cost
 constexpr int kCrrSmem = 2304;       // doubles of shared memory per CRR warp (N <= 2303)
 constexpr double kHeavyFactor = 0.0; // heavy: predicted cost > factor x (total / warps); 0: all
+constexpr double kSplitFactor = 0.04; // 16-warp CTAs: half-CTA teams below factor x (total / CTAs)
 // control words
 enum { C_HEAVY_HEAD = 0, C_LIGHT_HEAD = 1, C_NHEAVY = 2, C_T0_OVF = 3, C_T1_HEAD = 4, C_T1_OVF = 5,
        C_T2_HEAD = 6, C_T2_OVF = 7, C_WORDS = 8 };
@@ -78,6 +79,7 @@ __device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, cha
   bid = dnan();
   st.upts = st.wpts = st.zpts = 0;
   st.zmax_level = 0;
+  for (int c = 0; c < 4; ++c) st.hedge[c] = dnan();
   if (rc != obk::ST_OK) return;
   obk::Lay L;
   if (!obk::carve(slice, bytes, o.N, 2 * (o.N + 2), L)) {
@@ -94,7 +96,7 @@ __device__ __forceinline__ void price_one(const Team& tm, const obk::Opt& o, cha
 // list when a follow-up launch exists.
 __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, const obk::Stats& st,
                                        const obk::Opt& o, double* out, int* status, int* ovf_count,
-                                       int* ovf_list, bool retry, DevStats* ds) {
+                                       int* ovf_list, bool retry, DevStats* ds, double* hedge) {
   if (rc == obk::ST_CAPACITY && retry) {
     const int pos = atomicAdd(ovf_count, 1);
     ovf_list[pos] = oi;
@@ -103,6 +105,8 @@ __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, c
   }
   out[2 * oi] = rc ? dnan() : ask;
   out[2 * oi + 1] = rc ? dnan() : bid;
+  if (hedge)
+    for (int c = 0; c < 4; ++c) hedge[4 * (size_t)oi + c] = rc ? dnan() : st.hedge[c];
   if (status) status[oi] = rc;
   atomicAdd(&ds->options, 1ULL);
   if (rc == obk::ST_OK) {
@@ -118,15 +122,24 @@ __device__ __forceinline__ void finish(int oi, int rc, double ask, double bid, c
 }
 
 // Batched form.  Every CTA first takes the costliest options (order[0..nheavy))
-// one at a time as a whole-CTA team, then each of its warps takes the remaining
-// options one at a time from a second queue.  Both queues are device counters.
+// one at a time as a whole-CTA team, then the remaining options one at a time from a
+// second queue: each of its warps (WARPS), or each half of the CTA as a team of NW/2 warps
+// with its own barrier (HALVES), so that two options share the SM and one team's waits
+// at its barriers overlap the other's work.  Both queues are device counters.
 // CHIP: the CTA's dynamic shared memory holds the w arrays of chip_points points (the
 // fused level step of CTA teams, TcRun::level_fused).
-template <int NW, bool WARPS, bool CHIP = false>
+template <int NW>
+struct BatchedTbuf {  // exchange area of the CTA team, or of its two halves
+  static constexpr int whole = obk::BlockTeam<NW>::BUF, halves = 2 * obk::BlockTeam<NW / 2, true>::BUF;
+  static constexpr int value = whole > halves ? whole : halves;
+};
+
+template <int NW, bool WARPS, bool CHIP = false, bool HALVES = false>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
-    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds, int chip_points) {
-  __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
+    char* arena, size_t cta_bytes, int* ctl, int* ovf_list, DevStats* ds, int chip_points, double* hedge) {
+  static_assert(!(HALVES && (WARPS || CHIP || NW % 2)), "HALVES: even NW, no warp tail, no chip");
+  __shared__ long long tbuf[HALVES ? BatchedTbuf<NW>::value : obk::BlockTeam<NW>::BUF];
   extern __shared__ __align__(16) char chip_smem[];
   obk::BlockTeam<NW> bt{tbuf};
   const obk::WBuf chip = obk::carve_wbuf(chip_smem, chip_points);
@@ -143,8 +156,32 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     double ask, bid;
     obk::Stats st;
     price_one<obk::BlockTeam<NW>, CHIP>(bt, o, my, cta_bytes, rc, ask, bid, st, &chip);
-    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds, hedge);
     bt.sync();
+  }
+  if (HALVES) {
+    constexpr int HW = NW / 2;
+    using Half = obk::BlockTeam<HW, true>;
+    __syncthreads();  // the whole-CTA team's last exchange is read before tbuf is reused
+    const int h = threadIdx.x >= 32 * HW ? 1 : 0;
+    const Half ht{tbuf + h * Half::BUF, 32 * HW * h, 1 + h};
+    const size_t hbytes = (cta_bytes / 2) & ~(size_t)255;
+    char* hmy = my + (size_t)h * hbytes;
+    for (;;) {
+      int v = 0;
+      if (ht.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+      const int idx = ht.bcast0(v) + nh;
+      if (idx >= n) break;
+      const int oi = order[idx];
+      const obk::Opt o = opts[oi];
+      int rc;
+      double ask, bid;
+      obk::Stats st;
+      price_one(ht, o, hmy, hbytes, rc, ask, bid, st);
+      if (ht.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds, hedge);
+      ht.sync();
+    }
+    return;
   }
   if (!WARPS) return;  // every option went to a CTA team
   obk::WarpTeam wt;
@@ -161,7 +198,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     double ask, bid;
     obk::Stats st;
     price_one(wt, o, wmy, wbytes, rc, ask, bid, st);
-    if (wt.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds);
+    if (wt.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds, hedge);
     wt.sync();
   }
 }
@@ -191,20 +228,28 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // ------------------------------------------------------------------ adjoint (Greeks)
 template <class Team>
 __device__ __forceinline__ void greeks_one(const Team& tm, const obk::Opt& o, char* slice, size_t bytes,
-                                           int& rc, double& ask, double& bid, double* gA, double* gB) {
+                                           int& rc, double& ask, double& bid, double* gA, double* gB,
+                                           bool allow_full = true) {
   rc = check_option(o, true);
   ask = dnan();
   bid = dnan();
   if (rc != obk::ST_OK) return;
   obk::Lay L;
   obk::AdjLay A;
-  if (!obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A)) {
+  // full mode (records of every level, no recompute) when the predicted records fit:
+  // 2 doubles and about 2.5 ints per point of w, taken as twice the predicted breakpoints.
+  // A misprediction ends in ST_CAPACITY, and the follow-up launches (allow_full false:
+  // checkpoints, larger slices) price the option.
+  const double wpred = 2.0 * predicted_cost(o);
+  const bool full = allow_full && obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A, true) &&
+                    2.0 * wpred < (double)A.rd_cap && 2.5 * wpred < (double)A.ri_cap;
+  if (!full && !obk::carve_greeks(slice, bytes, o.N, 2 * (o.N + 2), L, A, false)) {
     rc = obk::ST_CAPACITY;
     return;
   }
   obk::TcRun<Team> R(tm, o, L);
   obk::TcAdj<Team> G(R, A);
-  rc = G.run(ask, bid, gA, gB);
+  rc = G.run(ask, bid, gA, gB, full);
 }
 
 __device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double bid, const double* gA,
@@ -279,11 +324,14 @@ struct BatchedArgs {
   int* ovf_list;
   DevStats* ds;
   int chip_points;
+  double* hedge;  // may be null: the hedge at the root, 4 doubles per option
 };
 
 // k_tc_batched<nw, warps, chip> on `grid` CTAs (ob_batched16.cu: nw 16, 12; ob_batched8.cu:
 // nw 8, 4 and the on-chip instantiations of nw 16, 8).
 cudaError_t launch_batched_wide(int nw, bool warps, int grid, cudaStream_t s, const BatchedArgs& a);
+// ob_batched_half.cu
+cudaError_t launch_batched_halves(int grid, cudaStream_t s, const BatchedArgs& a);
 cudaError_t launch_batched_narrow(int nw, bool warps, bool chip, int grid, size_t smem, cudaStream_t s,
                                   const BatchedArgs& a);
 cudaError_t set_chip_smem(int bytes16, int bytes8);
@@ -291,7 +339,7 @@ cudaError_t set_chip_smem(int bytes16, int bytes8);
 // ob_tiers.cu
 cudaError_t launch_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, int* status, char* arena,
                          size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count,
-                         int* ovf_list, int last, DevStats* ds);
+                         int* ovf_list, int last, DevStats* ds, double* hedge);
 cudaError_t launch_plain(int blocks, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
                          char* arena, size_t wbytes, int nworkers, DevStats* ds);
 

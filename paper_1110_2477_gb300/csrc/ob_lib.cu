@@ -193,6 +193,8 @@ struct GraphEntry {
   int n = 0;
   int team_warps = 0;
   int chip = 0;
+  double split = 0.0;
+  const double* hedge = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kGraphCache = 4;
@@ -215,8 +217,9 @@ struct DevPool {
   int chip_req = 0;               // on-chip w points per CTA (-1 all that fit, 0 off; OB_CHIP_POINTS)
   size_t fixed_bytes = 0;         // OB_POOL_MB: the pool has exactly this size
   double heavy_factor = kHeavyFactor;
+  double split_factor = kSplitFactor;  // 16-warp CTAs: options below it go to half-CTA teams
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
-  int greeks_warps = 8; // warps of a Greeks CTA team (8 or 16)
+  int greeks_warps = 16; // warps of a Greeks CTA team (16 or 8)
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -300,12 +303,13 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
     if (const size_t kb = env_size("OB_SM_KB", 0)) P.sm_bytes = kb << 10;  // or KiB per SM
     P.fixed_bytes = env_size("OB_POOL_MB", 0) << 20;
     if (const char* hf = getenv("OB_HEAVY_FACTOR")) P.heavy_factor = atof(hf);
+    if (const char* sf = getenv("OB_SPLIT_FACTOR")) P.split_factor = atof(sf);
     if (const char* tw = getenv("OB_TEAM_WARPS")) {
       const int v = atoi(tw);
       if (v == 4 || v == 8 || v == 12 || v == 16) P.team_warps = v;
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
-    if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 16 ? 16 : 8;
+    if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 8 ? 8 : 16;
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
     if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
@@ -412,12 +416,12 @@ size_t batched_need(const DevPool* P, int n) {
 }
 
 int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
-                    cudaStream_t s);
+                    cudaStream_t s, double* hedge = nullptr);
 int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
-                 cudaStream_t s);
+                 cudaStream_t s, double* hedge = nullptr);
 
 int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* status, void* stream,
-              bool plain) {
+              bool plain, double* hedge = nullptr) {
   if (n64 < 0 || n64 > (1 << 30)) return OB_ERR_ARG;
   if (n64 == 0) return OB_OK;
   if (!params || !out) return OB_ERR_ARG;
@@ -452,9 +456,9 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
   if ((rc = co.begin())) return rc;
   if (!P->use_graphs) {
     P->last_graph = 0;
-    rc = enqueue_batched(P, opts, n, out, status, s);
+    rc = enqueue_batched(P, opts, n, out, status, s, hedge);
   } else {
-    rc = launch_graph(P, opts, n, out, status, s);
+    rc = launch_graph(P, opts, n, out, status, s, hedge);
   }
   if (rc) return rc;
   return co.end();
@@ -463,19 +467,29 @@ int launch_tc(const ob_option_t* params, int64_t n64, double* out, int32_t* stat
 // The batched launch sequence: reset the queue words and counters, order the options
 // by predicted cost, run the persistent kernel, then the two follow-up tiers for
 // options that outgrew their scratch.  No host synchronisation, so it can be captured.
+// hedge (may be null): the hedge at the root, 4 doubles per option; the fused on-chip step
+// keeps no w_0 to read it from, so a call that asks for it runs without that step.
 int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
-                    cudaStream_t s) {
+                    cudaStream_t s, double* hedge) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(P->stats, 0, sizeof(DevStats), s)) != cudaSuccess) return cuda_fail(e);
   const int nctas = batched_ctas(P, n);
   const int* order = nullptr;
+  // with a heavy factor of 0 every option goes to a CTA team and the kernel leaves out
+  // the warp-team loop (and its registers); without the cost order, warps take them all
+  const bool warps = P->heavy_factor > 0.0 || n > kSortMax;
+  // the on-chip w arrays of the fused level step (CTA teams of 16 or 8 warps only)
+  const int chip = (warps || hedge || (P->team_warps != 16 && P->team_warps != 8)) ? 0 : chip_points(P, P->team_warps);
+  // 16-warp CTAs that split into two 8-warp teams for the options whose predicted cost is
+  // below split_factor x the mean per SM (the costliest ones keep whole CTAs)
+  const bool halves = !warps && chip == 0 && P->team_warps == 16 && P->split_factor > 0.0;
   if (n <= kSortMax) {
     int npad = 1;
     while (npad < n) npad <<= 1;
-    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order, P->ctl,
-                                                               nctas * P->team_warps, nctas,
-                                                               P->heavy_factor);
+    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(
+        opts, n, npad, P->order, P->ctl, halves ? nctas : nctas * P->team_warps, nctas,
+        halves ? P->split_factor : P->heavy_factor);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
@@ -484,24 +498,21 @@ int enqueue_batched(DevPool* P, const obk::Opt* opts, int n, double* out, int32_
   cta_bytes &= ~(size_t)255;
   int* list0 = P->lists;
   int* list1 = P->lists + P->list_cap;
-  // with a heavy factor of 0 every option goes to a CTA team and the kernel leaves out
-  // the warp-team loop (and its registers); without the cost order, warps take them all
-  const bool warps = P->heavy_factor > 0.0 || !order;
-  // the on-chip w arrays of the fused level step (CTA teams of 16 or 8 warps only)
-  const int chip = (warps || (P->team_warps != 16 && P->team_warps != 8)) ? 0 : chip_points(P, P->team_warps);
   const size_t chip_bytes = (size_t)chip * obk::WBUF_POINT_BYTES;
-const BatchedArgs ba{opts, n, order, out, status, P->arena, cta_bytes, P->ctl, list0, P->stats, chip};
-  if (chip > 0 || P->team_warps == 8 || P->team_warps == 4)
+  const BatchedArgs ba{opts, n, order, out, status, P->arena, cta_bytes, P->ctl, list0, P->stats, chip, hedge};
+  if (halves)
+    e = launch_batched_halves(nctas, s, ba);
+  else if (chip > 0 || P->team_warps == 8 || P->team_warps == 4)
     e = launch_batched_narrow(P->team_warps, warps, chip > 0, nctas, chip_bytes, s, ba);
   else
     e = launch_batched_wide(P->team_warps, warps, nctas, s, ba);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   e = launch_retry(kTier1Ctas, s, opts, out, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF], list0,
-                   &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0, P->stats);
+                   &P->ctl[C_T1_HEAD], &P->ctl[C_T1_OVF], list1, 0, P->stats, hedge);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_retry(1, s, opts, out, status, P->arena, P->arena_bytes & ~(size_t)255, &P->ctl[C_T1_OVF], list1,
-                   &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF], nullptr, 1, P->stats);
+                   &P->ctl[C_T2_HEAD], &P->ctl[C_T2_OVF], nullptr, 1, P->stats, hedge);
   if (e != cudaSuccess) return cuda_fail(e);
   P->last_tiers = kTiers + (order ? 1 : 0);
   return OB_OK;
@@ -510,12 +521,13 @@ const BatchedArgs ba{opts, n, order, out, status, P->arena, cta_bytes, P->ctl, l
 // Replay the cached graph of this call's key, or capture the sequence on the pool's
 // capture stream, instantiate it (evicting the oldest entry) and launch it on s.
 int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* status,
-                 cudaStream_t s) {
+                 cudaStream_t s, double* hedge) {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   cudaError_t e;
   for (GraphEntry& g : P->graphs) {
     if (g.exec && g.params == opts && g.n == n && g.out == out && g.status == status &&
-        g.team_warps == P->team_warps && g.chip == P->chip_req) {
+        g.team_warps == P->team_warps && g.chip == P->chip_req && g.split == P->split_factor &&
+        g.hedge == hedge) {
       if ((e = cudaGraphLaunch(g.exec, s)) != cudaSuccess) return cuda_fail(e);
       P->last_graph = 2;
       P->last_tiers = kTiers + (n <= kSortMax ? 1 : 0);
@@ -527,7 +539,7 @@ int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* 
     return cuda_fail(e);
   if ((e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return cuda_fail(e);
-  const int rc = enqueue_batched(P, opts, n, out, status, P->cap_stream);
+  const int rc = enqueue_batched(P, opts, n, out, status, P->cap_stream, hedge);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(P->cap_stream, &graph);
   if (rc || e != cudaSuccess) {
@@ -549,6 +561,8 @@ int launch_graph(DevPool* P, const obk::Opt* opts, int n, double* out, int32_t* 
   g.status = status;
   g.team_warps = P->team_warps;
   g.chip = P->chip_req;
+  g.split = P->split_factor;
+  g.hedge = hedge;
   if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(e);
   P->last_graph = 1;
   return OB_OK;
@@ -606,6 +620,12 @@ extern "C" {
 int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                      void* stream) {
   return launch_tc(params, n_options, out, status, stream, false);
+}
+
+int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
+                           double* hedge, void* stream) {
+  if (n_options > 0 && !hedge) return OB_ERR_ARG;
+  return launch_tc(params, n_options, out, status, stream, false, hedge);
 }
 
 int ob_price_ask_bid_plain(const ob_option_t* params, int64_t n_options, double* out,
@@ -1047,11 +1067,11 @@ int ob_price_ask_bid_noalloc(const ob_option_t* params, int64_t n_options, doubl
   const size_t cta_bytes = (arena_bytes / kNoAllocCtas) & ~(size_t)255;
   // every option goes to a CTA team (heavy factor 0), as in the pooled form
   {
-    const BatchedArgs ba{opts, n, order, out, status, arena, cta_bytes, ctl, list0, ds, 0};
+    const BatchedArgs ba{opts, n, order, out, status, arena, cta_bytes, ctl, list0, ds, 0, nullptr};
     if ((e = launch_batched_narrow(kNW, false, false, kNoAllocCtas, 0, s, ba)) != cudaSuccess) return cuda_fail(e);
   }
   if ((e = launch_retry(1, s, opts, out, status, arena, arena_bytes, &ctl[C_T0_OVF], list0, &ctl[C_T1_HEAD],
-                        &ctl[C_T1_OVF], list1, 1, ds)) != cudaSuccess)
+                        &ctl[C_T1_OVF], list1, 1, ds, nullptr)) != cudaSuccess)
     return cuda_fail(e);
   return OB_OK;
 }

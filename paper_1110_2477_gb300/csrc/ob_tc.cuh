@@ -50,6 +50,7 @@ struct Stats {
   long long upts;        // successor breakpoints merged (union points) over all levels
   long long wpts, zpts;  // points of w and of z summed over all levels (both parties)
   int zmax_level;        // largest number of z points in one level
+  double hedge[4];       // the hedge at the root (TcRun::root_hedge)
 };
 
 // Per-option scratch carved from one worker's arena.
@@ -666,6 +667,7 @@ struct TcRun {
     zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
     st.upts = st.wpts = st.zpts = 0;
     st.zmax_level = 0;
+    for (int c = 0; c < 4; ++c) st.hedge[c] = bitsd(0x7ff8000000000000LL);
     use_banks(N);
     if (CHIP) {
       wb = global_wbuf(L);
@@ -1057,6 +1059,31 @@ struct TcRun {
     return L.zF[0][k] + L.zS[0][k] * (0.0 - L.zY[0][k]);
   }
 
+  // The hedge at the root (Section 3: rebalancing at t = 0, where S^a = S^b = S0).  For the
+  // seller's node (0) and the buyer's (1) of level 0, the point of w_0 where
+  // g = w_0 + S0 lambda_0 y is least (the rightmost among equal keys): the stock holding a
+  // hedger with no stock moves to, attaining v_0(0) = min g; and whether immediate
+  // exercise sets the ask (u_0(0) > v_0(0)) or is the buyer's choice (u_0(0) < v_0(0)).
+  // Needs w_0, its g keys and wtot of level 0 in the arrays the passes used.
+  OB_HD void root_hedge(int wtot) {
+    const double* nt = L.nt[0];
+    const double uS = nt[2] + (double)zeta * nt[0];  // seller's u_0(0) lambda_0: xi + zeta S0
+    for (int p = 0; p < 2; ++p) {
+      long long cv = KMAXLL;
+      int ci = -1;
+      for (int base = 0; base < wtot; base += Team::W) {
+        const int i = base + tm.lane();
+        const bool ok = i < wtot && wN()[i] == p;
+        long long gk = ok ? wGK()[i] : KMAXLL;
+        int ix = ok ? i : -1;
+        tm.seg_argmin(gk, ix, false, cv, ci);
+      }
+      const long long ku = okey(p == 0 ? uS : -uS);
+      st.hedge[p] = ci >= 0 ? wY()[ci] : bitsd(0x7ff8000000000000LL);
+      st.hedge[2 + p] = (p == 0 ? ku > cv : ku < cv) ? 1.0 : 0.0;
+    }
+  }
+
   // Full induction for one option; returns a status code, writes ask and bid.
   OB_HD int run(double& ask, double& bid) {
     const int lane = tm.lane();
@@ -1085,11 +1112,13 @@ struct TcRun {
       tm.sync();
     }
     if (2 * (N + 2) > L.capZ) return ST_CAPACITY;
+    int wtot = 0;
     for (int t = N; t >= 0; --t) {
       use_banks(t);
       node_table(t);
       tm.sync();
-      int wtot = 0, ztot = 0, utot = 0;
+      int ztot = 0, utot = 0;
+      wtot = 0;
       if constexpr (CHIP) {
         if (!level_fused(t, utot, wtot, ztot)) return ST_CAPACITY;
       } else {
@@ -1102,6 +1131,7 @@ struct TcRun {
       st.zpts += ztot;
       if (ztot > st.zmax_level) st.zmax_level = ztot;
     }
+    if constexpr (!CHIP) root_hedge(wtot);  // the fused step keeps w_0 in its chunk arrays
     const double lam0 = L.lam[0];
     ask = root_value(0) / lam0;
     bid = -root_value(1) / lam0;

@@ -187,52 +187,73 @@ __device__ __forceinline__ long long from_ll<long long>(long long v) { return v;
 template <>
 __device__ __forceinline__ double from_ll<double>(long long v) { return __longlong_as_double(v); }
 
-// All threads of one CTA (NW warps, W = 32 NW lanes) working on one option.
+// Barrier b (1..15) for the n threads of a sub-team of a CTA, and its reductions.
+__device__ __forceinline__ void bar_sync(int b, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ int bar_popc(int b, int n, bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\tbar.red.popc.u32 %0, %2, %3, q;\n\t}"
+      : "=r"(r)
+      : "r"(p ? 1 : 0), "r"(b), "r"(n)
+      : "memory");
+  return r;
+}
+
+// The threads of one CTA (NW warps, W = 32 NW lanes) working on one option; SUB: the
+// team is the W threads from thread `base` on, one of several teams of the CTA, and
+// meets at barrier `bar` instead of the CTA's.
 // Exchanges go through shared memory, two halves used alternately, so that one
 // barrier per exchange suffices: a half is rewritten only after the next
 // exchange's barrier, which every thread reaches after its reads of that half.
-template <int NW>
+template <int NW, bool SUB = false>
 struct BlockTeam {
   static constexpr int W = 32 * NW;
   static constexpr int HALF = W + 4 * NW + 8;
   static constexpr int BUF = 2 * HALF;
   long long* buf;
+  int base = 0;  // SUB: first thread of the team
+  int bar = 0;   // SUB: its barrier
   mutable int par = 0;
   __device__ __forceinline__ long long* half() const {
     long long* h = buf + par * HALF;
     par ^= 1;
     return h;
   }
-  __device__ __forceinline__ int lane() const { return threadIdx.x; }
-  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ int lane() const { return SUB ? (int)threadIdx.x - base : (int)threadIdx.x; }
+  __device__ __forceinline__ void sync() const {
+    if (SUB) bar_sync(bar, W);
+    else __syncthreads();
+  }
   template <class T>
   __device__ __forceinline__ T bcast0(T v) const {
     long long* h = half();
-    if (threadIdx.x == 0) h[0] = to_ll(v);
-    __syncthreads();
+    if (lane() == 0) h[0] = to_ll(v);
+    sync();
     return from_ll<T>(h[0]);
   }
   template <class T>
   __device__ __forceinline__ T prev(T v, T carry) const {
     long long* h = half();
-    h[threadIdx.x] = to_ll(v);
-    __syncthreads();
-    return threadIdx.x ? from_ll<T>(h[threadIdx.x - 1]) : carry;
+    h[lane()] = to_ll(v);
+    sync();
+    return lane() ? from_ll<T>(h[lane() - 1]) : carry;
   }
   template <class T>
   __device__ __forceinline__ T prev_last(T v, T carry, T& last) const {
     long long* h = half();
-    h[threadIdx.x] = to_ll(v);
-    __syncthreads();
+    h[lane()] = to_ll(v);
+    sync();
     last = from_ll<T>(h[W - 1]);
-    return threadIdx.x ? from_ll<T>(h[threadIdx.x - 1]) : carry;
+    return lane() ? from_ll<T>(h[lane() - 1]) : carry;
   }
   template <class T>
   __device__ __forceinline__ void look2(T v, T c1, T c2, T& m1, T& m2, T& l1, T& l2) const {
     long long* h = half();
-    const int l = threadIdx.x;
+    const int l = lane();
     h[l] = to_ll(v);
-    __syncthreads();
+    sync();
     m1 = (l >= 1) ? from_ll<T>(h[l - 1]) : c1;
     m2 = (l >= 2) ? from_ll<T>(h[l - 2]) : (l == 1 ? c1 : c2);
     l1 = from_ll<T>(h[W - 1]);
@@ -245,8 +266,8 @@ struct BlockTeam {
   }
   __device__ __forceinline__ void count_le2(int v, int q1, int q2, int& c1, int& c2) const {
     long long* h = half();
-    h[threadIdx.x] = v;
-    __syncthreads();
+    h[lane()] = v;
+    sync();
     // first slots with value > q1 and > q2: both searches advance together over the
     // next power of two P >= W (slots past W read as +infinity)
     constexpr int P = pow2_ceil(W);
@@ -263,18 +284,18 @@ struct BlockTeam {
     c1 = lo1;
     c2 = lo2;
   }
-  __device__ __forceinline__ int count(bool p) const { return __syncthreads_count(p ? 1 : 0); }
-  __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p ? 1 : 0) != 0; }
+  __device__ __forceinline__ int count(bool p) const { return (SUB ? bar_popc(bar, W, p) : __syncthreads_count(p ? 1 : 0)); }
+  __device__ __forceinline__ bool any(bool p) const { return (SUB ? bar_popc(bar, W, p) : __syncthreads_or(p ? 1 : 0)) != 0; }
   __device__ __forceinline__ int excl_sum(int v, int& total) const {
     long long* h = half();
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = lane() & 31, w = lane() >> 5;
     int x = v;
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, d);
       if (l >= d) x += y;
     }
     if (l == 31) h[W + w] = x;
-    __syncthreads();
+    sync();
     // across warps: lane k of every warp takes warp k's total and the warp scans them with
     // shuffles; warp w's offset is the inclusive sum of warps 0..w-1
     int c = (l < NW) ? (int)h[W + l] : 0;
@@ -288,7 +309,7 @@ struct BlockTeam {
   }
   __device__ __forceinline__ long long seg_min(long long v, bool head, long long& carry) const {
     long long* h = half();
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = lane() & 31, w = lane() >> 5;
     int fl = head ? 1 : 0;
     for (int d = 1; d < 32; d <<= 1) {
       const long long vu = __shfl_up_sync(0xffffffffu, v, d);
@@ -302,7 +323,7 @@ struct BlockTeam {
       h[W + 2 * w] = v;
       h[W + 2 * w + 1] = fl;
     }
-    __syncthreads();
+    sync();
     // across warps: lane k of every warp takes warp k's record and the warp runs the
     // segmented scan over lanes 0..NW-1 with shuffles; acc_k = head in warp k ? its value :
     // min(acc_{k-1}, its value), acc_{-1} = carry
@@ -329,7 +350,7 @@ struct BlockTeam {
   __device__ __forceinline__ void seg_argmin(long long& v, int& ix, bool head, long long& cv,
                                              int& ci) const {
     long long* h = half();
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int l = lane() & 31, w = lane() >> 5;
     int fl = head ? 1 : 0;
     for (int d = 1; d < 32; d <<= 1) {
       const long long vu = __shfl_up_sync(0xffffffffu, v, d);
@@ -345,7 +366,7 @@ struct BlockTeam {
       h[W + 3 * w + 1] = ix;
       h[W + 3 * w + 2] = fl;
     }
-    __syncthreads();
+    sync();
     // across warps as in seg_min, carrying the index; among equal minima the latest wins
     long long rv = KMAXLL;
     int ri = 0, rf = 0;
@@ -374,8 +395,8 @@ struct BlockTeam {
   __device__ __forceinline__ double sum(double v) const {
     long long* h = half();
     for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if ((threadIdx.x & 31) == 0) h[W + (threadIdx.x >> 5)] = __double_as_longlong(v);
-    __syncthreads();
+    if ((lane() & 31) == 0) h[W + (lane() >> 5)] = __double_as_longlong(v);
+    sync();
     double t = 0.0;
     for (int k = 0; k < NW; ++k) t += __longlong_as_double(h[W + k]);
     return t;

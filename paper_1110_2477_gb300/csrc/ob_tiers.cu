@@ -9,7 +9,7 @@ namespace obl {
 __global__ void __launch_bounds__(kTeamBlock, 2) k_tc_retry(
     const obk::Opt* __restrict__ opts, double* out, int* status, char* arena, size_t cta_bytes,
     const int* in_count, const int* in_list, int* head, int* ovf_count, int* ovf_list, int last,
-    DevStats* ds) {
+    DevStats* ds, double* hedge) {
   __shared__ long long tbuf[obk::BlockTeam<kNW>::BUF];
   obk::BlockTeam<kNW> bt{tbuf};
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kTeamBlock, 2) k_tc_retry(
     double ask, bid;
     obk::Stats st;
     price_one(bt, o, my, cta_bytes, rc, ask, bid, st);
-    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, ovf_count, ovf_list, !last, ds);
+    if (threadIdx.x == 0) finish(oi, rc, ask, bid, st, o, out, status, ovf_count, ovf_list, !last, ds, hedge);
     bt.sync();
   }
 }
@@ -44,16 +44,16 @@ __global__ void __launch_bounds__(kBlock) k_tc_plain(const obk::Opt* __restrict_
     double ask, bid;
     obk::Stats st;
     price_one(tm, o, my, wbytes, rc, ask, bid, st);
-    if (tm.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, nullptr, nullptr, false, ds);
+    if (tm.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, nullptr, nullptr, false, ds, nullptr);
     tm.sync();
   }
 }
 
 cudaError_t launch_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, int* status, char* arena,
                          size_t cta_bytes, const int* in_count, const int* in_list, int* head, int* ovf_count,
-                         int* ovf_list, int last, DevStats* ds) {
+                         int* ovf_list, int last, DevStats* ds, double* hedge) {
   k_tc_retry<<<grid, kTeamBlock, 0, s>>>(opts, out, status, arena, cta_bytes, in_count, in_list, head, ovf_count,
-                                         ovf_list, last, ds);
+                                         ovf_list, last, ds, hedge);
   return cudaGetLastError();
 }
 

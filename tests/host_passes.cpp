@@ -112,13 +112,16 @@ extern "C" int hp_price_split(const obk::Opt* o, int G, double* out, long long* 
   return rc;
 }
 
-extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad) {
+// full = 1: the records of every level kept by the forward pass; 0: checkpoints and a
+// recomputed segment per checkpoint
+extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad, int full) {
   const size_t bytes = 512ull << 20;
   OneLane tm;
   obk::Lay L;
   obk::AdjLay A;
-  if (!obk::carve_greeks(arena(bytes), bytes, o->N, 2 * (o->N + 2), L, A)) return obk::ST_CAPACITY;
+  if (!obk::carve_greeks(arena(bytes), bytes, o->N, 2 * (o->N + 2), L, A, full != 0))
+    return obk::ST_CAPACITY;
   obk::TcRun<OneLane> R(tm, *o, L);
   obk::TcAdj<OneLane> G(R, A);
-  return G.run(out[0], out[1], grad, grad + obk::NPAR);
+  return G.run(out[0], out[1], grad, grad + obk::NPAR, full != 0);
 }

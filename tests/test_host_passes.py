@@ -102,16 +102,23 @@ def test_fused_level_step_is_bitwise_equal(cap):
 def test_host_adjoint_matches_oracle_gradient(payoff):
     """The adjoint (line adjoints per piece) against the oracle's gradient on 40 options of
     one payoff, N in [2, 160]: exercise branches in the left tails, running minima at the
-    ends of their range, and the crossings of nearly parallel pieces of calls and spreads."""
+    ends of their range, and the crossings of nearly parallel pieces of calls and spreads.
+    Both modes: records of every level kept by the forward pass (full), and checkpoints
+    with a recomputed segment each; they give the same bits."""
     t = W.random_table(40, 31500 + payoff, N_lo=2, N_hi=160, payoffs=(payoff,))
     t["k"] = np.maximum(t["k"], 1e-4)
     rout, rgrad, rst = oracle.greeks(t, nthreads=8)
     P = ctypes.c_void_p
     for i in range(len(t)):
         a = _rec(t[i])
-        out = np.zeros(2)
-        grad = np.zeros(12)
-        rc = _lib().hp_greeks(a.ctypes.data_as(P), out.ctypes.data_as(P), grad.ctypes.data_as(P))
-        assert rc == rst[i] == 0
-        scale = np.maximum(np.abs(rgrad[i].reshape(-1)), 1e-3 * t["K"][i])
-        assert np.all(np.abs(grad - rgrad[i].reshape(-1)) <= 1e-6 * scale), (i, grad, rgrad[i])
+        res = []
+        for full in (1, 0):
+            out = np.zeros(2)
+            grad = np.zeros(12)
+            rc = _lib().hp_greeks(a.ctypes.data_as(P), out.ctypes.data_as(P), grad.ctypes.data_as(P),
+                                  full)
+            assert rc == rst[i] == 0
+            scale = np.maximum(np.abs(rgrad[i].reshape(-1)), 1e-3 * t["K"][i])
+            assert np.all(np.abs(grad - rgrad[i].reshape(-1)) <= 1e-6 * scale), (i, full, grad, rgrad[i])
+            res.append(np.concatenate([out, grad]))
+        assert np.array_equal(res[0].view(np.int64), res[1].view(np.int64)), i
