@@ -44,7 +44,8 @@ CPU_SAMPLE = 48          # options of the batch the CPU oracle prices per step
 # recorded with the hash of the kernel's sources; reported only while the sources match
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_tc_batched_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1110_2477_gb300", "csrc", f)
-                  for f in ("ob_tc.cuh", "ob_team.cuh", "ob_kern.cuh", "ob_batched16.cu")]
+                  for f in ("ob_tc.cuh", "ob_team.cuh", "ob_kern.cuh", "ob_batched16.cu",
+                            "ob_batched_half.cu", "ob_lib.cu")]
 
 
 def kernel_source_hash():
@@ -145,6 +146,18 @@ def max_over_ranks(x, world):
     dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    """The sum of x over the ranks (units that all ranks processed)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -607,7 +620,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     job_s = max_over_ranks(dev_s, world)
-    value = world * nodes_per_step * args.steps / job_s
+    job_nodes = sum_over_ranks(nodes_per_step, world)  # each rank prices its own batch
+    value = job_nodes * args.steps / job_s
 
     # end to end through the host-buffer call: copies of inputs and results inside
     pin_in = torch.from_numpy(table.view(np.uint8).reshape(-1).copy()).pin_memory()
@@ -620,7 +634,7 @@ def main():
     for _ in range(args.steps):
         ob.ob_price_ask_bid_host(pin_in_np, pin_out.numpy(), pin_st.numpy())
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * nodes_per_step * args.steps / e2e_s, "unit": "node updates/s",
+    e2e = {"value": job_nodes * args.steps / e2e_s, "unit": "node updates/s",
            "h2d_bytes_per_step": int(table.nbytes),
            "d2h_bytes_per_step": int(pin_out.numel() * 8 + pin_st.numel() * 4)}
 

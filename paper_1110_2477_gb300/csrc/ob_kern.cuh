@@ -134,6 +134,36 @@ struct BatchedTbuf {  // exchange area of the CTA team, or of its two halves
   static constexpr int value = whole > halves ? whole : halves;
 };
 
+// The second phase of the HALVES form: the CTA as two teams of NW/2 warps, each with its
+// own barrier and half the CTA's scratch, taking options from the light queue.  Not
+// inlined: the kernel's first phase keeps its own register allocation.
+template <int NW>
+__device__ __noinline__ void batched_halves(const obk::Opt* __restrict__ opts, int n,
+                                            const int* __restrict__ order, double* out, int* status,
+                                            char* my, size_t cta_bytes, int* ctl, int* ovf_list,
+                                            DevStats* ds, double* hedge, long long* tbuf, int nh) {
+  constexpr int HW = NW / 2;
+  using Half = obk::BlockTeam<HW, true>;
+  const int h = threadIdx.x >= 32 * HW ? 1 : 0;
+  const Half ht{tbuf + h * Half::BUF, 32 * HW * h, 1 + h};
+  const size_t hbytes = (cta_bytes / 2) & ~(size_t)255;
+  char* hmy = my + (size_t)h * hbytes;
+  for (;;) {
+    int v = 0;
+    if (ht.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
+    const int idx = ht.bcast0(v) + nh;
+    if (idx >= n) break;
+    const int oi = order[idx];
+    const obk::Opt o = opts[oi];
+    int rc;
+    double ask, bid;
+    obk::Stats st;
+    price_one(ht, o, hmy, hbytes, rc, ask, bid, st);
+    if (ht.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds, hedge);
+    ht.sync();
+  }
+}
+
 template <int NW, bool WARPS, bool CHIP = false, bool HALVES = false>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     const obk::Opt* __restrict__ opts, int n, const int* __restrict__ order, double* out, int* status,
@@ -160,27 +190,8 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
     bt.sync();
   }
   if (HALVES) {
-    constexpr int HW = NW / 2;
-    using Half = obk::BlockTeam<HW, true>;
     __syncthreads();  // the whole-CTA team's last exchange is read before tbuf is reused
-    const int h = threadIdx.x >= 32 * HW ? 1 : 0;
-    const Half ht{tbuf + h * Half::BUF, 32 * HW * h, 1 + h};
-    const size_t hbytes = (cta_bytes / 2) & ~(size_t)255;
-    char* hmy = my + (size_t)h * hbytes;
-    for (;;) {
-      int v = 0;
-      if (ht.lane() == 0) v = atomicAdd(&ctl[C_LIGHT_HEAD], 1);
-      const int idx = ht.bcast0(v) + nh;
-      if (idx >= n) break;
-      const int oi = order[idx];
-      const obk::Opt o = opts[oi];
-      int rc;
-      double ask, bid;
-      obk::Stats st;
-      price_one(ht, o, hmy, hbytes, rc, ask, bid, st);
-      if (ht.lane() == 0) finish(oi, rc, ask, bid, st, o, out, status, &ctl[C_T0_OVF], ovf_list, true, ds, hedge);
-      ht.sync();
-    }
+    batched_halves<NW>(opts, n, order, out, status, my, cta_bytes, ctl, ovf_list, ds, hedge, tbuf, nh);
     return;
   }
   if (!WARPS) return;  // every option went to a CTA team

@@ -425,3 +425,26 @@ def test_crr_wide_appendix_put_large_n():
     assert np.all(s == 0)
     assert np.all(np.abs(g - ref) <= RTOL * ref)
     assert [round(float(x), 3) for x in g] == [13.906, 13.906]
+
+
+def test_wide_with_costs_at_n_10000_and_20000():
+    """Single options with costs beyond the paper's sizes on the whole GPU (N = 10000 and
+    20000): every status is OK, and the prices keep Section 5's ordering (bid <= the CRR
+    price <= ask, the ask rising and the bid falling with k, equal at k = 0)."""
+    recs = []
+    for N in (10000, 20000):
+        for k in (0.0, 0.0025, 0.005):
+            recs.append(W.make(k=k, N=N))
+        recs.append(W.make(K=95.0, K2=105.0, k=0.0025, N=N, payoff=W.SPREAD))
+    t = W.concat(*recs)
+    out, st = _ob().price(t, wide=True)
+    crr, cst = _ob().crr(t)
+    out, st, crr = out.cpu().numpy(), st.cpu().numpy(), crr.cpu().numpy()
+    assert np.all(st == 0) and np.all(cst.cpu().numpy() == 0)
+    for b in (0, 4):
+        p0, p1, p2 = out[b], out[b + 1], out[b + 2]
+        assert abs(p0[0] - p0[1]) <= 1e-9 * p0[0] and abs(p0[0] - crr[b]) <= 1e-9 * crr[b]
+        assert p2[1] <= p1[1] <= crr[b + 1] <= p1[0] <= p2[0]
+        assert p1[0] > p0[0] and p1[1] < p0[1]
+        sp = out[b + 3]
+        assert sp[1] <= crr[b + 3] <= sp[0] and 0.0 <= sp[1] and sp[0] <= 10.0
