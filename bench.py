@@ -593,7 +593,8 @@ def main():
     tuned = None
     if not args.no_autotune:
         tw, chip, tms = ob.ob_autotune(params, n, min(n, 1024), stream)
-        tuned = {"team_warps": tw, "chip_points": chip, "sample": min(n, 1024),
+        tuned = {"team_warps": tw, "chip_points": chip, "half_teams": ob.ob_get_stats()["half_teams"],
+                 "sample": min(n, 1024),
                  "sample_ms": {str(k): round(v, 2) for k, v in tms.items()}}
     for _ in range(args.warmup):
         ob.ob_price_ask_bid(params, n, out, st, stream)
@@ -695,6 +696,7 @@ def main():
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": "replicas (one batch per GPU)",
                    "team_warps": stats["team_warps"], "chip_points": stats["chip_points"],
+                   "half_teams": stats["half_teams"],
                    "autotune": tuned,
                    "launch": "CUDA graph replay" if stats["graph"] == 2 else
                              ("CUDA graph" if stats["graph"] == 1 else "direct")},

@@ -229,6 +229,8 @@ typedef struct {
   int32_t team_warps;     /* warps per CTA team of the batched form */
   int32_t chip_points;    /* batched form: points of w each CTA team keeps in shared memory
                              (the fused level step; 0: w in the global scratch) */
+  int32_t half_teams;     /* batched form: 1 when 16-warp CTAs split into two 8-warp teams for
+                             the light options (OB_SPLIT_FACTOR > 0 and no fused step), else 0 */
 } ob_stats_t;
 int ob_get_stats(ob_stats_t* host_out);
 
@@ -250,16 +252,19 @@ int ob_get_stats(ob_stats_t* host_out);
  * Drops the cached graphs.  Returns OB_ERR_ARG for another team width. */
 int ob_configure(int32_t team_warps, int32_t use_graphs, int32_t chip_points);
 
-/* Autotuner of the batched form: times six configurations -- team widths 16, 12, 8, 4
- * warps (hence the CTA size, the registers per thread and the per-CTA breakpoint
- * capacity) with w in the global scratch, then the fused level step with w on chip
- * (all the shared memory a CTA can take) for 16 and 8 warps -- on a sample of the given
+/* Autotuner of the batched form: times seven configurations -- 16-warp teams that split
+ * into two 8-warp teams for the light options, 16-warp teams throughout, team widths 12,
+ * 8, 4 warps (hence the CTA size, the registers per thread and the per-CTA breakpoint
+ * capacity) with w in the global scratch, then the fused level step with w on chip (all
+ * the shared memory a CTA can take) for 16 and 8 warps -- on a sample of the given
  * options (every (n_options / sample)-th option; sample <= 0 or >= n_options: all of
  * them), one warm-up run and one timed run each, with CUDA events on stream, and keeps
- * the fastest for later calls.  Synchronous.  params is a DEVICE pointer as in
+ * the fastest for later calls (a candidate replaces an earlier one only when it is more
+ * than 1 % faster).  Synchronous.  params is a DEVICE pointer as in
  * ob_price_ask_bid.  team_warps_out and chip_out (HOST, may be NULL) receive the
- * choice (chip_out: on-chip points per CTA, 0 for none); ms_out (HOST, 6 floats, may
- * be NULL) the timed milliseconds in the order above. */
+ * choice (chip_out: on-chip points per CTA, 0 for none; ob_stats_t.half_teams tells the
+ * first two apart); ms_out (HOST, 7 floats, may be NULL) the timed milliseconds in the
+ * order above. */
 int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, void* stream,
                 int32_t* team_warps_out, int32_t* chip_out, float* ms_out);
 

@@ -39,7 +39,7 @@ class ObStats(ctypes.Structure):
                 ("max_level_points", ctypes.c_int32), ("retried", ctypes.c_int32),
                 ("failed", ctypes.c_int32), ("tiers", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("team_warps", ctypes.c_int32),
-                ("chip_points", ctypes.c_int32)]
+                ("chip_points", ctypes.c_int32), ("half_teams", ctypes.c_int32)]
 
 
 class ObError(RuntimeError):
@@ -194,12 +194,13 @@ def ob_configure(team_warps=0, use_graphs=-1, chip_points=-2):
     _check(load().ob_configure(int(team_warps), int(use_graphs), int(chip_points)))
 
 
-TUNE_CANDIDATES = ("16", "12", "8", "4", "16+chip", "8+chip")
+TUNE_CANDIDATES = ("16", "16-whole", "12", "8", "4", "16+chip", "8+chip")
 
 
 def ob_autotune(params, n, sample=0, stream=None):
-    """Time the six configurations of TUNE_CANDIDATES on a sample of the device records and
-    keep the fastest.  Returns (team_warps, chip_points, {candidate: ms})."""
+    """Time the seven configurations of TUNE_CANDIDATES on a sample of the device records and
+    keep the fastest ("16": 16-warp teams that split into two 8-warp teams for the light
+    options; "16-whole": no split).  Returns (team_warps, chip_points, {candidate: ms})."""
     tw = ctypes.c_int32(0)
     chip = ctypes.c_int32(0)
     ms = (ctypes.c_float * len(TUNE_CANDIDATES))()

@@ -4,14 +4,14 @@
 namespace obl {
 
 cudaError_t launch_greeks_team8(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
-                                int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list) {
-  k_greeks_team<8><<<grid, 256, 0, s>>>(opts, n, out, grad, status, arena, cta_bytes, ctl, ovf_list);
+                                int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list, int allow_full) {
+  k_greeks_team<8><<<grid, 256, 0, s>>>(opts, n, out, grad, status, arena, cta_bytes, ctl, ovf_list, allow_full);
   return cudaGetLastError();
 }
 
 cudaError_t launch_greeks_team16(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
-                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list) {
-  k_greeks_team<16><<<grid, 512, 0, s>>>(opts, n, out, grad, status, arena, cta_bytes, ctl, ovf_list);
+                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list, int allow_full) {
+  k_greeks_team<16><<<grid, 512, 0, s>>>(opts, n, out, grad, status, arena, cta_bytes, ctl, ovf_list, allow_full);
   return cudaGetLastError();
 }
 

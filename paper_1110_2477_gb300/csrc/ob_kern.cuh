@@ -284,7 +284,7 @@ __device__ __forceinline__ void greeks_finish(int oi, int rc, double ask, double
 template <int NW>
 __global__ void __launch_bounds__(32 * NW, NW >= 16 ? 1 : 8 / NW) k_greeks_team(
     const obk::Opt* __restrict__ opts, int n, double* out, double* grad, int* status, char* arena,
-    size_t cta_bytes, int* ctl, int* ovf_list) {
+    size_t cta_bytes, int* ctl, int* ovf_list, int allow_full) {
   __shared__ long long tbuf[obk::BlockTeam<NW>::BUF];
   obk::BlockTeam<NW> bt{tbuf};
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(32 * NW, NW >= 16 ? 1 : 8 / NW) k_greeks_team(
     const obk::Opt o = opts[oi];
     int rc;
     double ask, bid, gA[obk::NPAR], gB[obk::NPAR];
-    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB);
+    greeks_one(bt, o, my, cta_bytes, rc, ask, bid, gA, gB, allow_full != 0);
     if (threadIdx.x == 0) greeks_finish(oi, rc, ask, bid, gA, gB, out, grad, status, &ctl[C_T0_OVF], ovf_list, true);
     bt.sync();
   }
@@ -365,9 +365,9 @@ cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, dou
 
 // ob_greeks8.cu (8- and 16-warp CTA teams) and ob_greeks.cu (the follow-up launches)
 cudaError_t launch_greeks_team8(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
-                                int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list);
+                                int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list, int allow_full);
 cudaError_t launch_greeks_team16(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,
-                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list);
+                                 int* status, char* arena, size_t cta_bytes, int* ctl, int* ovf_list, int allow_full);
 cudaError_t launch_greeks_retry(int grid, cudaStream_t s, const obk::Opt* opts, double* out, double* grad,
                                 int* status, char* arena, size_t cta_bytes, const int* in_count,
                                 const int* in_list, int* head, int* ovf_count, int* ovf_list, int last);

@@ -198,7 +198,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kGraphCache = 4;
-constexpr int kTuneCands = 6;  // configurations the autotuner times
+constexpr int kTuneCands = 7;  // configurations the autotuner times
 
 // Scratch budgets.  The pool is one device allocation that grows to the largest
 // need of any call so far (never shrinks before ob_release); OB_POOL_MB fixes its size.
@@ -220,6 +220,7 @@ struct DevPool {
   double split_factor = kSplitFactor;  // 16-warp CTAs: options below it go to half-CTA teams
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
   int greeks_warps = 16; // warps of a Greeks CTA team (16 or 8)
+  int greeks_full = 1;   // records of every level when they fit (OB_GREEKS_FULL=0: checkpoints only)
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -310,6 +311,7 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
     }
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
     if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 8 ? 8 : 16;
+    if (const char* g = getenv("OB_GREEKS_FULL")) P.greeks_full = atoi(g) != 0;
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
     if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
@@ -778,8 +780,10 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   if (wbytes > kGreeksSmBytes / per_sm) wbytes = kGreeksSmBytes / per_sm;
   wbytes &= ~(size_t)255;
   e = P->greeks_warps == 16
-          ? launch_greeks_team16(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0)
-          : launch_greeks_team8(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0);
+          ? launch_greeks_team16(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0,
+                                 P->greeks_full)
+          : launch_greeks_team8(workers, s, opts, n, out, grad, status, P->arena, wbytes, P->ctl, list0,
+                                P->greeks_full);
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t t1_bytes = (P->arena_bytes / kTier1Ctas) & ~(size_t)255;
   e = launch_greeks_retry(kTier1Ctas, s, opts, out, grad, status, P->arena, t1_bytes, &P->ctl[C_T0_OVF], list0,
@@ -858,6 +862,7 @@ int ob_get_stats(ob_stats_t* host_out) {
   host_out->graph = P->last_graph;
   host_out->team_warps = P->team_warps;
   host_out->chip_points = (P->team_warps == 16 || P->team_warps == 8) ? chip_points(P, P->team_warps) : 0;
+  host_out->half_teams = (P->team_warps == 16 && P->split_factor > 0.0 && host_out->chip_points == 0) ? 1 : 0;
   return OB_OK;
 }
 
@@ -921,15 +926,20 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     if (a) cudaEventDestroy(a);
     return cuda_fail(e);
   }
-  // candidates: team width, and on-chip w points per CTA (0: w in the global scratch;
-  // -1: the fused level step with all the shared memory a CTA can take)
-  const int cands[kTuneCands][2] = {{16, 0}, {12, 0}, {8, 0}, {4, 0}, {16, -1}, {8, -1}};
+  // candidates: team width, on-chip w points per CTA (0: w in the global scratch; -1: the
+  // fused level step with all the shared memory a CTA can take), and whether 16-warp CTAs
+  // split into two 8-warp teams for the light options
+  const int cands[kTuneCands][3] = {{16, 0, 1}, {16, 0, 0}, {12, 0, 0}, {8, 0, 0}, {4, 0, 0}, {16, -1, 0}, {8, -1, 0}};
   const int keep_chip = P->chip_req;
+  const double keep_split = P->split_factor;
+  const double split_on = keep_split > 0.0 ? keep_split : kSplitFactor;
   int best = keep, best_chip = keep_chip;
+  double best_split = keep_split;
   float best_ms = 0.0f;
   for (int c = 0; c < kTuneCands && rc == OB_OK; ++c) {
     P->team_warps = cands[c][0];
     P->chip_req = cands[c][1];
+    P->split_factor = cands[c][2] ? split_on : 0.0;
     float ms = 0.0f;
     for (int rep = 0; rep < 2 && rc == OB_OK; ++rep) {  // one warm-up run, one timed run
       if ((e = cudaEventRecord(a, s)) != cudaSuccess) { rc = cuda_fail(e); break; }
@@ -943,12 +953,20 @@ int ob_autotune(const ob_option_t* params, int64_t n_options, int64_t sample, vo
     }
     if (rc) break;
     if (ms_out) ms_out[c] = ms;
-    if (c == 0 || ms < best_ms) { best_ms = ms; best = cands[c][0]; best_chip = cands[c][1]; }
+    // a later candidate must beat the best so far by 1 %: the sample's timings are close for
+    // the first two, and a timing's noise should not move the choice
+    if (c == 0 || ms < 0.99f * best_ms) {
+      best_ms = ms;
+      best = cands[c][0];
+      best_chip = cands[c][1];
+      best_split = P->split_factor;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   P->team_warps = rc ? keep : best;
   P->chip_req = rc ? keep_chip : best_chip;
+  P->split_factor = rc ? keep_split : best_split;
   drop_graphs(P);
   if (team_warps_out) *team_warps_out = P->team_warps;
   if (chip_out) *chip_out = chip_points(P, P->team_warps);

@@ -131,3 +131,41 @@ def test_greeks_config_1024_puts_sampled():
     scale_g = np.maximum(np.abs(rgrad), 1e-3 * t["K"][idx][:, None, None])
     assert np.all(np.abs(grad[idx] - rgrad) <= GTOL * scale_g)
     assert np.all(np.abs(out[idx] - rout) <= 1e-10 * np.maximum(np.abs(rout), 1.0))
+
+
+_MODE_CHILD = r"""
+import sys, json, numpy as np, torch
+sys.path.insert(0, %(root)r)
+import workloads as W, paper_1110_2477_gb300 as ob
+t = W.concat(W.random_table(40, 5151, N_lo=2, N_hi=600),
+             W.make(k=0.02, N=500, sigma=0.1, payoff=W.CALL),
+             W.make(K=95.0, K2=105.0, k=0.015, N=400, sigma=0.12, payoff=W.SPREAD))
+out, grad, st = ob.greeks(t)
+torch.cuda.synchronize()
+np.save(%(npy)r, np.concatenate([out.cpu().numpy().reshape(-1), grad.cpu().numpy().reshape(-1),
+                                  st.cpu().numpy().astype(np.float64)]))
+"""
+
+
+def test_full_mode_and_checkpoint_mode_agree(tmp_path):
+    """The forward pass that keeps every level's records (the default when they fit) and the
+    checkpoint mode with recomputed segments (OB_GREEKS_FULL=0) give the same prices bit for
+    bit and the same derivatives up to the order of the atomic additions of the scatter."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for full in ("1", "0"):
+        npy = str(tmp_path / ("g%s.npy" % full))
+        env = dict(os.environ, OB_GREEKS_FULL=full)
+        r = subprocess.run([sys.executable, "-c", _MODE_CHILD % {"root": root, "npy": npy}], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res.append(np.load(npy))
+    n = 42
+    a, b = res
+    assert np.array_equal(a[-n:], b[-n:]) and np.all(a[-n:] == 0)
+    assert np.array_equal(a[:2 * n].view(np.int64), b[:2 * n].view(np.int64))
+    ga, gb = a[2 * n:-n], b[2 * n:-n]
+    assert np.all(np.abs(ga - gb) <= 1e-11 * np.maximum(np.abs(gb), 1.0))
