@@ -43,12 +43,58 @@ __device__ bool grid_barrier(GroupState* gs, unsigned& gen, unsigned long long w
   return s_ok != 0;
 }
 
+// One trapezoid round of k_tc_group from the complete shared level B (TcTrap): this CTA's
+// window of columns down D levels, the grid barrier for the counts, the copy into the shared
+// level B - D and the barrier that ends the round.  Sets t to the next level to compute
+// (B - D - 1) and returns the status every CTA agrees on.
+__device__ __forceinline__ int trap_round(obk::TcTrap<obk::BlockTeam<kGroupNW>>& tr, int B, int G, int c,
+                                          GroupState* gs, unsigned& gen, unsigned long long wait_ns,
+                                          int* s_cnt, int* s_cnt2, obk::Stats& acc, int& t) {
+  int D, Ga, a, b;
+  tr.plan(B, kTrapD, G, c, D, Ga, a, b);
+  const obk::Stats before = tr.R.st;
+  const bool ok = tr.compute(B, D, a, b);
+  acc.upts += tr.R.st.upts - before.upts;
+  acc.wpts += tr.R.st.wpts - before.wpts;
+  acc.zpts += tr.R.st.zpts - before.zpts;
+  if (threadIdx.x == 0) {
+    gs->cnt[0][c] = ok ? tr.nS : -1;
+    gs->cnt[1][c] = ok ? tr.nB : 0;
+  }
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  int bad = 0;
+  for (int k = threadIdx.x; k < G; k += blockDim.x) {
+    s_cnt[k] = __ldcg(&gs->cnt[0][k]);
+    s_cnt2[k] = __ldcg(&gs->cnt[1][k]);
+    if (s_cnt[k] < 0) bad = 1;
+  }
+  if (__syncthreads_or(bad)) return obk::ST_CAPACITY;
+  if (!tr.publish(B - D, G, c, s_cnt, s_cnt2)) return obk::ST_CAPACITY;
+  if (tr.R.st.zmax_level > acc.zmax_level) acc.zmax_level = tr.R.st.zmax_level;
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  t = B - D - 1;
+  return obk::ST_OK;
+}
+
+// Trapezoid rounds only where the columns carry about the same work: puts, and calls
+// whose cost rate stays below one step's move (spreads gather breakpoints around their
+// strikes, and a round's halo columns would repeat that work).
+__device__ __forceinline__ bool even_columns(const obk::Opt& o) {
+  if (o.payoff == obk::PAY_PUT) return true;
+  if (o.payoff != obk::PAY_CALL || !(o.N >= 1) || !(o.sigma > 0.0) || !(o.T > 0.0)) return false;
+  return o.k <= o.sigma * sqrt(o.T / o.N);
+}
+
+// TRAP: the options with even columns (even_columns), with trapezoid rounds for light
+// levels; otherwise the others, a level at a time.  The two instantiations run one after
+// the other on the call's stream, so each keeps its own register allocation.
+template <bool TRAP>
 __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
     size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds, unsigned long long wait_ns,
     int skip_cta) {
   __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
-  __shared__ int s_cnt[kGroupMax];
+  __shared__ int s_cnt[kGroupMax], s_cnt2[kGroupMax];
   obk::BlockTeam<kGroupNW> bt{tbuf};
   const int G = gridDim.x, c = blockIdx.x;
   // test control: this CTA never arrives at any barrier, so the others' bounded waits
@@ -58,6 +104,7 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
   unsigned gen = 0;
   for (int oi = 0; oi < n; ++oi) {
     const obk::Opt o = opts[oi];
+    if (even_columns(o) != TRAP) continue;  // the other instantiation prices it
     int rc = check_option(o, true);
     double ask = dnan(), bid = dnan();
     obk::Stats st;
@@ -70,9 +117,20 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
       rc = obk::ST_CAPACITY;
     if (rc == obk::ST_OK) {
       obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
+      obk::TcTrap<obk::BlockTeam<kGroupNW>> tr(bt, o, Lp, S);
       rc = g.begin();
       if (rc == obk::ST_OK && !grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
-      for (int t = o.N; t >= 0 && rc == obk::ST_OK; --t) {
+      for (int t = o.N; t >= 0 && rc == obk::ST_OK;) {
+        // a light level (few points a CTA, small nodes) goes down kTrapD levels in one
+        // trapezoid round
+        const int B = t + 1;
+        const int zb = __ldcg(&S.off[B & 1][2 * (B + 1)]);
+        if constexpr (TRAP) {
+          if (zb <= kTrapPoints * G && zb <= kTrapColumnPoints * (B + 1)) {
+            rc = trap_round(tr, B, G, c, gs, gen, wait_ns, s_cnt, s_cnt2, st, t);
+            continue;
+          }
+        }
         const bool ok = g.compute(t);
         if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? g.ztot : -1;
         if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
@@ -84,9 +142,14 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
         if (__syncthreads_or(bad)) { rc = obk::ST_CAPACITY; break; }
         if (!g.publish(t, s_cnt)) { rc = obk::ST_CAPACITY; break; }
         if (!grid_barrier(gs, gen, wait_ns)) { rc = ST_TIMEOUT; break; }
+        --t;
       }
       if (rc == obk::ST_OK && c == 0) g.root(ask, bid);
-      st = g.R.st;
+      const obk::Stats gst = g.R.st;
+      st.upts += gst.upts;
+      st.wpts += gst.wpts;
+      st.zpts += gst.zpts;
+      if (gst.zmax_level > st.zmax_level) st.zmax_level = gst.zmax_level;
     }
     if (threadIdx.x == 0) {
       if (rc == obk::ST_OK) {
@@ -200,7 +263,13 @@ cudaError_t launch_crr_group(int G, cudaStream_t s, const obk::Opt* opts, int n,
 }
 
 cudaError_t group_occupancy(int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tc_group, 32 * kGroupNW, 0);
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_tc_group<true>, 32 * kGroupNW, 0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tc_group<false>, 32 * kGroupNW, 0)) != cudaSuccess)
+    return e;
+  *per_sm = a < b ? a : b;
+  return cudaSuccess;
 }
 
 cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
@@ -209,7 +278,13 @@ cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, dou
   void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
                   (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds, (void*)&wait_ns,
                   (void*)&skip_cta};
-  return cudaLaunchCooperativeKernel((const void*)k_tc_group, dim3(G), dim3(32 * kGroupNW), args, 0, s);
+  // the options with even columns first (trapezoid rounds), then the others; the grid
+  // barrier's state starts from zero for each launch
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_tc_group<true>, dim3(G), dim3(32 * kGroupNW),
+                                              args, 0, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(gs, 0, sizeof(GroupState), s)) != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void*)k_tc_group<false>, dim3(G), dim3(32 * kGroupNW), args, 0, s);
 }
 
 }  // namespace obl

@@ -221,6 +221,9 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_tc_batched(
 constexpr int kGroupMax = 1024;                                    // CTAs of the grid at most
 constexpr unsigned long long kGroupWaitNs = 10000000000ULL;        // 10 s per barrier wait
 constexpr int kGroupNW = 16;                                       // warps per CTA
+constexpr int kTrapD = 8;         // levels of a trapezoid round of the whole-GPU form
+constexpr int kTrapPoints = 128;  // a level is light below this many points per CTA
+constexpr int kTrapColumnPoints = 8;  // ... and this many per column on average (small nodes)
 
 struct GroupState {
   unsigned int count;  // arrivals at the current barrier

@@ -11,8 +11,10 @@
 //                 outgrows its slice goes to an overflow list
 //  ob_tiers.cu    k_tc_retry (the follow-up launches: 16 CTAs, then one, larger slices)
 //                 and k_tc_plain (one warp per option in index order)
-//  ob_group.cu    k_tc_group: one cooperative launch of a CTA per SM, each option in
-//                 turn, every level split over all CTAs (TcGroup), bounded grid barriers
+//  ob_group.cu    k_tc_group: cooperative launches of a CTA per SM, each option in
+//                 turn, every level split over all CTAs (TcGroup) or, for light levels of
+//                 options with even columns, trapezoid rounds of levels (TcTrap); bounded
+//                 grid barriers
 //  ob_greeks8.cu, ob_greeks.cu   the adjoint (ob_adj.cuh) on CTA teams, single warps,
 //                 and its follow-up launches
 #include <cuda_runtime.h>

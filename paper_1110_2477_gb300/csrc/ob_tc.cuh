@@ -646,7 +646,10 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
 // ------------------------------------------------------------------ the option
 // CHIP: the instantiation with the fused level step (w of chunks of nodes in on-chip
 // arrays, level_fused); the plain instantiation reads and writes w in the global scratch.
-template <class Team, bool CHIP = false>
+// LOCAL: the passes see a window of columns of each level (a trapezoid round of the
+// whole-GPU form, TcTrap): level t holds the columns [cj0, min(cjend + t, t + 1)), indexed
+// from cj0 in the level arrays and the node tables; otherwise every column.
+template <class Team, bool CHIP = false, bool LOCAL = false>
 struct TcRun {
   const Team& tm;
   const Opt& o;
@@ -662,6 +665,7 @@ struct TcRun {
   int outCap;
   WBuf wb;    // CHIP: where passes 1-3 keep w (chip, or the global scratch for big nodes)
   WBuf chip;  // CHIP: on-chip arrays of the fused level step
+  int cj0 = 0, cjend = 0;  // LOCAL: the column window (see above)
 
   OB_HD TcRun(const Team& tm_, const Opt& o_, const Lay& L_) : tm(tm_), o(o_), L(L_), N(o_.N) {
     zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
@@ -694,7 +698,17 @@ struct TcRun {
     outCap = L.capZ;
   }
 
-  OB_HD void node_table(int t) { node_table_range(t, 0, t); }
+  // columns of level t that the level arrays hold
+  OB_HD int cols(int t) const {
+    if constexpr (LOCAL) {
+      const int e = cjend + t;
+      return (e < t + 1 ? e : t + 1) - cj0;
+    } else {
+      return t + 1;
+    }
+  }
+
+  OB_HD void node_table(int t) { node_table_range(t, 0, cols(t) - 1); }
 
   // per-node constants of level t for the nodes jlo <= j <= jhi
   OB_HD void node_table_range(int t, int jlo, int jhi) {
@@ -703,7 +717,8 @@ struct TcRun {
     const double lam = L.lam[t];
     const double kt = (t == 0) ? 0.0 : o.k;
     for (int j = jlo + lane; j <= jhi; j += Team::W) {
-      const double S = L.Stab[2 * j - t + N + 1];
+      const int ja = LOCAL ? j + cj0 : j;  // the column in the tree
+      const double S = L.Stab[2 * ja - t + N + 1];
       const double Sl = S * lam;
       nt[4 * j] = Sl * (1.0 + kt);
       nt[4 * j + 1] = Sl * (1.0 - kt);
@@ -723,7 +738,7 @@ struct TcRun {
 
   // union start of node n (seller nodes 0..t, then buyer nodes) of level t; n in [0, 2(t+1)]
   OB_HD int ustart_node(int t, int n) const {
-    const int W1 = t + 2, W0 = t + 1;
+    const int W1 = cols(t + 1), W0 = cols(t);
     const int UB1 = ustart(inOff, W1, 0, 0, W0);
     const int p = n >= W0 ? 1 : 0;
     return ustart(inOff, W1, UB1, p, n - p * W0);
@@ -738,7 +753,7 @@ struct TcRun {
                    int* wtail = nullptr) {
     const int lane = tm.lane();
     const int b1 = (t + 1) & 1;
-    const int W1 = t + 2, W0 = t + 1, nNodes = 2 * W0;
+    const int W1 = cols(t + 1), W0 = cols(t), nNodes = 2 * W0;
     const int* o1 = inOff;
     const double *Y1 = inY, *F1 = inF, *S1 = inS;
     const double* nt1 = L.nt[b1];
@@ -820,7 +835,7 @@ struct TcRun {
   template <bool TRACK = false>
   OB_HD void pass2(int t, int wtot, int* argA = nullptr, int* argB = nullptr) {
     const int lane = tm.lane();
-    const int W0 = t + 1;
+    const int W0 = cols(t);
     const double* nt = L.nt[t & 1];
     const long long KMAX = 0x7fffffffffffffffLL;
     long long carry = KMAX;
@@ -872,7 +887,7 @@ struct TcRun {
 
   // inputs of the piece starting at point i of w (level t)
   OB_HD void load_piece(int t, int i, int wtot, PieceIn<double>& in, int& node) const {
-    const int W0 = t + 1;
+    const int W0 = cols(t);
     const double* nt = L.nt[t & 1];
     node = wN()[i];
     in.head = (i == 0 || wN()[i - 1] != node);
@@ -917,7 +932,7 @@ struct TcRun {
   OB_HD bool pass3(int t, int wtot, int& ztot, int zbase = 0, unsigned* zsrc = nullptr,
                    unsigned* ztail = nullptr, const int* argA = nullptr, const int* argB = nullptr) {
     const int lane = tm.lane();
-    const int nNodes = 2 * (t + 1);
+    const int nNodes = 2 * cols(t);
     int* off = outOff;
     double* Yz = outY;
     double* Fz = outF;
@@ -990,7 +1005,7 @@ struct TcRun {
   // round the team probes W evenly spaced nodes of the bracket at once and keeps the
   // gap that holds it
   OB_HD int node_at(int t, long long target) const {
-    int lo = 0, hi = 2 * (t + 1);  // the answer lies in [lo, hi]
+    int lo = 0, hi = 2 * cols(t);  // the answer lies in [lo, hi]
     while (lo < hi) {
       const int step = (hi - lo + Team::W - 1) / Team::W;
       const int n = lo + tm.lane() * step;
@@ -1013,7 +1028,7 @@ struct TcRun {
   // numbers as the one-pass level.  Returns false on overflow of the global arrays.
   OB_HD bool level_fused(int t, int& utot, int& wtot, int& ztot) {
     static_assert(CHIP, "the fused level step needs the on-chip instantiation");
-    const int nNodes = 2 * (t + 1);
+    const int nNodes = 2 * cols(t);
     const WBuf gw = global_wbuf(L);
     const int cap = chip.cap - chip.cap / 8;  // merged points per chunk: room for crossings
     int zpos = 0, n0 = 0;
@@ -1299,6 +1314,159 @@ struct TcGroup {
     const double lam0 = L.lam[0];
     ask = R.root_value(0) / lam0;
     bid = -R.root_value(1) / lam0;
+  }
+};
+
+// ------------------------------------------------------------------ one option, trapezoid rounds
+// A round of the whole-GPU form for levels light enough that a level step is latency, not
+// work: from the complete shared level B, team c of Ga takes the columns [j0, j1) of level
+// B - D, copies the window [j0, min(j1 + D, B + 1)) of level B (both parties) into its
+// private arrays and computes the D levels below it there, each one column narrower on the
+// right (node (t, j) needs (t+1, j) and (t+1, j+1)); the columns right of j1 are computed by
+// the next team as well (the halo).  So the teams meet twice per round (counts, copy)
+// instead of twice per level.  The results are the same bits as a level at a time: every
+// node comes out of the same element-wise code from the same successors.
+template <class Team>
+struct TcTrap {
+  Lay Lp;                    // private arrays (both banks)
+  TcRun<Team, false, true> R;
+  GroupLay S;
+  int nS = 0, nB = 0;        // points of the round's output level: seller and buyer columns
+  int j0 = 0, j1 = 0;        // output columns of the round (none when j0 >= j1)
+
+  OB_HD TcTrap(const Team& tm, const Opt& o, const Lay& Lp_, const GroupLay& S_)
+      : Lp(Lp_), R(tm, o, Lp), S(S_) {}
+
+  // points of the complete level B in its columns below j (seller and buyer)
+  OB_HD long long col_points(int B, int j) const {
+    const int* so = S.off[B & 1];
+    const int W = B + 1;
+    return (long long)so[j] + so[W + j] - so[W];
+  }
+
+  // first column j in [0, cols] of level B with col_points(B, j) >= target: each round the
+  // team probes W evenly spaced columns of the bracket and keeps the gap that holds it
+  OB_HD int col_at(int B, int cols, long long target) const {
+    const Team& tm = R.tm;
+    int lo = 0, hi = cols;
+    while (lo < hi) {
+      const int step = (hi - lo + Team::W - 1) / Team::W;
+      const int j = lo + tm.lane() * step;
+      const bool below = j < hi && col_points(B, j) < target;
+      const int cnt = tm.count(below);
+      if (cnt == 0) break;
+      const int nhi = lo + cnt * step;
+      lo = lo + (cnt - 1) * step + 1;
+      if (nhi < hi) hi = nhi;
+    }
+    return lo;
+  }
+
+  // A round from the complete level B (B >= 1): D levels (B-1 .. B-D, at most Dmax), Ga
+  // active teams of G (at least 2D output columns each on average), and team c's output
+  // columns [a, b): the c-th Ga-quantile of level B's points over the output columns (every
+  // team computes the same bounds).
+  OB_HD void plan(int B, int Dmax, int G, int c, int& D, int& Ga, int& a, int& b) const {
+    D = B < Dmax ? B : Dmax;
+    const int cout = B - D + 1;
+    Ga = cout / (2 * D);
+    if (Ga < 1) Ga = 1;
+    if (Ga > G) Ga = G;
+    const long long tot = col_points(B, cout);
+    a = (c == 0) ? 0 : (c < Ga ? col_at(B, cout, tot * c / Ga) : cout);
+    b = (c >= Ga - 1) ? cout : col_at(B, cout, tot * (c + 1) / Ga);
+  }
+
+  // this team's window of levels B-1 .. B-D into its private banks; false on overflow
+  OB_HD bool compute(int B, int D, int a, int b) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    j0 = a;
+    j1 = b;
+    nS = nB = 0;
+    if (j0 >= j1) return true;  // idle this round
+    R.cj0 = j0;
+    R.cjend = j1 + D - B;
+    // the window of level B, seller columns then buyer columns, offsets from 0
+    const int W = B + 1, cl = R.cols(B), je = j0 + cl, pb = B & 1;
+    const int* so = S.off[pb];
+    const int bs = so[j0], ns = so[je] - bs, bb = so[W + j0], nb = so[W + je] - bb;
+    if (ns + nb > Lp.capZ) return false;
+    double *Y = Lp.zY[pb], *F = Lp.zF[pb], *Sl = Lp.zS[pb];
+    const double *SY = S.zY[pb], *SF = S.zF[pb], *SS = S.zS[pb];
+    int* po = Lp.off[pb];
+    for (int i = lane; i < ns; i += Team::W) {
+      Y[i] = SY[bs + i];
+      F[i] = SF[bs + i];
+      Sl[i] = SS[bs + i];
+    }
+    for (int i = lane; i < nb; i += Team::W) {
+      Y[ns + i] = SY[bb + i];
+      F[ns + i] = SF[bb + i];
+      Sl[ns + i] = SS[bb + i];
+    }
+    for (int k = lane; k < cl; k += Team::W) po[k] = so[j0 + k] - bs;
+    for (int k = lane; k <= cl; k += Team::W) po[cl + k] = ns + so[W + j0 + k] - bb;
+    R.node_table(B);  // the successors' tails of the first level
+    tm.sync();
+    for (int t = B - 1; t >= B - D; --t) {
+      R.use_banks(t);
+      R.node_table(t);
+      tm.sync();
+      int wtot = 0, utot = 0, ztot = 0;
+      if (!R.pass1(t, wtot, utot)) return false;
+      R.pass2(t, wtot);
+      if (!R.pass3(t, wtot, ztot)) return false;
+      R.st.upts += utot;
+      R.st.wpts += wtot;
+      R.st.zpts += ztot;
+    }
+    const int bt = (B - D) & 1, cw = j1 - j0;
+    nS = Lp.off[bt][cw];
+    nB = Lp.off[bt][2 * cw] - nS;
+    return true;
+  }
+
+  // place this team's output columns of level T in the shared bank; cs[g], cb[g]: the
+  // seller and buyer points of team g of G (0 for idle teams).  False when the level
+  // outgrows the shared bank (every team sees the same).
+  OB_HD bool publish(int T, int G, int c, const int* cs, const int* cb) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    long long preS = 0, preB = 0, totS = 0, totB = 0;
+    for (int g = 0; g < G; ++g) {
+      if (g < c) {
+        preS += cs[g];
+        preB += cb[g];
+      }
+      totS += cs[g];
+      totB += cb[g];
+    }
+    if (totS + totB > S.capZ) return false;
+    const int bt = T & 1, W = T + 1, cw = j1 - j0;
+    double *Y = S.zY[bt], *F = S.zF[bt], *Sl = S.zS[bt];
+    int* off = S.off[bt];
+    const double *pY = Lp.zY[bt], *pF = Lp.zF[bt], *pS = Lp.zS[bt];
+    const int* po = Lp.off[bt];
+    const int ps = (int)preS, pbz = (int)(totS + preB);
+    for (int i = lane; i < nS; i += Team::W) {
+      Y[ps + i] = pY[i];
+      F[ps + i] = pF[i];
+      Sl[ps + i] = pS[i];
+    }
+    for (int i = lane; i < nB; i += Team::W) {
+      Y[pbz + i] = pY[nS + i];
+      F[pbz + i] = pF[nS + i];
+      Sl[pbz + i] = pS[nS + i];
+    }
+    for (int k = lane; k < cw; k += Team::W) {
+      off[j0 + k] = ps + po[k];
+      off[W + j0 + k] = pbz + (po[cw + k] - nS);
+    }
+    if (c == 0 && lane == 0) off[2 * W] = (int)(totS + totB);
+    if ((int)(totS + totB) > R.st.zmax_level) R.st.zmax_level = (int)(totS + totB);
+    tm.sync();
+    return true;
   }
 };
 

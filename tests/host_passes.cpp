@@ -112,6 +112,68 @@ extern "C" int hp_price_split(const obk::Opt* o, int G, double* out, long long* 
   return rc;
 }
 
+// The whole-GPU form's level loop with trapezoid rounds (TcTrap) for light levels, G teams
+// run phase by phase over NaN-poisoned scratch: a level B whose points are at most
+// light_points * G goes down up to Dmax levels in one round, otherwise one level (TcGroup).
+// rounds[0] counts the trapezoid rounds, rounds[1] the single levels.
+extern "C" int hp_price_trap(const obk::Opt* o, int G, int Dmax, int light_points, int column_points,
+                             double* out, long long* pts, int* rounds) {
+  const size_t shared_bytes = 64ull << 20, priv_bytes = 32ull << 20;
+  char* base = arena(shared_bytes + priv_bytes * (size_t)G);
+  std::memset(base, 0xff, shared_bytes + priv_bytes * (size_t)G);
+  OneLane tm;
+  obk::GroupLay S;
+  if (!obk::carve_group_shared(base, shared_bytes, o->N, 2 * (o->N + 2), S)) return obk::ST_CAPACITY;
+  std::vector<obk::Lay> Lp(G);
+  std::vector<obk::TcGroup<OneLane>*> team(G);
+  std::vector<obk::TcTrap<OneLane>*> trap(G);
+  for (int c = 0; c < G; ++c) {
+    if (!obk::carve(base + shared_bytes + priv_bytes * (size_t)c, priv_bytes, o->N, 16, Lp[c]))
+      return obk::ST_CAPACITY;
+    team[c] = new obk::TcGroup<OneLane>(tm, *o, Lp[c], S, G, c);
+    trap[c] = new obk::TcTrap<OneLane>(tm, *o, Lp[c], S);
+  }
+  int rc = team[0]->begin();
+  for (int c = 1; c < G; ++c) team[c]->begin();
+  std::vector<int> cnt(G), cnt2(G);
+  rounds[0] = rounds[1] = 0;
+  for (int t = o->N; t >= 0 && rc == obk::ST_OK;) {
+    const int B = t + 1;
+    const long long zb = S.off[B & 1][2 * (B + 1)];
+    if (zb <= (long long)light_points * G && zb <= (long long)column_points * (B + 1)) {
+      int D = 0, Ga = 0;
+      for (int c = 0; c < G; ++c) {
+        int a, b;
+        trap[c]->plan(B, Dmax, G, c, D, Ga, a, b);
+        const bool ok = trap[c]->compute(B, D, a, b);
+        cnt[c] = ok ? trap[c]->nS : -1;
+        cnt2[c] = ok ? trap[c]->nB : 0;
+        if (!ok) rc = obk::ST_CAPACITY;
+      }
+      for (int c = 0; c < G && rc == obk::ST_OK; ++c)
+        if (!trap[c]->publish(B - D, G, c, cnt.data(), cnt2.data())) rc = obk::ST_CAPACITY;
+      ++rounds[0];
+      t = B - D - 1;
+      continue;
+    }
+    for (int c = 0; c < G; ++c) cnt[c] = team[c]->compute(t) ? team[c]->ztot : -1;
+    for (int c = 0; c < G; ++c)
+      if (cnt[c] < 0) rc = obk::ST_CAPACITY;
+    for (int c = 0; c < G && rc == obk::ST_OK; ++c)
+      if (!team[c]->publish(t, cnt.data())) rc = obk::ST_CAPACITY;
+    ++rounds[1];
+    --t;
+  }
+  if (rc == obk::ST_OK) team[0]->root(out[0], out[1]);
+  pts[0] = pts[1] = pts[2] = 0;
+  for (int c = 0; c < G; ++c) {
+    pts[0] += team[c]->R.st.upts + trap[c]->R.st.upts;
+    delete team[c];
+    delete trap[c];
+  }
+  return rc;
+}
+
 // full = 1: the records of every level kept by the forward pass; 0: checkpoints and a
 // recomputed segment per checkpoint
 extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad, int full) {

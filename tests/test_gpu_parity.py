@@ -109,6 +109,13 @@ def test_empty_batch_is_noop():
     out = torch.empty(0, dtype=torch.float64, device="cuda")
     ob.ob_price_ask_bid(params, 0, out)
     ob.ob_crr_american(params, 0, out)
+    ob.ob_price_ask_bid_hedge(params, 0, out, None, None)
+    ob.ob_price_ask_bid_plain(params, 0, out)
+    ob.ob_price_ask_bid_wide(params, 0, out)
+    ob.ob_crr_american_wide(params, 0, out)
+    ob.ob_price_ask_bid_noalloc(params, 0, out)
+    ob.ob_greeks(params, 0, out, out)
+    torch.cuda.synchronize()
 
 
 def test_batched_equals_plain_bitwise():
@@ -371,8 +378,11 @@ def test_wide_paper_scale_matches_oracle_and_batched():
     a, sa = _gpu(t)
     s2 = _ob().ob_get_stats()
     assert np.array_equal(a.view(np.int64), b.view(np.int64))
-    for k in ("node_updates", "u_points", "w_points", "z_points", "max_level_points"):
-        assert s[k] == s2[k], k
+    assert s["node_updates"] == s2["node_updates"]
+    # the trapezoid rounds recompute halo columns and publish every D-th level only
+    for k in ("u_points", "w_points", "z_points"):
+        assert s[k] >= s2[k], k
+    assert s["max_level_points"] <= s2["max_level_points"]
     ref, rst = oracle.price_ask_bid(t, nthreads=2)
     _assert_parity(t, b, sb, ref, rst)
 

@@ -98,6 +98,36 @@ def test_fused_level_step_is_bitwise_equal(cap):
             assert np.array_equal(pts1, pts2)
 
 
+@pytest.mark.parametrize("G,Dmax,light,colp", [(1, 8, 1 << 30, 1 << 30), (2, 3, 1 << 30, 1 << 30),
+                                                (3, 8, 1 << 30, 1 << 30), (7, 2, 1 << 30, 1 << 30),
+                                                (16, 8, 1 << 30, 1 << 30), (5, 8, 6, 1 << 30),
+                                                (4, 1, 1 << 30, 1 << 30), (3, 8, 0, 1 << 30),
+                                                (9, 8, 1 << 30, 5)])
+def test_trapezoid_rounds_are_bitwise_equal(G, Dmax, light, colp):
+    """The whole-GPU form's trapezoid rounds (TcTrap: each team copies a window of columns of
+    the complete level, split by points, and goes down up to Dmax levels on it, recomputing
+    the halo columns its right neighbour owns), alone or mixed with single levels (light: the
+    points a team, colp: the points a column, below which a level is taken in a round),
+    give the bits of the single-team run."""
+    t = _table()
+    P = ctypes.c_void_p
+    for i in range(len(t)):
+        rc1, out1, _ = _price(t[i])
+        a = _rec(t[i])
+        out2 = np.zeros(2)
+        pts = np.zeros(3, np.int64)
+        rounds = np.zeros(2, np.int32)
+        rc2 = _lib().hp_price_trap(a.ctypes.data_as(P), G, Dmax, light, colp, out2.ctypes.data_as(P),
+                                   pts.ctypes.data_as(P), rounds.ctypes.data_as(P))
+        assert rc1 == rc2, (i, rc1, rc2)
+        if rc1 == 0:
+            assert np.array_equal(out1.view(np.int64), out2.view(np.int64)), (i, out1, out2)
+            if light >= (1 << 30) and colp >= (1 << 30):
+                assert rounds[1] == 0 and rounds[0] >= (t["N"][i] + 1) // Dmax
+            if light == 0:
+                assert rounds[0] == 0
+
+
 @pytest.mark.parametrize("payoff", [W.PUT, W.CALL, W.SPREAD])
 def test_host_adjoint_matches_oracle_gradient(payoff):
     """The adjoint (line adjoints per piece) against the oracle's gradient on 40 options of
