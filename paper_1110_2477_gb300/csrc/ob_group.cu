@@ -43,6 +43,37 @@ __device__ bool grid_barrier(GroupState* gs, unsigned& gen, unsigned long long w
   return s_ok != 0;
 }
 
+// One level t of k_tc_group with its nodes split over the CTAs (TcSplit): pass 1 and the
+// share's pass 2, a grid barrier; the running minima across shares and the boundary points,
+// a barrier; pass 3, a barrier for the counts; the copy into the shared level, a barrier.
+// Returns the status every CTA agrees on.
+__device__ __forceinline__ int split_level(obk::TcSplit<obk::BlockTeam<kGroupNW>>& sp, int t, int G, int c,
+                                           GroupState* gs, unsigned& gen, unsigned long long wait_ns,
+                                           int* s_cnt, obk::Stats& acc) {
+  const obk::Stats before = sp.R.st;
+  sp.phase_a(t, gs->sr);
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  if (obk::TcSplit<obk::BlockTeam<kGroupNW>>::overflow(gs->sr, G)) return obk::ST_CAPACITY;
+  sp.phase_b(gs->sr);
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  const bool ok = sp.phase_c(t, gs->sr);
+  acc.upts += sp.R.st.upts - before.upts;
+  acc.wpts += sp.R.st.wpts - before.wpts;
+  acc.zpts += sp.R.st.zpts - before.zpts;
+  if (threadIdx.x == 0) gs->cnt[t & 1][c] = ok ? sp.ztot : -1;
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  int bad = 0;
+  for (int k = threadIdx.x; k < G; k += blockDim.x) {
+    s_cnt[k] = __ldcg(&gs->cnt[t & 1][k]);
+    if (s_cnt[k] < 0) bad = 1;
+  }
+  if (__syncthreads_or(bad)) return obk::ST_CAPACITY;
+  if (!sp.publish(t, s_cnt)) return obk::ST_CAPACITY;
+  if (sp.R.st.zmax_level > acc.zmax_level) acc.zmax_level = sp.R.st.zmax_level;
+  if (!grid_barrier(gs, gen, wait_ns)) return ST_TIMEOUT;
+  return obk::ST_OK;
+}
+
 // One trapezoid round of k_tc_group from the complete shared level B (TcTrap): this CTA's
 // window of columns down D levels, the grid barrier for the counts, the copy into the shared
 // level B - D and the barrier that ends the round.  Sets t to the next level to compute
@@ -76,25 +107,31 @@ __device__ __forceinline__ int trap_round(obk::TcTrap<obk::BlockTeam<kGroupNW>>&
   return obk::ST_OK;
 }
 
-// Trapezoid rounds only where the columns carry about the same work: puts, and calls
-// whose cost rate stays below one step's move (spreads gather breakpoints around their
-// strikes, and a round's halo columns would repeat that work).
-__device__ __forceinline__ bool even_columns(const obk::Opt& o) {
-  if (o.payoff == obk::PAY_PUT) return true;
-  if (o.payoff != obk::PAY_CALL || !(o.N >= 1) || !(o.sigma > 0.0) || !(o.T > 0.0)) return false;
-  return o.k <= o.sigma * sqrt(o.T / o.N);
+// How an option runs on the whole GPU.  Trapezoid rounds (1) where the columns carry about
+// the same work: puts, and calls whose cost rate stays below one step's move (spreads gather
+// breakpoints around their strikes, and a round's halo columns would repeat that work).
+// Nodes split over the CTAs (2) where large nodes would leave most CTAs waiting: calls and
+// spreads with k > split_x sigma sqrt(dt), on the levels whose largest node outgrows a share
+// (split_x < 0: every level of every such option, a test control).  Otherwise shares of
+// whole nodes (0).
+enum { WIDE_NODES = 0, WIDE_TRAP = 1, WIDE_SPLIT = 2 };
+__device__ __forceinline__ int wide_mode(const obk::Opt& o, double split_x) {
+  if (o.payoff == obk::PAY_PUT) return WIDE_TRAP;
+  if (!(o.N >= 1) || !(o.sigma > 0.0) || !(o.T > 0.0) || !(o.k >= 0.0)) return WIDE_NODES;
+  const double step = o.sigma * sqrt(o.T / o.N);
+  if (o.payoff == obk::PAY_CALL && o.k <= step) return WIDE_TRAP;
+  return (o.k > split_x * step) ? WIDE_SPLIT : WIDE_NODES;
 }
 
-// TRAP: the options with even columns (even_columns), with trapezoid rounds for light
-// levels; otherwise the others, a level at a time.  The two instantiations run one after
-// the other on the call's stream, so each keeps its own register allocation.
-template <bool TRAP>
+// MODE: the options of that wide_mode; the three instantiations run one after the other on
+// the call's stream, so each keeps its own register allocation.
+template <int MODE>
 __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     const obk::Opt* __restrict__ opts, int n, double* out, int* status, char* arena,
     size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds, unsigned long long wait_ns,
-    int skip_cta) {
+    int skip_cta, double split_x) {
   __shared__ long long tbuf[obk::BlockTeam<kGroupNW>::BUF];
-  __shared__ int s_cnt[kGroupMax], s_cnt2[kGroupMax];
+  __shared__ int s_cnt[kGroupMax], s_cnt2[kGroupMax], s_max;
   obk::BlockTeam<kGroupNW> bt{tbuf};
   const int G = gridDim.x, c = blockIdx.x;
   // test control: this CTA never arrives at any barrier, so the others' bounded waits
@@ -104,7 +141,7 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
   unsigned gen = 0;
   for (int oi = 0; oi < n; ++oi) {
     const obk::Opt o = opts[oi];
-    if (even_columns(o) != TRAP) continue;  // the other instantiation prices it
+    if (wide_mode(o, split_x) != MODE) continue;  // another instantiation prices it
     int rc = check_option(o, true);
     double ask = dnan(), bid = dnan();
     obk::Stats st;
@@ -118,6 +155,7 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
     if (rc == obk::ST_OK) {
       obk::TcGroup<obk::BlockTeam<kGroupNW>> g(bt, o, Lp, S, G, c);
       obk::TcTrap<obk::BlockTeam<kGroupNW>> tr(bt, o, Lp, S);
+      obk::TcSplit<obk::BlockTeam<kGroupNW>> sp(bt, o, Lp, S, G, c);
       rc = g.begin();
       if (rc == obk::ST_OK && !grid_barrier(gs, gen, wait_ns)) rc = ST_TIMEOUT;
       for (int t = o.N; t >= 0 && rc == obk::ST_OK;) {
@@ -125,9 +163,28 @@ __global__ void __launch_bounds__(32 * kGroupNW, 1) k_tc_group(
         // trapezoid round
         const int B = t + 1;
         const int zb = __ldcg(&S.off[B & 1][2 * (B + 1)]);
-        if constexpr (TRAP) {
+        if constexpr (MODE == WIDE_TRAP) {
           if (zb <= kTrapPoints * G && zb <= kTrapColumnPoints * (B + 1)) {
             rc = trap_round(tr, B, G, c, gs, gen, wait_ns, s_cnt, s_cnt2, st, t);
+            continue;
+          }
+        }
+        if constexpr (MODE == WIDE_SPLIT) {
+          // split the nodes when the largest union of two successors exceeds a share by more
+          // than the split's own cost (two more grid barriers and the boundary exchanges)
+          if (threadIdx.x == 0) s_max = 0;
+          __syncthreads();
+          const int* so = S.off[B & 1];
+          int m = 0;
+          for (int k = threadIdx.x; k < 2 * (B + 1); k += blockDim.x) {
+            const int d = __ldcg(&so[k + 1]) - __ldcg(&so[k]);
+            m = d > m ? d : m;
+          }
+          atomicMax(&s_max, m);
+          __syncthreads();
+          if (split_x < 0.0 || 2LL * s_max * G > 2LL * zb + (long long)kSplitExtraPoints * G) {
+            rc = split_level(sp, t, G, c, gs, gen, wait_ns, s_cnt, st);
+            --t;
             continue;
           }
         }
@@ -263,28 +320,36 @@ cudaError_t launch_crr_group(int G, cudaStream_t s, const obk::Opt* opts, int n,
 }
 
 cudaError_t group_occupancy(int* per_sm) {
-  int a = 0, b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_tc_group<true>, 32 * kGroupNW, 0);
+  int a = 0, b = 0, d = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_tc_group<WIDE_TRAP>, 32 * kGroupNW, 0);
   if (e != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tc_group<false>, 32 * kGroupNW, 0)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tc_group<WIDE_SPLIT>, 32 * kGroupNW, 0)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_tc_group<WIDE_NODES>, 32 * kGroupNW, 0)) !=
+      cudaSuccess)
     return e;
   *per_sm = a < b ? a : b;
+  if (d < *per_sm) *per_sm = d;
   return cudaSuccess;
 }
 
 cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
                          char* arena, size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds,
-                         unsigned long long wait_ns, int skip_cta) {
+                         unsigned long long wait_ns, int skip_cta, double split_x) {
   void* args[] = {(void*)&opts, (void*)&n, (void*)&out, (void*)&status, (void*)&arena,
                   (void*)&shared_bytes, (void*)&cta_bytes, (void*)&gs, (void*)&ds, (void*)&wait_ns,
-                  (void*)&skip_cta};
-  // the options with even columns first (trapezoid rounds), then the others; the grid
-  // barrier's state starts from zero for each launch
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_tc_group<true>, dim3(G), dim3(32 * kGroupNW),
-                                              args, 0, s);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(gs, 0, sizeof(GroupState), s)) != cudaSuccess) return e;
-  return cudaLaunchCooperativeKernel((const void*)k_tc_group<false>, dim3(G), dim3(32 * kGroupNW), args, 0, s);
+                  (void*)&skip_cta, (void*)&split_x};
+  // one launch per wide_mode; the grid barrier's state starts from zero for each launch
+  const void* kern[3] = {(const void*)k_tc_group<WIDE_TRAP>, (const void*)k_tc_group<WIDE_SPLIT>,
+                         (const void*)k_tc_group<WIDE_NODES>};
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < 3; ++m) {
+    if (m > 0 && (e = cudaMemsetAsync(gs, 0, sizeof(GroupState), s)) != cudaSuccess) return e;
+    if ((e = cudaLaunchCooperativeKernel(kern[m], dim3(G), dim3(32 * kGroupNW), args, 0, s)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace obl

@@ -224,6 +224,8 @@ constexpr int kGroupNW = 16;                                       // warps per 
 constexpr int kTrapD = 8;         // levels of a trapezoid round of the whole-GPU form
 constexpr int kTrapPoints = 128;  // a level is light below this many points per CTA
 constexpr int kTrapColumnPoints = 8;  // ... and this many per column on average (small nodes)
+constexpr double kWideSplitX = 6.0;   // nodes split over CTAs when k > this x sigma sqrt(dt)
+constexpr int kSplitExtraPoints = 4000;  // ... on levels whose largest node exceeds a share by this
 
 struct GroupState {
   unsigned int count;  // arrivals at the current barrier
@@ -231,6 +233,7 @@ struct GroupState {
   int err;             // a wait ran out: every later barrier fails at once
   int pad;
   int cnt[2][kGroupMax];  // points of each CTA's share of a level (-1: overflow)
+  obk::SplitRec sr[kGroupMax];  // each CTA's share of a level whose nodes are split (TcSplit)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -364,7 +367,7 @@ cudaError_t launch_crr_group(int G, cudaStream_t s, const obk::Opt* opts, int n,
                              double* buf, size_t buf_doubles, GroupState* gs, unsigned long long wait_ns);
 cudaError_t launch_group(int G, cudaStream_t s, const obk::Opt* opts, int n, double* out, int* status,
                          char* arena, size_t shared_bytes, size_t cta_bytes, GroupState* gs, DevStats* ds,
-                         unsigned long long wait_ns, int skip_cta);
+                         unsigned long long wait_ns, int skip_cta, double split_x);
 
 // ob_greeks8.cu (8- and 16-warp CTA teams) and ob_greeks.cu (the follow-up launches)
 cudaError_t launch_greeks_team8(int grid, cudaStream_t s, const obk::Opt* opts, int n, double* out, double* grad,

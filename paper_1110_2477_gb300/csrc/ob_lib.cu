@@ -246,6 +246,7 @@ struct DevPool {
   GroupState* gstate = nullptr;  // whole-GPU form
   int group_ctas = 0;
   unsigned long long wide_wait_ns = kGroupWaitNs;  // bound of one grid-barrier wait
+  double wide_split_x = kWideSplitX;  // whole-GPU form: nodes split above this (OB_WIDE_SPLIT_X)
   int test_skip_calls = 0;  // OB_TEST_WIDE_SKIP: calls in which one CTA never arrives
   // autotuner sample buffers
   obk::Opt* tune_params = nullptr;
@@ -315,6 +316,7 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
     if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 8 ? 8 : 16;
     if (const char* g = getenv("OB_GREEKS_FULL")) P.greeks_full = atoi(g) != 0;
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
+    if (const char* x = getenv("OB_WIDE_SPLIT_X")) P.wide_split_x = atof(x);
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
     if (const char* c = getenv("OB_CHIP_POINTS")) P.chip_req = atoi(c);
     if ((e = cudaDeviceGetAttribute(&P.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
@@ -683,7 +685,8 @@ int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* 
     --P->test_skip_calls;
     skip_cta = G - 1;
   }
-  if ((e = launch_group(G, s, opts, n, out, status, arena, shared_bytes, cta_bytes, gs, ds, wait_ns, skip_cta)) !=
+  if ((e = launch_group(G, s, opts, n, out, status, arena, shared_bytes, cta_bytes, gs, ds, wait_ns, skip_cta,
+                        P->wide_split_x)) !=
       cudaSuccess)
     return cuda_fail(e);
   P->last_tiers = 1;

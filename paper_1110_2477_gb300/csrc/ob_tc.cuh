@@ -649,7 +649,10 @@ OB_HD void piece(const PieceIn<T>& in, O& out, D& dec) {
 // LOCAL: the passes see a window of columns of each level (a trapezoid round of the
 // whole-GPU form, TcTrap): level t holds the columns [cj0, min(cjend + t, t + 1)), indexed
 // from cj0 in the level arrays and the node tables; otherwise every column.
-template <class Team, bool CHIP = false, bool LOCAL = false>
+// SPLIT: pass 1 takes a range of union points that may start and end inside nodes (a share
+// of a split level, TcSplit), and passes 2-3 see the w points just outside their range (the
+// neighbouring shares' points at index -1 and wtot when the first and last nodes continue).
+template <class Team, bool CHIP = false, bool LOCAL = false, bool SPLIT = false>
 struct TcRun {
   const Team& tm;
   const Opt& o;
@@ -666,6 +669,12 @@ struct TcRun {
   WBuf wb;    // CHIP: where passes 1-3 keep w (chip, or the global scratch for big nodes)
   WBuf chip;  // CHIP: on-chip arrays of the fused level step
   int cj0 = 0, cjend = 0;  // LOCAL: the column window (see above)
+  // SPLIT: the union points [ub, ue) of pass 1, the owner code (2 own) of the union point
+  // before ub, whether the first and last nodes continue in the previous and next shares,
+  // and the slope of the function just left of the first piece when the first node does
+  int ub = 0, ue = 0, carry0 = 0;
+  bool lcont = false, rcont = false, head_m1 = false;
+  double slope0 = 0.0;
 
   OB_HD TcRun(const Team& tm_, const Opt& o_, const Lay& L_) : tm(tm_), o(o_), L(L_), N(o_.N) {
     zeta = (o.payoff == PAY_PUT) ? -1 : (o.payoff == PAY_CALL ? 1 : 0);
@@ -744,6 +753,28 @@ struct TcRun {
     return ustart(inOff, W1, UB1, p, n - p * W0);
   }
 
+  // SPLIT: 2 * (owner just left of the next union point) of the last union point before q
+  // that is not a duplicate, for q inside node n of level t (q > its first union point); the
+  // carry that pass 1 would hand across from the union points before q.
+  OB_HD int own_before(int t, int n, int q) const {
+    const int W1 = cols(t + 1), W0 = cols(t);
+    const int* o1 = inOff;
+    const double* nt1 = L.nt[(t + 1) & 1];
+    const int UB1 = ustart(o1, W1, 0, 0, W0);
+    const int p = n >= W0 ? 1 : 0;
+    const int j = n - p * W0;
+    const int* op = o1 + p * W1;
+    const int aoff = op[j + 1], ma = op[j + 2] - aoff, boff = op[j], mb = aoff - boff;
+    int ql = q - 1 - ustart(o1, W1, UB1, p, j);
+    P1 e;
+    p1_analyze(inY + aoff, inF + aoff, inS + aoff, ma, -nt1[4 * (j + 1)], inY + boff, inF + boff,
+               inS + boff, mb, -nt1[4 * j], ql, e);
+    if (e.dup && ql > 0)  // duplicates are never adjacent, and never a node's first point
+      p1_analyze(inY + aoff, inF + aoff, inS + aoff, ma, -nt1[4 * (j + 1)], inY + boff, inF + boff,
+                 inS + boff, mb, -nt1[4 * j], ql - 1, e);
+    return 2 * e.own;
+  }
+
   // pass 1: w = max(z_up, z_down) for the nodes n0 <= n < n1 of level t (n1 < 0: all
   // nodes); w of node n0 starts at position 0.  Returns false on overflow.
   // PROV (the adjoint's rerun): wsrc[i] receives the successor piece whose line w follows
@@ -759,10 +790,10 @@ struct TcRun {
     const double* nt1 = L.nt[b1];
     const int UB1 = ustart(o1, W1, 0, 0, W0);
     if (n1 < 0) n1 = nNodes;
-    const int u0 = ustart_node(t, n0);
-    const int Utot = ustart_node(t, n1);  // end of the range
+    const int u0 = SPLIT ? ub : ustart_node(t, n0);
+    const int Utot = SPLIT ? ue : ustart_node(t, n1);  // end of the range
     utot = Utot - u0;
-    int ncur = n0, wpos = 0, carry_own = 0;  // carry_own: 2*own of the last non-duplicate point
+    int ncur = n0, wpos = 0, carry_own = SPLIT ? carry0 : 0;  // 2*own of the last non-duplicate point
     bool ovf = false;
     for (int base = u0; base < Utot; base += Team::W) {
       const int q = base + lane;
@@ -890,8 +921,18 @@ struct TcRun {
     const int W0 = cols(t);
     const double* nt = L.nt[t & 1];
     node = wN()[i];
-    in.head = (i == 0 || wN()[i - 1] != node);
-    in.tail = (i + 1 == wtot || wN()[i + 1] != node);
+    if constexpr (SPLIT) {
+      if (i < 0) {  // the previous share's last point: its head flag came with it
+        in.head = head_m1;
+        in.tail = false;
+      } else {
+        in.head = (i == 0) ? !lcont : wN()[i - 1] != node;
+        in.tail = (i + 1 == wtot) ? !rcont : wN()[i + 1] != node;
+      }
+    } else {
+      in.head = (i == 0 || wN()[i - 1] != node);
+      in.tail = (i + 1 == wtot || wN()[i + 1] != node);
+    }
     const int p = node >= W0 ? 1 : 0;
     const int j = node - p * W0;
     in.Sa = nt[4 * j];
@@ -923,6 +964,21 @@ struct TcRun {
     }
   }
 
+  // SPLIT: the slope of z just left of w point 0 when its node continues from the previous
+  // share: the last slope of the piece that starts at that share's last point (index -1)
+  OB_HD double slope_before(int t) const {
+    PieceIn<double> in;
+    int node;
+    load_piece(t, -1, 0, in, node);
+    PieceOut<double> po;
+    po.ntl = po.nm = 0;
+    po.first = EmT<double>{0.0, 0.0, 0.0};
+    po.last_slope = po.tail_slope = 0.0;
+    NoDec nd;
+    piece(in, po, nd);
+    return po.last_slope;
+  }
+
   // pass 3: restriction and exercise for every piece of w; writes level t, the
   // points from position zbase on (w of a chunk of nodes: its first node's points)
   // PROV (the adjoint's rerun): zsrc[p] receives the line (KW..KU4 code) the function
@@ -939,7 +995,7 @@ struct TcRun {
     double* Sz = outS;
     int zpos = zbase;
     bool ovf = false;
-    double carry_slope = 0.0;
+    double carry_slope = SPLIT ? slope0 : 0.0;
     for (int base = 0; base < wtot; base += Team::W) {
       const int i = base + lane;
       const bool ok = i < wtot;
@@ -1309,8 +1365,11 @@ struct TcGroup {
     return true;
   }
 
-  // ask and bid from the shared level 0 (after the last publish and barrier)
-  OB_HD void root(double& ask, double& bid) const {
+  // ask and bid from the shared level 0 (after the last publish and barrier); the node table
+  // of level 0 is this team's own (a share of split nodes may not have held node 0)
+  OB_HD void root(double& ask, double& bid) {
+    R.node_table_range(0, 0, 0);
+    R.tm.sync();
     const double lam0 = L.lam[0];
     ask = R.root_value(0) / lam0;
     bid = -R.root_value(1) / lam0;
@@ -1465,6 +1524,226 @@ struct TcTrap {
     }
     if (c == 0 && lane == 0) off[2 * W] = (int)(totS + totB);
     if ((int)(totS + totB) > R.st.zmax_level) R.st.zmax_level = (int)(totS + totB);
+    tm.sync();
+    return true;
+  }
+};
+
+// ------------------------------------------------------------------ one option, nodes split over teams
+// A level of the whole-GPU form whose nodes are large next to a share of whole nodes: team
+// c of G takes the c-th G-quantile of the level's merged successor points wherever nodes
+// begin or end, so one large node is shared by several teams.  What crosses a share boundary:
+//   - pass 1: the owner of the segment before the share's first union point (recomputed from
+//     that point's successors, own_before);
+//   - pass 2: the running minima of h (from the left) and g (from the right) restart at the
+//     share's ends and are then combined with the other shares' parts of the same node
+//     (phase B, after every team published the minima of its first and last node);
+//   - pass 3: the piece at the share's last point ends at the next share's first point, and
+//     the first piece needs the slope just left of it; each team publishes its first and last
+//     points (phase B) and reads its neighbours' into index -1 and wtot (phase C).
+// The w and z points are the ones a single team produces, so the results are the same bits.
+struct SplitRec {
+  int state;                // A: 0 points of w, 1 empty, 2 overflow
+  int first_node, last_node;
+  int lhead;                // B: the last point starts its node
+  long long cb_last, ca_first;               // A: h minimum of the last node's part, g of the first's
+  double fy, ff, fs, ly, lf, ls;             // B: first and last point of w
+  long long fgk, fhk, fca, fcb, lgk, lhk, lca, lcb;
+};
+
+template <class Team>
+struct TcSplit {
+  Lay L;  // the shared level banks, the private arrays with w shifted by one point
+  TcRun<Team, false, false, true> R;
+  int G, c;
+  double *zpY, *zpF, *zpS;
+  int* poff;
+  int capP;
+  int n0 = 0, n1 = 0, wtot = 0, ztot = 0, fnode = -1, lnode = -1;
+
+  OB_HD static Lay merge(const Lay& Lp, const GroupLay& S) {
+    Lay L = Lp;
+    for (int b = 0; b < 2; ++b) {
+      L.zY[b] = S.zY[b]; L.zF[b] = S.zF[b]; L.zS[b] = S.zS[b]; L.off[b] = S.off[b];
+    }
+    L.capZ = S.capZ;
+    L.wY += 1; L.wF += 1; L.wS += 1; L.wN += 1;  // index -1 holds the previous share's point
+    L.wGK += 1; L.wHK += 1; L.wCA += 1; L.wCB += 1;
+    L.capW -= 2;                                 // and index wtot the next share's
+    return L;
+  }
+
+  OB_HD TcSplit(const Team& tm, const Opt& o, const Lay& Lp, const GroupLay& S, int G_, int c_)
+      : L(merge(Lp, S)), R(tm, o, L), G(G_), c(c_), zpY(Lp.zY[0]), zpF(Lp.zF[0]), zpS(Lp.zS[0]),
+        poff(Lp.off[0]), capP(Lp.capZ) {}
+
+  // phase A: pass 1 on this team's union points, pass 2 within the share; rec = its record
+  OB_HD void phase_a(int t, SplitRec* recs) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    R.use_banks(t);
+    const int nNodes = 2 * (t + 1), W0 = t + 1;
+    const long long U = R.ustart_node(t, nNodes);
+    const int u0 = (int)(U * c / G), u1 = (int)(U * (c + 1) / G);
+    wtot = ztot = 0;
+    fnode = lnode = -1;
+    int state = 1;
+    if (u0 < u1) {
+      n0 = R.node_at(t, (long long)u0 + 1) - 1;
+      n1 = R.node_at(t, u1);
+      // node constants of the share: level t for its nodes, level t+1 for j, j+1
+      const int s_lo = n0, s_hi = (n1 < W0 ? n1 : W0) - 1;
+      const int b_lo = (n0 > W0 ? n0 : W0) - W0, b_hi = n1 - 1 - W0;
+      if (s_lo <= s_hi) {
+        R.node_table_range(t, s_lo, s_hi);
+        R.node_table_range(t + 1, s_lo, s_hi + 1);
+      }
+      if (b_lo <= b_hi) {
+        R.node_table_range(t, b_lo, b_hi);
+        R.node_table_range(t + 1, b_lo, b_hi + 1);
+      }
+      tm.sync();
+      int code = 0;
+      if (u0 > R.ustart_node(t, n0) && lane == 0) code = R.own_before(t, n0, u0);
+      R.carry0 = tm.bcast0(code);
+      R.ub = u0;
+      R.ue = u1;
+      R.outY = zpY; R.outF = zpF; R.outS = zpS; R.outOff = poff; R.outCap = capP;
+      int utot = 0;
+      if (!R.pass1(t, wtot, utot, n0, n1)) {
+        state = 2;
+      } else {
+        R.st.upts += utot;
+        R.pass2(t, wtot);
+        state = wtot > 0 ? 0 : 1;
+      }
+    }
+    if (state == 0) {
+      fnode = R.wN()[0];
+      lnode = R.wN()[wtot - 1];
+    }
+    if (lane == 0) {
+      SplitRec& r = recs[c];
+      r.state = state;
+      r.first_node = fnode;
+      r.last_node = lnode;
+      r.cb_last = state == 0 ? R.wCB()[wtot - 1] : KMAXLL;
+      r.ca_first = state == 0 ? R.wCA()[0] : KMAXLL;
+    }
+    tm.sync();
+  }
+
+  // after the barrier: any team's overflow (every team sees the same)
+  OB_HD static bool overflow(const SplitRec* recs, int G) {
+    for (int g = 0; g < G; ++g)
+      if (recs[g].state == 2) return true;
+    return false;
+  }
+
+  // the nearest team before (dir -1) or after (+1) this one with points of w
+  OB_HD int neighbour(const SplitRec* recs, int dir) const {
+    for (int g = c + dir; g >= 0 && g < G; g += dir)
+      if (recs[g].state == 0) return g;
+    return -1;
+  }
+
+  // phase B: the running minima of the first and last node combined with the other shares'
+  // parts of those nodes; then this team's first and last points into its record
+  OB_HD void phase_b(SplitRec* recs) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    R.lcont = R.rcont = false;
+    if (wtot == 0) return;
+    long long carryB = KMAXLL, carryA = KMAXLL;
+    for (int g = c - 1; g >= 0; --g) {  // h from the left: the earlier parts of the first node
+      const SplitRec& r = recs[g];
+      if (r.state != 0) continue;
+      if (r.last_node != fnode) break;
+      R.lcont = true;
+      carryB = kmin(carryB, r.cb_last);
+      if (r.first_node != r.last_node) break;
+    }
+    for (int g = c + 1; g < G; ++g) {  // g from the right: the later parts of the last node
+      const SplitRec& r = recs[g];
+      if (r.state != 0) continue;
+      if (r.first_node != lnode) break;
+      R.rcont = true;
+      carryA = kmin(carryA, r.ca_first);
+      if (r.first_node != r.last_node) break;
+    }
+    long long* CB = R.wCB();
+    long long* CA = R.wCA();
+    const int* wn = R.wN();
+    for (int i = lane; i < wtot; i += Team::W) {
+      const int n = wn[i];
+      if (n == fnode) CB[i] = kmin(CB[i], carryB);
+      if (n == lnode) CA[i] = kmin(CA[i], carryA);
+    }
+    tm.sync();
+    if (lane == 0) {
+      SplitRec& r = recs[c];
+      const int a = 0, b = wtot - 1;
+      r.fy = R.wY()[a]; r.ff = R.wF()[a]; r.fs = R.wS()[a];
+      r.fgk = R.wGK()[a]; r.fhk = R.wHK()[a]; r.fca = CA[a]; r.fcb = CB[a];
+      r.ly = R.wY()[b]; r.lf = R.wF()[b]; r.ls = R.wS()[b];
+      r.lgk = R.wGK()[b]; r.lhk = R.wHK()[b]; r.lca = CA[b]; r.lcb = CB[b];
+      r.lhead = (b == 0) ? !R.lcont : (wn[b - 1] != lnode);
+    }
+    tm.sync();
+  }
+
+  // phase C: the neighbours' points at index -1 and wtot, then pass 3; false on overflow
+  OB_HD bool phase_c(int t, const SplitRec* recs) {
+    const Team& tm = R.tm;
+    ztot = 0;
+    if (wtot == 0) return true;
+    if (R.lcont && tm.lane() == 0) {
+      const SplitRec& r = recs[neighbour(recs, -1)];
+      R.wY()[-1] = r.ly; R.wF()[-1] = r.lf; R.wS()[-1] = r.ls; R.wN()[-1] = fnode;
+      R.wGK()[-1] = r.lgk; R.wHK()[-1] = r.lhk; R.wCA()[-1] = r.lca; R.wCB()[-1] = r.lcb;
+    }
+    if (R.rcont && tm.lane() == 0) {
+      const SplitRec& r = recs[neighbour(recs, 1)];
+      R.wY()[wtot] = r.fy; R.wF()[wtot] = r.ff; R.wS()[wtot] = r.fs; R.wN()[wtot] = lnode;
+      R.wGK()[wtot] = r.fgk; R.wHK()[wtot] = r.fhk; R.wCA()[wtot] = r.fca; R.wCB()[wtot] = r.fcb;
+    }
+    tm.sync();
+    R.slope0 = 0.0;
+    if (R.lcont) {
+      R.head_m1 = recs[neighbour(recs, -1)].lhead != 0;
+      R.slope0 = R.slope_before(t);
+    }
+    if (!R.pass3(t, wtot, ztot)) return false;
+    R.st.wpts += wtot;
+    R.st.zpts += ztot;
+    return true;
+  }
+
+  // phase D: this team's z points into the shared bank at their prefix, and the offsets of
+  // the nodes whose first point is here; cnt[g] = points of team g.  False when the level
+  // outgrows the shared bank (every team sees the same).
+  OB_HD bool publish(int t, const int* cnt) {
+    const Team& tm = R.tm;
+    const int lane = tm.lane();
+    long long pre = 0, total = 0;
+    for (int g = 0; g < G; ++g) {
+      if (g < c) pre += cnt[g];
+      total += cnt[g];
+    }
+    if (total > L.capZ) return false;
+    const int bt = t & 1;
+    double *Y = L.zY[bt], *F = L.zF[bt], *S = L.zS[bt];
+    int* off = L.off[bt];
+    const int p = (int)pre;
+    for (int i = lane; i < ztot; i += Team::W) {
+      Y[p + i] = zpY[i];
+      F[p + i] = zpF[i];
+      S[p + i] = zpS[i];
+    }
+    if (wtot > 0)
+      for (int n = fnode + (R.lcont ? 1 : 0) + lane; n <= lnode; n += Team::W) off[n] = p + poff[n];
+    if (c == 0 && lane == 0) off[2 * (t + 1)] = (int)total;
+    if ((int)total > R.st.zmax_level) R.st.zmax_level = (int)total;
     tm.sync();
     return true;
   }

@@ -174,6 +174,48 @@ extern "C" int hp_price_trap(const obk::Opt* o, int G, int Dmax, int light_point
   return rc;
 }
 
+// Every level with its nodes split over G teams at the G-quantiles of the merged successor
+// points (TcSplit), the teams run phase by phase over NaN-poisoned scratch.
+extern "C" int hp_price_nsplit(const obk::Opt* o, int G, double* out, long long* pts) {
+  const size_t shared_bytes = 64ull << 20, priv_bytes = 32ull << 20;
+  char* base = arena(shared_bytes + priv_bytes * (size_t)G);
+  std::memset(base, 0xff, shared_bytes + priv_bytes * (size_t)G);
+  OneLane tm;
+  obk::GroupLay S;
+  if (!obk::carve_group_shared(base, shared_bytes, o->N, 2 * (o->N + 2), S)) return obk::ST_CAPACITY;
+  std::vector<obk::Lay> Lp(G);
+  std::vector<obk::TcSplit<OneLane>*> team(G);
+  for (int c = 0; c < G; ++c) {
+    if (!obk::carve(base + shared_bytes + priv_bytes * (size_t)c, priv_bytes, o->N, 16, Lp[c]))
+      return obk::ST_CAPACITY;
+    team[c] = new obk::TcSplit<OneLane>(tm, *o, Lp[c], S, G, c);
+  }
+  obk::TcGroup<OneLane> g0(tm, *o, Lp[0], S, G, 0);
+  int rc = g0.begin();  // the leaves, and every team's tree constants
+  for (int c = 1; c < G; ++c) obk::TcGroup<OneLane>(tm, *o, Lp[c], S, G, c).begin();
+  std::vector<obk::SplitRec> recs(G);
+  std::vector<int> cnt(G);
+  for (int t = o->N; t >= 0 && rc == obk::ST_OK; --t) {
+    for (int c = 0; c < G; ++c) team[c]->phase_a(t, recs.data());
+    if (obk::TcSplit<OneLane>::overflow(recs.data(), G)) { rc = obk::ST_CAPACITY; break; }
+    for (int c = 0; c < G; ++c) team[c]->phase_b(recs.data());
+    for (int c = 0; c < G; ++c) cnt[c] = team[c]->phase_c(t, recs.data()) ? team[c]->ztot : -1;
+    for (int c = 0; c < G; ++c)
+      if (cnt[c] < 0) rc = obk::ST_CAPACITY;
+    for (int c = 0; c < G && rc == obk::ST_OK; ++c)
+      if (!team[c]->publish(t, cnt.data())) rc = obk::ST_CAPACITY;
+  }
+  if (rc == obk::ST_OK) g0.root(out[0], out[1]);
+  pts[0] = pts[1] = pts[2] = 0;
+  for (int c = 0; c < G; ++c) {
+    pts[0] += team[c]->R.st.upts;
+    pts[1] += team[c]->R.st.wpts;
+    pts[2] += team[c]->R.st.zpts;
+    delete team[c];
+  }
+  return rc;
+}
+
 // full = 1: the records of every level kept by the forward pass; 0: checkpoints and a
 // recomputed segment per checkpoint
 extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad, int full) {

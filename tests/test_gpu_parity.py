@@ -489,3 +489,41 @@ def test_split_factor_gives_the_same_bits(tmp_path):
     assert np.all(res[0][-600:] == 0)
     for x in res[1:]:
         assert np.array_equal(x.view(np.int64), res[0].view(np.int64))
+
+
+_WIDE_MODE_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %(root)r)
+import workloads as W, paper_1110_2477_gb300 as ob
+t = W.concat(W.random_table(12, 9393, N_lo=40, N_hi=700, payoffs=(W.CALL, W.SPREAD), k_hi=0.05),
+             W.make(K=95.0, K2=105.0, k=0.01, N=1500, payoff=W.SPREAD),
+             W.make(k=0.02, N=900, sigma=0.1, payoff=W.CALL), W.make(k=0.005, N=300))
+out, st = ob.price(t, wide=True)
+ref, rst = ob.price(t)
+torch.cuda.synchronize()
+np.save(%(npy)r, np.concatenate([out.cpu().numpy().reshape(-1), ref.cpu().numpy().reshape(-1),
+                                  st.cpu().numpy().astype(np.float64), rst.cpu().numpy().astype(np.float64)]))
+"""
+
+
+def test_wide_node_split_gives_the_same_bits(tmp_path):
+    """The whole-GPU form with nodes split over the CTAs at the quantiles of the merged points
+    (OB_WIDE_SPLIT_X=-1: every level of every call and spread), with the default choice (calls
+    and spreads with k > 6 sigma sqrt(dt), on levels whose largest node outgrows a share), and
+    with none (shares of whole nodes) prices bit for bit as the batched form."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    n = 15
+    for x in ("-1", "6", "1e9"):
+        npy = str(tmp_path / ("w%s.npy" % x))
+        env = dict(os.environ, OB_WIDE_SPLIT_X=x)
+        r = subprocess.run([sys.executable, "-c", _WIDE_MODE_CHILD % {"root": root, "npy": npy}], env=env,
+                           capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stderr[-2000:]
+        a = np.load(npy)
+        wide, batched = a[:2 * n], a[2 * n:4 * n]
+        st, rst = a[4 * n:5 * n], a[5 * n:]
+        assert np.all(st == 0) and np.all(rst == 0), x
+        assert np.array_equal(wide.view(np.int64), batched.view(np.int64)), x

@@ -128,6 +128,28 @@ def test_trapezoid_rounds_are_bitwise_equal(G, Dmax, light, colp):
                 assert rounds[0] == 0
 
 
+@pytest.mark.parametrize("G", [1, 2, 3, 5, 16, 61])
+def test_nodes_split_over_teams_are_bitwise_equal(G):
+    """Every level with its nodes split over G teams at the quantiles of the merged successor
+    points (TcSplit: shares that begin and end inside nodes, the owner carry recomputed, the
+    running minima combined across shares, the neighbouring shares' boundary points for the
+    pieces that cross a boundary), with as many teams as points at the top of the tree (empty
+    shares), give the bits and the point counts of the single-team run."""
+    t = W.concat(_table(), W.make(K=95.0, K2=105.0, k=0.03, N=120, sigma=0.1, payoff=W.SPREAD),
+                 W.make(k=0.04, N=110, sigma=0.1, payoff=W.CALL))
+    P = ctypes.c_void_p
+    for i in range(len(t)):
+        rc1, out1, pts1 = _price(t[i])
+        a = _rec(t[i])
+        out2 = np.zeros(2)
+        pts2 = np.zeros(3, np.int64)
+        rc2 = _lib().hp_price_nsplit(a.ctypes.data_as(P), G, out2.ctypes.data_as(P), pts2.ctypes.data_as(P))
+        assert rc1 == rc2, (i, rc1, rc2)
+        if rc1 == 0:
+            assert np.array_equal(out1.view(np.int64), out2.view(np.int64)), (i, out1, out2)
+            assert np.array_equal(pts1, pts2), (i, pts1, pts2)
+
+
 @pytest.mark.parametrize("payoff", [W.PUT, W.CALL, W.SPREAD])
 def test_host_adjoint_matches_oracle_gradient(payoff):
     """The adjoint (line adjoints per piece) against the oracle's gradient on 40 options of
