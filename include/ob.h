@@ -177,11 +177,17 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
  * level the CTAs split the nodes by their merged successor breakpoints (whole
  * nodes, G equal shares), run the same element-wise passes as ob_price_ask_bid
  * into private scratch, then place their breakpoints in the shared level; two
- * grid barriers per level.  One cooperative launch per call.  Results are bitwise
- * equal to ob_price_ask_bid.  Arguments, ownership and statuses as
- * ob_price_ask_bid; a barrier wait longer than 10 s gives OB_ERR_TIMEOUT for the
- * option in progress and every later option of the call; a level that outgrows
- * the shared scratch (1/8 of the pool) gives OB_ERR_CAPACITY. */
+ * grid barriers per level.  Puts, and calls with k <= sigma sqrt(T/N), take their
+ * light levels (at most 128 points per CTA) eight at a time: each CTA works on a
+ * window of columns with a halo of its neighbour's (Section 4.2's blocks of
+ * levels), two barriers per round.  Calls and spreads with k > 6 sigma sqrt(T/N)
+ * split their largest nodes over the CTAs on the levels where a node outgrows a
+ * share (four barriers per level).  Three cooperative launches per call, one per
+ * kind of option.  Results are bitwise equal to ob_price_ask_bid.  Arguments,
+ * ownership and statuses as ob_price_ask_bid; a barrier wait longer than 10 s
+ * gives OB_ERR_TIMEOUT for the option in progress and every later option of its
+ * launch; a level that outgrows the shared scratch (1/8 of the pool) gives
+ * OB_ERR_CAPACITY. */
 int ob_price_ask_bid_wide(const ob_option_t* params, int64_t n_options, double* out,
                           int32_t* status, void* stream);
 
