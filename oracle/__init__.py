@@ -71,13 +71,14 @@ def _load():
             lib.or_initial_hedge.argtypes = [P, i64, P, P, i32]
             lib.or_pl_rebalance.argtypes = [P, P, i32, d, d, d, d, d, P, P]
             lib.or_root_objective.argtypes = [P, i32, P, i32, P]
+            lib.or_hedge_path.argtypes = [P, i64, P, i64, P, P, P, i32]
             lib.or_alg1_tc.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_crr.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_rounds.argtypes = [i32, i32, i32, P, i32]
             for f in (lib.or_price_tc, lib.or_tc_stats, lib.or_greeks_tc, lib.or_price_crr,
                       lib.or_pl_envelope, lib.or_pl_restrict, lib.or_pl_eval, lib.or_node_step,
                       lib.or_alg1_tc, lib.or_alg1_crr, lib.or_alg1_rounds, lib.or_initial_hedge,
-                      lib.or_pl_rebalance, lib.or_root_objective):
+                      lib.or_pl_rebalance, lib.or_root_objective, lib.or_hedge_path):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -154,6 +155,23 @@ def initial_hedge(opts, nthreads: int = 1):
     st = np.empty(n, np.int32)
     _load().or_initial_hedge(_ptr(a), n, _ptr(out), _ptr(st), _threads(nthreads))
     return out, st
+
+
+def hedge_path(opts, moves, nthreads: int = 1):
+    """The hedge along a path of each option: moves[n, stride] (1 up, 0 down; option i uses
+    its first N_i), returns (hold[n, stride + 1, 2] = seller's and buyer's stock holdings after
+    rebalancing at t = 0..N_i, NaN beyond and after the buyer stops; stop[n] = the buyer's
+    stopping time or -1; status[n])."""
+    a = _as_table(opts)
+    n = a.shape[0]
+    mv = np.ascontiguousarray(moves, np.int8).reshape(n, -1)
+    stride = mv.shape[1]
+    hold = np.empty((n, stride + 1, 2), np.float64)
+    stop = np.empty(n, np.int32)
+    st = np.empty(n, np.int32)
+    _load().or_hedge_path(_ptr(a), n, _ptr(mv), stride, _ptr(hold), _ptr(stop), _ptr(st),
+                          _threads(nthreads))
+    return hold, stop, st
 
 
 def root_objective(opt, party: int, ys):

@@ -865,6 +865,73 @@ int initial_hedge(const Model<double>& m, double* out) {
   return OR_OK;
 }
 
+// The hedge along one path of the tree: the same rebalancing at every node the path visits.
+// moves[t] = 1 for an up move from level t to t+1, 0 for a down move (t < N); the path's node
+// at level t is j_t = the number of up moves before t.  hold[2t] is the seller's stock holding
+// after rebalancing at t (from the previous holding, 0 before t = 0; to the y' attaining
+// v_t(y) = inf_y' [w_t(y')/r + theta_t(y' - y)]), hold[2t+1] the buyer's; the buyer stops at the
+// first t where u_t(y) < v_t(y) for the holding y he arrives with (*stop = t, NaN from there
+// on; -1 if he never does).  The functions w_t of the path's nodes are kept during the
+// induction of price_tc (built the same way).
+int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* stop) {
+  const int N = m.N;
+  std::vector<int> jt(N + 1, 0);
+  for (int t = 1; t <= N; ++t) jt[t] = jt[t - 1] + (moves[t - 1] ? 1 : 0);
+  std::vector<PL<double>> zs(N + 2), zb(N + 2), Fs(N + 1), Fb(N + 1);
+  for (int j = 0; j <= N + 1; ++j) {
+    const double S = stock(m, N + 1, j);
+    const double Sa = (1.0 + m.k) * S, Sb = (1.0 - m.k) * S;
+    zs[j] = pl_expense(0.0, 0.0, Sa, Sb, false);
+    zb[j] = pl_expense(0.0, 0.0, Sa, Sb, true);
+  }
+  for (int t = N; t >= 0; --t) {
+    for (int j = 0; j <= t; ++j) {
+      const double S = stock(m, t, j);
+      const double kt = (t == 0) ? 0.0 : m.k;
+      const double Sa = (1.0 + kt) * S, Sb = (1.0 - kt) * S;
+      double xi, zeta;
+      payoff_at(m, S, xi, zeta);
+      if (j == jt[t]) {  // the path's node: keep w / r
+        Fs[t] = pl_div(pl_envelope(zs[j + 1], zs[j], true), m.r);
+        Fb[t] = pl_div(pl_envelope(zb[j + 1], zb[j], true), m.r);
+      }
+      PL<double> ns, nb;
+      int rc = node_step(zs[j + 1], zs[j], m.r, Sa, Sb, xi, zeta, false, ns);
+      if (rc) return rc;
+      rc = node_step(zb[j + 1], zb[j], m.r, Sa, Sb, xi, zeta, true, nb);
+      if (rc) return rc;
+      zs[j] = std::move(ns);
+      zb[j] = std::move(nb);
+    }
+  }
+  double ys = 0.0, yb = 0.0;
+  *stop = -1;
+  for (int t = 0; t <= N; ++t) {
+    const double S = stock(m, t, jt[t]);
+    const double kt = (t == 0) ? 0.0 : m.k;
+    const double Sa = (1.0 + kt) * S, Sb = (1.0 - kt) * S;
+    double y = 0.0, v = 0.0;
+    int rc = pl_rebalance(Fs[t], Sa, Sb, ys, y, v);
+    if (rc) return rc;
+    hold[2 * t] = ys = y;
+    if (*stop >= 0) {
+      hold[2 * t + 1] = NAN;
+      continue;
+    }
+    if ((rc = pl_rebalance(Fb[t], Sa, Sb, yb, y, v))) return rc;
+    double xi, zeta;
+    payoff_at(m, S, xi, zeta);
+    const double u = pl_eval(pl_expense(xi, zeta, Sa, Sb, true), yb);
+    if (u < v) {
+      *stop = t;
+      hold[2 * t + 1] = NAN;
+    } else {
+      hold[2 * t + 1] = yb = y;
+    }
+  }
+  return OR_OK;
+}
+
 // ---------------------------------------------------------------- Algorithm 1 (Section 4.2)
 // The paper's parallel scheme for one option on p threads, driving the node steps above
 // (price_tc's and price_crr's arithmetic, node for node, so the results are bitwise the
@@ -1246,6 +1313,31 @@ int or_pl_rebalance(const double* y, const double* f, int m, double sL, double s
   if (m < 1) return OR_ERR_ARG;
   PL<double> F = pl_from<double>(y, f, m, sL, sR);
   return pl_rebalance(F, Sa, Sb, y0, *yopt, *vopt);
+}
+
+
+// The hedge along a path for each option (hedge_path): moves + i * stride holds option i's N
+// moves, hold + 2 * (stride + 1) * i its 2 (N + 1) holdings, stop[i] the buyer's stopping time.
+int or_hedge_path(const or_option_t* opts, int64_t n, const int8_t* moves, int64_t stride,
+                  double* hold, int32_t* stop, int32_t* status, int nthreads) {
+  parallel_for(n, nthreads, [&](int64_t i) {
+    const or_option_t& o = opts[i];
+    double* h = hold + 2 * (stride + 1) * i;
+    int rc = check_option(o);
+    if (rc == OR_OK && o.N > stride) rc = OR_ERR_ARG;
+    int st = -1;
+    if (rc == OR_OK) {
+      Model<double> m = make_model<double>(o, o.S0, o.K, o.sigma, o.R, o.T, o.k);
+      rc = hedge_path(m, moves + stride * i, h, &st);
+    }
+    if (rc)
+      for (int64_t k = 0; k < 2 * (stride + 1); ++k) h[k] = NAN;
+    else
+      for (int64_t k = 2 * ((int64_t)o.N + 1); k < 2 * (stride + 1); ++k) h[k] = NAN;
+    stop[i] = rc ? -1 : st;
+    if (status) status[i] = rc;
+  });
+  return OR_OK;
 }
 
 }  // extern "C"

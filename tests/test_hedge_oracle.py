@@ -119,3 +119,80 @@ def test_rebalance_against_grid_search():
         assert abs(vs - obj.min()) <= 1e-12 * max(1.0, abs(vs)), trial
         at = F(np.array([ys]))[0] + (Sa if ys >= y0 else Sb) * (ys - y0)
         assert abs(at - vs) <= 1e-12 * max(1.0, abs(vs)), trial
+
+
+def _crr_tree(o):
+    """Textbook American CRR values V[t][j] for t <= N (plain numpy), the stock prices, the
+    exercise values and the continuation values."""
+    N = int(o["N"])
+    dt = o["T"] / N
+    u = np.exp(o["sigma"] * np.sqrt(dt))
+    d = 1.0 / u
+    r = np.exp(o["R"] * dt)
+    p = (r - d) / (u - d)
+
+    def payoff(S):
+        if o["payoff"] == W.PUT:
+            return o["K"] - S
+        if o["payoff"] == W.CALL:
+            return S - o["K"]
+        return np.maximum(S - o["K"], 0.0) - np.maximum(S - o["K2"], 0.0)
+
+    S = [o["S0"] * u ** (2 * np.arange(t + 1) - t) for t in range(N + 2)]
+    V = [None] * (N + 2)
+    cont = [None] * (N + 1)
+    V[N + 1] = np.zeros(N + 2)
+    V[N] = np.maximum(payoff(S[N]), 0.0)
+    cont[N] = np.zeros(N + 1)
+    for t in range(N - 1, -1, -1):
+        cont[t] = (p * V[t + 1][1:] + (1 - p) * V[t + 1][:-1]) / r
+        V[t] = np.maximum(payoff(S[t]), cont[t])
+    return S, V, cont, [payoff(S[t]) for t in range(N + 1)]
+
+
+@pytest.mark.parametrize("payoff", [W.PUT, W.CALL, W.SPREAD])
+def test_no_costs_path_hedge_is_crr_delta_and_exercise_boundary(payoff):
+    """Without costs the hedge along any path is the CRR delta of the path's node at every
+    step (the seller's; the buyer's is its negative), and the buyer stops at the first node of
+    the path where exercise beats continuation."""
+    rng = np.random.default_rng(91 + payoff)
+    for _ in range(8):
+        N = int(rng.integers(2, 90))
+        o = W.make(S0=float(rng.uniform(70, 130)), K=100.0, K2=110.0, sigma=float(rng.uniform(0.1, 0.5)),
+                   R=float(rng.uniform(0.0, 0.1)), T=float(rng.uniform(0.1, 2.0)), k=0.0, N=N,
+                   payoff=payoff)
+        mv = rng.integers(0, 2, (1, N)).astype(np.int8)
+        hold, stop, st = oracle.hedge_path(o, mv)
+        assert st[0] == 0
+        S, V, cont, ex = _crr_tree(o[0])
+        j = 0
+        want_stop = -1
+        for t in range(N + 1):
+            delta = (V[t + 1][j + 1] - V[t + 1][j]) / (S[t + 1][j + 1] - S[t + 1][j])
+            scale = max(1.0, abs(delta))
+            assert abs(hold[0, t, 0] - delta) <= 1e-9 * scale, (t, hold[0, t], delta)
+            gap = ex[t][j] - cont[t][j]
+            if want_stop < 0:
+                if abs(gap) <= 1e-9 * max(1.0, abs(cont[t][j])):
+                    break  # a tie between exercise and continuation: either choice is optimal
+                if gap > 0:
+                    want_stop = t
+                else:
+                    assert abs(hold[0, t, 1] + delta) <= 1e-9 * scale, (t, hold[0, t], delta)
+            if t < N:
+                j += int(mv[0, t])
+        else:
+            assert stop[0] == want_stop, (stop[0], want_stop)
+
+
+def test_path_hedge_starts_with_the_root_hedge():
+    t = W.random_table(20, 6060, N_lo=2, N_hi=120)
+    mv = np.random.default_rng(3).integers(0, 2, (len(t), int(t["N"].max()))).astype(np.int8)
+    hold, stop, st = oracle.hedge_path(t, mv, nthreads=4)
+    h0, st0 = oracle.initial_hedge(t, nthreads=4)
+    assert np.array_equal(st, st0)
+    ok = st == 0
+    assert np.array_equal(hold[ok, 0, 0], h0[ok, 0])
+    buyer_at_root = np.where(stop[ok] == 0, np.nan, h0[ok, 1])
+    assert np.array_equal(hold[ok, 0, 1], buyer_at_root, equal_nan=True)
+    assert np.all((stop[ok] == 0) == (h0[ok, 3] == 1.0))
