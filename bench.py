@@ -17,7 +17,8 @@ timed region sets the job time.
 Other workloads (--workload): small (48 options, for profiler captures), crr
 (65536 CRR puts at N = 2048 and one put at N = 20000), paper (18 paper-scale
 single options, one per launch on the whole GPU), greeks (1024 puts, prices
-and the 12 derivatives; --options n for a smaller case).
+and the 12 derivatives; --options n for a smaller case), path (the same puts,
+the hedge along one random path each).
 """
 import argparse
 import json
@@ -111,8 +112,8 @@ def parse():
                     help="skip the one-warp-per-option comparison kernel (for profiler captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default team width")
     ap.add_argument("--options", type=int, default=1024,
-                    help="greeks workload: the first n of the 1024 puts (smaller for profiling)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr", "paper", "greeks"],
+                    help="greeks and path workloads: the first n of the 1024 puts (smaller for profiling)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "small", "crr", "paper", "greeks", "path"],
                     help="batched: the 4096-option batch (the reported metric); small: 48 options "
                          "with N in [200, 600] (seed 321), for profiler captures")
     return ap.parse_args()
@@ -551,6 +552,93 @@ def run_greeks(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_path(args, rank, world, local):
+    """The hedge along a path: the 1024 puts of the Greeks workload (N = 1000, seed 4), one
+    random path per option (seed 8), prices plus both parties' holdings at every node of the
+    path and the buyer's stopping level in one ob_hedge_path call per step; options/s against
+    the pricing call on the same options."""
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    dev = torch.device("cuda", local)
+    table = W.greeks_puts()[:args.options]
+    n = len(table)
+    S = int(table["N"].max())
+    params = ob.to_device(table, dev)
+    moves = torch.as_tensor(np.random.default_rng(8).integers(0, 2, (n, S)).astype(np.int8)).to(dev)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    hold = torch.empty((n, S + 1, 2), dtype=torch.float64, device=dev)
+    stop = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ob.ob_hedge_path(params, n, moves, S, out, hold, stop, st, stream)
+    torch.cuda.synchronize(dev)
+    assert int((st != 0).sum().item()) == 0
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    sampler.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ob.ob_hedge_path(params, n, moves, S, out, hold, stop, st, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    job_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ob.ob_price_ask_bid(params, n, out, st, stream)
+    pa.record(stream)
+    ob.ob_price_ask_bid(params, n, out, st, stream)
+    pb.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_s = pa.elapsed_time(pb) / 1e3
+    u_points = ob.ob_get_stats()["u_points"]
+    peak = measure_fp64_peak(local)
+    if rank != 0:
+        return
+    value = world * n * args.steps / job_s
+    p_flops = 1.0 * FLOPS_PER_MERGED_POINT * float(u_points)
+    p_achieved = p_flops / (job_s / args.steps) / 1e12
+    line = {
+        "metric": "options/s with the hedge along a path (ask, bid, holdings, stopping level), FP64",
+        "value": value, "unit": "options/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * job_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%d American puts, N=1000, batched-table distributions (seed 4), one "
+                               "random path each (seed 8)" % n,
+                   "node_updates_per_step": int(np.sum(W.node_updates(table))),
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "plain": {"value": n / plain_s, "unit": "options/s", "call": "ob_price_ask_bid"},
+        "path_over_plain_time": (job_s / args.steps) / plain_s,
+        "gpu_launches": args.steps, "step_ms": step_ms, "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": p_achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": p_achieved / peak["tflops"], "traffic": None,
+                     "note": "algorithmic FP64 flops = %d per merged successor breakpoint of the "
+                             "induction (U of the pricing pass, counted by the last pricing call); "
+                             "the copies of the path's w and the rebalancing sweep are not counted; "
+                             "peak = ob_fp64_peak" % FLOPS_PER_MERGED_POINT,
+                     "peak_measurement": peak},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        sample = table[:cores]
+        mv = moves[:cores].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.hedge_path(sample, mv, nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(sample) / dt, "unit": "options/s", "cores": cores,
+                                "kind": "oracle", "sample": "the first %d options and paths, %.1f s" %
+                                (len(sample), dt)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -570,6 +658,9 @@ def main():
         return
     if args.workload == "paper":
         run_paper(args, rank, world, local)
+        return
+    if args.workload == "path":
+        run_path(args, rank, world, local)
         return
     if args.workload == "greeks":
         run_greeks(args, rank, world, local)

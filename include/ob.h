@@ -114,6 +114,40 @@ int ob_price_ask_bid(const ob_option_t* params, int64_t n_options, double* out, 
 int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double* out, int32_t* status,
                            double* hedge, void* stream);
 
+/* The hedge along one path of the tree per option (Section 3, the rebalancing of
+ * ob_price_ask_bid_hedge made at every node the path visits): at level t the
+ * hedger moves its stock holding from the one it arrived with (no stock before
+ * t = 0) to the y' attaining v_t(y) = min over y' of w_t(y')/r + theta_t(y' - y),
+ * theta_t buying at S^a = (1+k) S and selling at S^b = (1-k) S (k = 0 at t = 0);
+ * the rightmost y' among equal minima.  The buyer stops at the first level
+ * where exercising with the holding it arrived with costs less than keeping
+ * the hedge, u_t(y) < v_t(y) (Eq. 6's expense for the buyer).
+ *   params  DEVICE pointer, n_options options (as for ob_price_ask_bid).
+ *   moves   DEVICE pointer, n_options * stride int8: moves[i*stride + t] for
+ *           t < N_i is the move from level t to t+1 (non-zero up, 0 down);
+ *           the path's node at level t is the number of up moves before t.
+ *   stride  row length of moves, 1 <= stride; every N_i <= stride (an option
+ *           with N_i > stride gets OB_ERR_ARG in status).
+ *   out     DEVICE pointer, 2*n_options doubles: ask and bid, equal bit for bit
+ *           to ob_price_ask_bid's.
+ *   hold    DEVICE pointer, n_options * (stride+1) * 2 doubles:
+ *           hold[(i*(stride+1) + t)*2]     the seller's holding after
+ *                                          rebalancing at level t (t <= N_i),
+ *           hold[(i*(stride+1) + t)*2 + 1] the buyer's, NaN from its stopping
+ *                                          level on;
+ *           NaN for t > N_i and for an option whose status is not OB_OK.
+ *   stop    DEVICE pointer, n_options int32: the buyer's stopping level, -1 if
+ *           it never stops (or the status is not OB_OK).
+ *   status  DEVICE pointer or NULL, n_options int32 (as for ob_price_ask_bid).
+ * One 16-warp CTA team per option, up to one per SM, with 128 MiB of scratch
+ * each: three quarters for the level arrays, one quarter for w_t of the path's
+ * nodes.  No follow-up launch: an option that outgrows either part gets
+ * OB_ERR_CAPACITY.  Same pool, serialisation and call ordering as
+ * ob_price_ask_bid.  Returns OB_ERR_ARG on a NULL pointer (status may be NULL)
+ * or stride outside [1, 2^26]. */
+int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* moves, int64_t stride,
+                  double* out, double* hold, int32_t* stop, int32_t* status, void* stream);
+
 /* The plain form of the same computation: one warp per option, options taken
  * in index order with a static assignment, no queue and no retry (an option
  * that outgrows its warp's scratch gets OB_ERR_CAPACITY).  Arguments and

@@ -870,7 +870,7 @@ int initial_hedge(const Model<double>& m, double* out) {
 // at level t is j_t = the number of up moves before t.  hold[2t] is the seller's stock holding
 // after rebalancing at t (from the previous holding, 0 before t = 0; to the y' attaining
 // v_t(y) = inf_y' [w_t(y')/r + theta_t(y' - y)]), hold[2t+1] the buyer's; the buyer stops at the
-// first t where u_t(y) < v_t(y) for the holding y he arrives with (*stop = t, NaN from there
+// first t where u_t(y) < v_t(y) for the holding y it arrives with (*stop = t, NaN from there
 // on; -1 if he never does).  The functions w_t of the path's nodes are kept during the
 // induction of price_tc (built the same way).
 int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* stop) {

@@ -29,7 +29,8 @@ OB_OK, OB_ERR_ARG, OB_ERR_ARBITRAGE, OB_ERR_CAPACITY, OB_ERR_TIMEOUT, OB_ERR_CUD
 EXPORTS = ("ob_price_ask_bid", "ob_price_ask_bid_plain", "ob_crr_american", "ob_price_ask_bid_host",
            "ob_get_stats", "ob_release", "ob_strerror", "ob_last_cuda_error",
            "ob_price_ask_bid_noalloc", "ob_greeks", "ob_configure", "ob_autotune",
-           "ob_price_ask_bid_wide", "ob_fp64_peak", "ob_crr_american_wide", "ob_price_ask_bid_hedge")
+           "ob_price_ask_bid_wide", "ob_fp64_peak", "ob_crr_american_wide", "ob_price_ask_bid_hedge",
+           "ob_hedge_path")
 
 
 class ObStats(ctypes.Structure):
@@ -64,6 +65,8 @@ def load():
         lib.ob_greeks.restype = ctypes.c_int
         lib.ob_price_ask_bid_hedge.argtypes = [P, i64, P, P, P, P]
         lib.ob_price_ask_bid_hedge.restype = ctypes.c_int
+        lib.ob_hedge_path.argtypes = [P, i64, P, i64, P, P, P, P, P]
+        lib.ob_hedge_path.restype = ctypes.c_int
         lib.ob_price_ask_bid_host.argtypes = [P, i64, P, P]
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
         lib.ob_get_stats.argtypes = [ctypes.POINTER(ObStats)]
@@ -126,6 +129,14 @@ def ob_price_ask_bid_hedge(params, n, out, status, hedge, stream=None):
     rebalancing at t = 0, buyer's, immediate exercise sets the ask, buyer exercises at once)."""
     _check(load().ob_price_ask_bid_hedge(_ptr(params), int(n), _ptr(out), _ptr(status), _ptr(hedge),
                                          _stream(stream)))
+
+
+def ob_hedge_path(params, n, moves, stride, out, hold, stop, status=None, stream=None):
+    """The hedge along one path per option: moves[n, stride] int8 (non-zero up), out[n, 2] ask/bid,
+    hold[n, stride + 1, 2] the seller's and buyer's holdings after rebalancing at each level,
+    stop[n] the buyer's stopping level (-1: never)."""
+    _check(load().ob_hedge_path(_ptr(params), int(n), _ptr(moves), int(stride), _ptr(out), _ptr(hold),
+                                _ptr(stop), _ptr(status), _stream(stream)))
 
 
 def ob_price_ask_bid_plain(params, n, out, status=None, stream=None):
@@ -239,6 +250,26 @@ def hedge(table, stream=None):
     st = torch.empty(n, dtype=torch.int32, device=dev.device)
     ob_price_ask_bid_hedge(dev, n, out, st, hg, stream)
     return out, hg, st
+
+
+def hedge_path(table, moves, stream=None):
+    """The hedge along the paths moves[n, stride] (int8, non-zero up) of a workloads table:
+    (out[n,2], hold[n,stride+1,2], stop[n], status[n]) tensors."""
+    import torch
+    n = int(np.asarray(table).shape[0])
+    dev = to_device(table)
+    mv = torch.as_tensor(np.ascontiguousarray(moves, dtype=np.int8)).to(dev.device)
+    if mv.dim() != 2 or mv.shape[0] != n:
+        raise ValueError("moves must be [n_options, stride]")
+    stride = max(int(mv.shape[1]), 1)
+    if mv.shape[1] == 0:
+        mv = torch.zeros((n, 1), dtype=torch.int8, device=dev.device)
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev.device)
+    hold = torch.empty((n, stride + 1, 2), dtype=torch.float64, device=dev.device)
+    stop = torch.empty(n, dtype=torch.int32, device=dev.device)
+    st = torch.empty(n, dtype=torch.int32, device=dev.device)
+    ob_hedge_path(dev, n, mv, stride, out, hold, stop, st, stream)
+    return out, hold, stop, st
 
 
 def crr(table, stream=None, wide=False):

@@ -800,6 +800,31 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
   return co.end();
 }
 
+int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* moves, int64_t stride,
+                  double* out, double* hold, int32_t* stop, int32_t* status, void* stream) {
+  if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
+  if (n_options == 0) return OB_OK;
+  if (!params || !out || !hold || !stop || !moves || stride < 1 || stride > (1 << 26)) return OB_ERR_ARG;
+  const int n = (int)n_options;
+  DevPool* P = nullptr;
+  int dev = 0;
+  int rc = pool_get(&P, &dev);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_call_mu[dev]);
+  const int workers = n < P->sms ? n : P->sms;  // one 16-warp CTA team per SM
+  if ((rc = pool_reserve(P, 1, (size_t)workers * kGreeksSmBytes))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CallOrder co{P, s};
+  if ((rc = co.begin())) return rc;
+  size_t wbytes = P->arena_bytes / (size_t)workers;
+  if (wbytes > kGreeksSmBytes) wbytes = kGreeksSmBytes;
+  wbytes &= ~(size_t)255;
+  cudaError_t e = launch_path(workers, s, (const obk::Opt*)params, n, moves, (long long)stride, out, hold, stop,
+                              status, P->arena, wbytes);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return co.end();
+}
+
 int ob_price_ask_bid_host(const ob_option_t* params, int64_t n_options, double* out,
                           int32_t* status) {
   if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;

@@ -1,0 +1,113 @@
+"""The hedge along a path of the tree on the GPU (ob_hedge_path) against the oracle.
+
+  * prices: bitwise those of ob_price_ask_bid on the same records;
+  * holdings: the oracle's within 1e-9 (relative to max(1, |y|)) at every level of the path,
+    NaN in the same places (beyond N_i, and from the buyer's stopping level on);
+  * the buyer's stopping level: the oracle's;
+  * paths: random, all up, all down, alternating; rows longer than N_i; N = 1;
+  * an option with N_i > stride, and one that fails its checks, carry NaN and their status;
+  * the paper's option sizes (N = 1500) on a sample of paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(table, moves):
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    out, hold, stop, st = ob.hedge_path(table, moves)
+    ref_out, ref_st = ob.price(table)
+    torch.cuda.synchronize()
+    return (out.cpu().numpy(), hold.cpu().numpy(), stop.cpu().numpy(), st.cpu().numpy(),
+            ref_out.cpu().numpy(), ref_st.cpu().numpy())
+
+
+def _check(table, moves, nthreads=8):
+    out, hold, stop, st, ref_out, ref_st = _gpu(table, moves)
+    assert np.array_equal(st, ref_st)
+    assert np.array_equal(out.view(np.int64), ref_out.view(np.int64))
+    oh, ostop, ost = oracle.hedge_path(table, moves, nthreads=nthreads)
+    assert np.array_equal(st, ost)
+    ok = st == 0
+    assert np.array_equal(stop[ok], ostop[ok])
+    assert np.all(stop[~ok] == -1)
+    assert np.all(np.isnan(hold[~ok]))
+    g, o = hold[ok], oh[ok]
+    assert np.array_equal(np.isnan(g), np.isnan(o))
+    fin = ~np.isnan(o)
+    err = np.abs(g[fin] - o[fin]) / np.maximum(1.0, np.abs(o[fin]))
+    assert err.max(initial=0.0) <= 1e-9, err.max()
+    return out, hold, stop, st
+
+
+def test_random_paths_mixed_payoffs():
+    t = W.random_table(40, 7070, N_lo=2, N_hi=260)
+    rng = np.random.default_rng(17)
+    mv = rng.integers(0, 2, (len(t), int(t["N"].max()) + 3)).astype(np.int8)
+    _, hold, stop, _ = _check(t, mv)
+    assert np.any(stop >= 0)  # some buyers stop on their paths
+
+
+@pytest.mark.parametrize("kind", ["up", "down", "alternate"])
+def test_extreme_paths(kind):
+    t = W.concat(W.make(N=120, payoff=W.PUT, k=0.004), W.make(N=97, payoff=W.CALL, k=0.01, R=0.03),
+                 W.make(N=150, payoff=W.SPREAD, K2=110.0, k=0.002, sigma=0.3), W.make(N=1, k=0.01),
+                 W.make(N=64, payoff=W.PUT, k=0.0, S0=80.0))
+    S = int(t["N"].max())
+    if kind == "up":
+        mv = np.ones((len(t), S), np.int8)
+    elif kind == "down":
+        mv = np.zeros((len(t), S), np.int8)
+    else:
+        mv = np.tile(np.arange(S) % 2, (len(t), 1)).astype(np.int8)
+    _check(t, mv)
+
+
+def test_no_costs_holdings_are_the_oracle_crr_deltas():
+    t = W.random_table(24, 8181, N_lo=2, N_hi=200, k_zero=True)
+    mv = np.random.default_rng(5).integers(0, 2, (len(t), int(t["N"].max()))).astype(np.int8)
+    _check(t, mv)
+
+
+def test_short_rows_and_bad_options():
+    t = W.concat(W.make(N=50), W.make(N=30), W.make(N=40, sigma=-1.0), W.make(N=40))
+    mv = np.random.default_rng(9).integers(0, 2, (len(t), 40)).astype(np.int8)
+    out, hold, stop, st, ref_out, ref_st = _gpu(t, mv)
+    assert st[0] == -1 and np.all(np.isnan(out[0])) and np.all(np.isnan(hold[0])) and stop[0] == -1
+    assert st[2] == -1 and np.all(np.isnan(out[2])) and np.all(np.isnan(hold[2]))
+    assert st[1] == 0 and st[3] == 0
+    assert np.all(np.isnan(hold[1, 31:]))
+    oh, ostop, ost = oracle.hedge_path(t[[1, 3]], mv[[1, 3]])
+    for gi, oi in ((1, 0), (3, 1)):
+        assert np.array_equal(out[gi].view(np.int64), ref_out[gi].view(np.int64))
+        assert stop[gi] == ostop[oi]
+        g, o = hold[gi], oh[oi]
+        assert np.array_equal(np.isnan(g), np.isnan(o))
+        fin = ~np.isnan(o)
+        assert np.all(np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1.0, np.abs(o[fin])))
+
+
+def test_empty_batch():
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    p = torch.empty((0, 8), dtype=torch.float64, device="cuda")
+    mv = torch.zeros((0, 4), dtype=torch.int8, device="cuda")
+    out = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    hold = torch.empty((0, 5, 2), dtype=torch.float64, device="cuda")
+    stop = torch.empty(0, dtype=torch.int32, device="cuda")
+    ob.ob_hedge_path(p, 0, mv, 4, out, hold, stop)
+    torch.cuda.synchronize()
+
+
+def test_paper_size_sample():
+    t = W.concat(W.make(N=1500, payoff=W.PUT, k=0.005), W.make(N=1500, payoff=W.CALL, k=0.0025),
+                 W.make(N=1500, payoff=W.SPREAD, K2=110.0, k=0.005))
+    mv = np.random.default_rng(23).integers(0, 2, (len(t), 1500)).astype(np.int8)
+    _check(t, mv, nthreads=3)
