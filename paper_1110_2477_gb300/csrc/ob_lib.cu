@@ -819,8 +819,20 @@ int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* mo
   size_t wbytes = P->arena_bytes / (size_t)workers;
   if (wbytes > kGreeksSmBytes) wbytes = kGreeksSmBytes;
   wbytes &= ~(size_t)255;
-  cudaError_t e = launch_path(workers, s, (const obk::Opt*)params, n, moves, (long long)stride, out, hold, stop,
-                              status, P->arena, wbytes);
+  const obk::Opt* opts = (const obk::Opt*)params;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->ctl, 0, sizeof(int) * C_WORDS, s)) != cudaSuccess) return cuda_fail(e);
+  const int* order = nullptr;  // the costliest options first, as in the batched form
+  if (n <= kSortMax) {
+    int npad = 1;
+    while (npad < n) npad <<= 1;
+    k_order<<<1, 1024, sizeof(unsigned long long) * npad, s>>>(opts, n, npad, P->order, P->ctl, workers * 16,
+                                                                workers, 0.0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    order = P->order;
+  }
+  e = launch_path(workers, s, opts, n, order, &P->ctl[C_HEAVY_HEAD], moves, (long long)stride, out, hold, stop,
+                  status, P->arena, wbytes);
   if (e != cudaSuccess) return cuda_fail(e);
   return co.end();
 }

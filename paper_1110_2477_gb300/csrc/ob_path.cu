@@ -171,15 +171,25 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
   return obk::ST_OK;
 }
 
-// One 16-warp CTA team per option, options i = blockIdx.x, blockIdx.x + gridDim.x, ...
+// One 16-warp CTA team per option, taken from a device queue: position q = atomicAdd(head)
+// of order (the costliest first; index order when order is null).
 __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__ opts, int n,
+                                                    const int* __restrict__ order, int* head,
                                                     const int8_t* __restrict__ moves, long long stride,
                                                     double* out, double* hold, int* stop, int* status,
                                                     char* arena, size_t cta_bytes) {
   __shared__ long long tbuf[obk::BlockTeam<16>::BUF];
+  __shared__ int s_next;
   obk::BlockTeam<16> bt{tbuf};
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int q = atomicAdd(head, 1);
+      s_next = q < n ? (order ? order[q] : q) : -1;
+    }
+    __syncthreads();
+    const int i = s_next;
+    if (i < 0) break;
     const obk::Opt o = opts[i];
     double* h = hold + 2 * (stride + 1) * (long long)i;
     double ask, bid;
@@ -202,10 +212,10 @@ __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__
   }
 }
 
-cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int8_t* moves,
-                        long long stride, double* out, double* hold, int* stop, int* status, char* arena,
-                        size_t cta_bytes) {
-  k_tc_path<<<grid, 512, 0, s>>>(opts, n, moves, stride, out, hold, stop, status, arena, cta_bytes);
+cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* order, int* head,
+                        const int8_t* moves, long long stride, double* out, double* hold, int* stop, int* status,
+                        char* arena, size_t cta_bytes) {
+  k_tc_path<<<grid, 512, 0, s>>>(opts, n, order, head, moves, stride, out, hold, stop, status, arena, cta_bytes);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
     NaN in the same places (beyond N_i, and from the buyer's stopping level on);
   * the buyer's stopping level: the oracle's;
   * paths: random, all up, all down, alternating; rows longer than N_i; N = 1;
+  * a batch above the cost-ordering limit (8192 options: taken in index order);
   * an option with N_i > stride, and one that fails its checks, carry NaN and their status;
   * the paper's option sizes (N = 1500) on a sample of paths.
 """
@@ -91,6 +92,12 @@ def test_short_rows_and_bad_options():
         assert np.array_equal(np.isnan(g), np.isnan(o))
         fin = ~np.isnan(o)
         assert np.all(np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1.0, np.abs(o[fin])))
+
+
+def test_batch_above_the_ordering_limit():
+    t = W.random_table(8200, 9090, N_lo=1, N_hi=6)
+    mv = np.random.default_rng(31).integers(0, 2, (len(t), 6)).astype(np.int8)
+    _check(t, mv)
 
 
 def test_empty_batch():
