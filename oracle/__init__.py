@@ -71,7 +71,7 @@ def _load():
             lib.or_initial_hedge.argtypes = [P, i64, P, P, i32]
             lib.or_pl_rebalance.argtypes = [P, P, i32, d, d, d, d, d, P, P]
             lib.or_root_objective.argtypes = [P, i32, P, i32, P]
-            lib.or_hedge_path.argtypes = [P, i64, P, i64, P, P, P, i32]
+            lib.or_hedge_path.argtypes = [P, i64, P, i64, P, P, P, P, i32]
             lib.or_alg1_tc.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_crr.argtypes = [P, i32, i32, P, P, P]
             lib.or_alg1_rounds.argtypes = [i32, i32, i32, P, i32]
@@ -160,18 +160,21 @@ def initial_hedge(opts, nthreads: int = 1):
 def hedge_path(opts, moves, nthreads: int = 1):
     """The hedge along a path of each option: moves[n, stride] (1 up, 0 down; option i uses
     its first N_i), returns (hold[n, stride + 1, 2] = seller's and buyer's stock holdings after
-    rebalancing at t = 0..N_i, NaN beyond and after the buyer stops; stop[n] = the buyer's
-    stopping time or -1; status[n])."""
+    rebalancing at t = 0..N_i, NaN beyond and after the buyer stops; cash[n, stride + 1, 2] =
+    their cash after rebalancing, in time-t money, of the self-financing portfolios that start
+    from the ask and from minus the bid, NaN where hold is; stop[n] = the buyer's stopping time
+    or -1; status[n])."""
     a = _as_table(opts)
     n = a.shape[0]
     mv = np.ascontiguousarray(moves, np.int8).reshape(n, -1)
     stride = mv.shape[1]
     hold = np.empty((n, stride + 1, 2), np.float64)
+    cash = np.empty((n, stride + 1, 2), np.float64)
     stop = np.empty(n, np.int32)
     st = np.empty(n, np.int32)
-    _load().or_hedge_path(_ptr(a), n, _ptr(mv), stride, _ptr(hold), _ptr(stop), _ptr(st),
+    _load().or_hedge_path(_ptr(a), n, _ptr(mv), stride, _ptr(hold), _ptr(cash), _ptr(stop), _ptr(st),
                           _threads(nthreads))
-    return hold, stop, st
+    return hold, cash, stop, st
 
 
 def root_objective(opt, party: int, ys):

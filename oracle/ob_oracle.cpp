@@ -872,8 +872,11 @@ int initial_hedge(const Model<double>& m, double* out) {
 // v_t(y) = inf_y' [w_t(y')/r + theta_t(y' - y)]), hold[2t+1] the buyer's; the buyer stops at the
 // first t where u_t(y) < v_t(y) for the holding y it arrives with (*stop = t, NaN from there
 // on; -1 if he never does).  The functions w_t of the path's nodes are kept during the
-// induction of price_tc (built the same way).
-int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* stop) {
+// induction of price_tc (built the same way).  cash[2t] and cash[2t+1] are the parties' cash
+// after rebalancing at t, in time-t money, of the self-financing portfolios that start at
+// t = 0 with no stock and the ask (seller) or minus the bid (buyer, who borrows it to buy the
+// option): x_t = r x_{t-1} - theta_t(y_t - y_{t-1}), x_{-1} r = ask or -bid.
+int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, double* cash, int* stop) {
   const int N = m.N;
   std::vector<int> jt(N + 1, 0);
   for (int t = 1; t <= N; ++t) jt[t] = jt[t - 1] + (moves[t - 1] ? 1 : 0);
@@ -905,6 +908,7 @@ int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* s
     }
   }
   double ys = 0.0, yb = 0.0;
+  double xs = pl_eval(zs[0], 0.0), xb = pl_eval(zb[0], 0.0);  // ask and -bid
   *stop = -1;
   for (int t = 0; t <= N; ++t) {
     const double S = stock(m, t, jt[t]);
@@ -913,9 +917,13 @@ int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* s
     double y = 0.0, v = 0.0;
     int rc = pl_rebalance(Fs[t], Sa, Sb, ys, y, v);
     if (rc) return rc;
+    if (t > 0) xs *= m.r;
+    xs -= (y >= ys ? Sa : Sb) * (y - ys);
     hold[2 * t] = ys = y;
+    cash[2 * t] = xs;
     if (*stop >= 0) {
       hold[2 * t + 1] = NAN;
+      cash[2 * t + 1] = NAN;
       continue;
     }
     if ((rc = pl_rebalance(Fb[t], Sa, Sb, yb, y, v))) return rc;
@@ -925,8 +933,12 @@ int hedge_path(const Model<double>& m, const int8_t* moves, double* hold, int* s
     if (u < v) {
       *stop = t;
       hold[2 * t + 1] = NAN;
+      cash[2 * t + 1] = NAN;
     } else {
+      if (t > 0) xb *= m.r;
+      xb -= (y >= yb ? Sa : Sb) * (y - yb);
       hold[2 * t + 1] = yb = y;
+      cash[2 * t + 1] = xb;
     }
   }
   return OR_OK;
@@ -1317,23 +1329,22 @@ int or_pl_rebalance(const double* y, const double* f, int m, double sL, double s
 
 
 // The hedge along a path for each option (hedge_path): moves + i * stride holds option i's N
-// moves, hold + 2 * (stride + 1) * i its 2 (N + 1) holdings, stop[i] the buyer's stopping time.
+// moves, hold + 2 * (stride + 1) * i its 2 (N + 1) holdings, cash (same layout) the parties'
+// cash after rebalancing, stop[i] the buyer's stopping time.
 int or_hedge_path(const or_option_t* opts, int64_t n, const int8_t* moves, int64_t stride,
-                  double* hold, int32_t* stop, int32_t* status, int nthreads) {
+                  double* hold, double* cash, int32_t* stop, int32_t* status, int nthreads) {
   parallel_for(n, nthreads, [&](int64_t i) {
     const or_option_t& o = opts[i];
     double* h = hold + 2 * (stride + 1) * i;
+    double* c = cash + 2 * (stride + 1) * i;
     int rc = check_option(o);
     if (rc == OR_OK && o.N > stride) rc = OR_ERR_ARG;
     int st = -1;
     if (rc == OR_OK) {
       Model<double> m = make_model<double>(o, o.S0, o.K, o.sigma, o.R, o.T, o.k);
-      rc = hedge_path(m, moves + stride * i, h, &st);
+      rc = hedge_path(m, moves + stride * i, h, c, &st);
     }
-    if (rc)
-      for (int64_t k = 0; k < 2 * (stride + 1); ++k) h[k] = NAN;
-    else
-      for (int64_t k = 2 * ((int64_t)o.N + 1); k < 2 * (stride + 1); ++k) h[k] = NAN;
+    for (int64_t k = rc ? 0 : 2 * ((int64_t)o.N + 1); k < 2 * (stride + 1); ++k) h[k] = c[k] = NAN;
     stop[i] = rc ? -1 : st;
     if (status) status[i] = rc;
   });

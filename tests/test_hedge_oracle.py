@@ -9,7 +9,12 @@ the mathematics fix:
     (V_u - V_d) / (S0 u - S0 d) for the seller and its negative for the buyer, with V_u, V_d
     from a textbook CRR recursion written here;
   * the rebalancing target on random PL functions against a dense grid search of the
-    objective (convex and non-convex, with and without a kink at the starting holding).
+    objective (convex and non-convex, with and without a kink at the starting holding);
+  * along a path, the defining property of the two prices (Section 3): the seller's
+    self-financing portfolio started from the ask with the path's holdings can settle an
+    exercise at every node and its stock at N+1, and the buyer's, started from minus the
+    bid, can settle the buyer's exercise at its stopping node (or its stock at N+1); the
+    settlement costs are written out here from the payoff and the bid/ask prices.
 """
 import json
 import os
@@ -162,7 +167,7 @@ def test_no_costs_path_hedge_is_crr_delta_and_exercise_boundary(payoff):
                    R=float(rng.uniform(0.0, 0.1)), T=float(rng.uniform(0.1, 2.0)), k=0.0, N=N,
                    payoff=payoff)
         mv = rng.integers(0, 2, (1, N)).astype(np.int8)
-        hold, stop, st = oracle.hedge_path(o, mv)
+        hold, cash, stop, st = oracle.hedge_path(o, mv)
         assert st[0] == 0
         S, V, cont, ex = _crr_tree(o[0])
         j = 0
@@ -188,7 +193,7 @@ def test_no_costs_path_hedge_is_crr_delta_and_exercise_boundary(payoff):
 def test_path_hedge_starts_with_the_root_hedge():
     t = W.random_table(20, 6060, N_lo=2, N_hi=120)
     mv = np.random.default_rng(3).integers(0, 2, (len(t), int(t["N"].max()))).astype(np.int8)
-    hold, stop, st = oracle.hedge_path(t, mv, nthreads=4)
+    hold, cash, stop, st = oracle.hedge_path(t, mv, nthreads=4)
     h0, st0 = oracle.initial_hedge(t, nthreads=4)
     assert np.array_equal(st, st0)
     ok = st == 0
@@ -196,3 +201,157 @@ def test_path_hedge_starts_with_the_root_hedge():
     buyer_at_root = np.where(stop[ok] == 0, np.nan, h0[ok, 1])
     assert np.array_equal(hold[ok, 0, 1], buyer_at_root, equal_nan=True)
     assert np.all((stop[ok] == 0) == (h0[ok, 3] == 1.0))
+
+
+def _settle(o, S, kt, x, y, buyer):
+    """Cash left after settling the payoff at a node with stock price S and cost rate kt,
+    from cash x and y shares, then closing the stock position: the seller pays (xi, zeta),
+    the buyer receives it (Eq. 1, Eq. 6).  Shares are bought at (1+kt) S, sold at (1-kt) S."""
+    if o["payoff"] == W.PUT:
+        xi, zeta = o["K"], -1.0
+    elif o["payoff"] == W.CALL:
+        xi, zeta = -o["K"], 1.0
+    else:
+        xi, zeta = max(S - o["K"], 0.0) - max(S - o["K2"], 0.0), 0.0
+    if buyer:
+        x, q = x + xi, y + zeta
+    else:
+        x, q = x - xi, y - zeta
+    return x + q * (1.0 - kt) * S if q >= 0 else x + q * (1.0 + kt) * S
+
+
+def _no_payoff(o):
+    a = dict(zip(o.dtype.names, o.tolist()))
+    a["payoff"], a["K"], a["K2"] = W.SPREAD, 1e300, 1e300  # xi = 0, zeta = 0
+    return a
+
+
+@pytest.mark.parametrize("payoff", [W.PUT, W.CALL, W.SPREAD])
+def test_path_portfolios_superhedge(payoff):
+    rng = np.random.default_rng(404 + payoff)
+    t = W.random_table(16, 505 + payoff, N_lo=2, N_hi=160, payoffs=(payoff,), k_hi=0.03)
+    mv = rng.integers(0, 2, (len(t), int(t["N"].max()))).astype(np.int8)
+    hold, cash, stop, st = oracle.hedge_path(t, mv, nthreads=4)
+    ask_bid, pst = oracle.price_ask_bid(t, nthreads=4)
+    assert np.all(st == 0) and np.all(pst == 0)
+    for i, o in enumerate(t):
+        N = int(o["N"])
+        dt = o["T"] / N
+        u = np.exp(o["sigma"] * np.sqrt(dt))
+        r = np.exp(o["R"] * dt)
+        ask, bid = ask_bid[i]
+        jt = np.concatenate([[0], np.cumsum(mv[i, :N] != 0)])
+
+        def S(tt, j):
+            return o["S0"] * u ** (2 * j - tt)
+
+        def tol(x, y, s):
+            return 1e-9 * max(1.0, abs(x), s * abs(y))
+
+        # the seller: cash before the rebalancing at t is r x_{t-1} (the ask at t = 0)
+        x, y = ask, 0.0
+        for tt in range(N + 1):
+            kt = 0.0 if tt == 0 else o["k"]
+            s = S(tt, jt[tt])
+            left = _settle(o, s, kt, x, y, False)
+            assert left >= -tol(x, y, s), (i, tt, x, y, left)
+            x, y = cash[i, tt, 0] * r, hold[i, tt, 0]
+        for j in (jt[N], jt[N] + 1):  # both nodes of the extra instant N+1
+            s = S(N + 1, j)
+            left = _settle(_no_payoff(o), s, o["k"], x, y, False)
+            assert left >= -tol(x, y, s), (i, "N+1", x, y, left)
+        # the buyer: cash before the rebalancing at t is r x_{t-1} (minus the bid at t = 0)
+        x, y = -bid, 0.0
+        tau = int(stop[i])
+        assert tau == -1 or np.all(np.isnan(hold[i, tau:N + 1, 1]))
+        last = N if tau < 0 else tau - 1
+        assert not np.any(np.isnan(hold[i, :last + 1, 1]))
+        for tt in range(last + 1):
+            x, y = cash[i, tt, 1] * r, hold[i, tt, 1]
+        if tau >= 0:
+            s = S(tau, jt[tau])
+            if tau == 0:
+                x, y = -bid, 0.0
+            left = _settle(o, s, 0.0 if tau == 0 else o["k"], x, y, True)
+            assert left >= -tol(x, y, s), (i, "stop", tau, x, y, left)
+        else:
+            for j in (jt[N], jt[N] + 1):
+                s = S(N + 1, j)
+                left = _settle(_no_payoff(o), s, o["k"], x, y, True)
+                assert left >= -tol(x, y, s), (i, "N+1 buyer", x, y, left)
+
+
+
+def _node_functions(o, buyer):
+    """z_t at every node of a small tree, built level by level with the oracle's node step
+    (itself pinned by the price tests): z[t][j], t = 0..N+1."""
+    N = int(o["N"])
+    dt = o["T"] / N
+    u = np.exp(o["sigma"] * np.sqrt(dt))
+    r = np.exp(o["R"] * dt)
+    z = [None] * (N + 2)
+    z[N + 1] = []
+    for j in range(N + 2):
+        S = o["S0"] * u ** (2 * j - N - 1)
+        z[N + 1].append(oracle.PL([0.0], [0.0], -(1 + o["k"]) * S, -(1 - o["k"]) * S))
+    for t in range(N, -1, -1):
+        kt = 0.0 if t == 0 else o["k"]
+        z[t] = []
+        for j in range(t + 1):
+            S = o["S0"] * u ** (2 * j - t)
+            if o["payoff"] == W.PUT:
+                xi, zeta = o["K"], -1.0
+            elif o["payoff"] == W.CALL:
+                xi, zeta = -o["K"], 1.0
+            else:
+                xi, zeta = max(S - o["K"], 0.0) - max(S - o["K2"], 0.0), 0.0
+            z[t].append(oracle.node_step(z[t + 1][j + 1], z[t + 1][j], r, (1 + kt) * S, (1 - kt) * S,
+                                         xi, zeta, buyer))
+    return z, u, r
+
+
+@pytest.mark.parametrize("party", [0, 1])
+def test_path_portfolios_are_tight_on_the_binding_path(party):
+    """The portfolios start from exactly the price, so they carry no slack where the price is
+    attained: following at each level the successor whose z is larger at the holding (the one
+    that sets w = max(z_up, z_down)), the cash before rebalancing equals z_t at the holding
+    the party arrives with, until exercise binds (z_t = u_t there).  Catches cash that is too
+    high (a rebalancing charged too little) as the superhedging pins catch cash too low."""
+    t = W.concat(W.make(N=10, k=0.01, payoff=W.PUT, S0=95.0), W.make(N=12, k=0.02, payoff=W.CALL),
+                 W.make(N=9, k=0.005, payoff=W.SPREAD, K=95.0, K2=105.0, sigma=0.3),
+                 W.make(N=11, k=0.015, payoff=W.PUT, S0=110.0, R=0.02),
+                 W.make(N=8, k=0.03, payoff=W.CALL, S0=90.0, sigma=0.4))
+    checked = 0
+    for i, o in enumerate(t):
+        N = int(o["N"])
+        z, u, r = _node_functions(o, party == 1)
+        moves = np.zeros((1, N), np.int8)
+        for tt in range(N):  # the binding successor at each level, given the holding there
+            hold, cash, stop, st = oracle.hedge_path(t[i:i + 1], moves)
+            y = hold[0, tt, party]
+            if np.isnan(y):
+                break
+            j = int(moves[0, :tt].sum())
+            moves[0, tt] = 1 if z[tt + 1][j + 1](y)[0] >= z[tt + 1][j](y)[0] else 0
+        hold, cash, stop, st = oracle.hedge_path(t[i:i + 1], moves)
+        ask_bid, _ = oracle.price_ask_bid(t[i:i + 1])
+        C = ask_bid[0, 0] if party == 0 else -ask_bid[0, 1]
+        y, j = 0.0, 0
+        for tt in range(N + 2):
+            if tt == N + 1:  # the extra instant: the binding node of the two
+                j = j + 1 if z[N + 1][j + 1](y)[0] >= z[N + 1][j](y)[0] else j
+            elif tt > 0:
+                j += int(moves[0, tt - 1])
+            S = o["S0"] * u ** (2 * j - tt)
+            zt = z[tt][j](y)[0]
+            scale = max(1.0, abs(C), S * abs(y))
+            assert abs(C - zt) <= 1e-9 * scale, (i, party, tt, C, zt)
+            checked += 1
+            kt = 0.0 if tt == 0 else o["k"]
+            oo = o if tt <= N else _no_payoff(o)
+            if abs(zt + _settle(oo, S, kt, 0.0, y, party == 1)) <= 1e-9 * scale:
+                break  # exercise (or the final settlement) binds here
+            if tt == N + 1 or np.isnan(hold[0, tt, party]):
+                break
+            C, y = cash[0, tt, party] * r, hold[0, tt, party]
+    assert checked >= 2 * len(t)
