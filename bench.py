@@ -554,8 +554,8 @@ def run_greeks(args, rank, world, local):
 
 def run_path(args, rank, world, local):
     """The hedge along a path: the 1024 puts of the Greeks workload (N = 1000, seed 4), one
-    random path per option (seed 8), prices plus both parties' holdings at every node of the
-    path and the buyer's stopping level in one ob_hedge_path call per step; options/s against
+    random path per option (seed 8), prices plus both parties' holdings and cash at every node
+    of the path and the buyer's stopping level in one ob_hedge_path call per step; options/s against
     the pricing call on the same options."""
     import torch
 
@@ -568,12 +568,13 @@ def run_path(args, rank, world, local):
     moves = torch.as_tensor(np.random.default_rng(8).integers(0, 2, (n, S)).astype(np.int8)).to(dev)
     out = torch.empty((n, 2), dtype=torch.float64, device=dev)
     hold = torch.empty((n, S + 1, 2), dtype=torch.float64, device=dev)
+    cash = torch.empty_like(hold)
     stop = torch.empty(n, dtype=torch.int32, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
-        ob.ob_hedge_path(params, n, moves, S, out, hold, stop, st, stream)
+        ob.ob_hedge_path(params, n, moves, S, out, hold, cash, stop, st, stream)
     torch.cuda.synchronize(dev)
     assert int((st != 0).sum().item()) == 0
     sampler = ClockSampler(local)
@@ -584,7 +585,7 @@ def run_path(args, rank, world, local):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        ob.ob_hedge_path(params, n, moves, S, out, hold, stop, st, stream)
+        ob.ob_hedge_path(params, n, moves, S, out, hold, cash, stop, st, stream)
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -605,7 +606,7 @@ def run_path(args, rank, world, local):
     p_flops = 1.0 * FLOPS_PER_MERGED_POINT * float(u_points)
     p_achieved = p_flops / (job_s / args.steps) / 1e12
     line = {
-        "metric": "options/s with the hedge along a path (ask, bid, holdings, stopping level), FP64",
+        "metric": "options/s with the hedge along a path (ask, bid, holdings, cash, stopping level), FP64",
         "value": value, "unit": "options/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * job_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",

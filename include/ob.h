@@ -136,6 +136,14 @@ int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double*
  *           hold[(i*(stride+1) + t)*2 + 1] the buyer's, NaN from its stopping
  *                                          level on;
  *           NaN for t > N_i and for an option whose status is not OB_OK.
+ *   cash    DEVICE pointer or NULL, same layout as hold: each party's cash after
+ *           rebalancing at level t, in time-t money, of the self-financing
+ *           portfolio that starts at t = 0 with no stock and the ask (seller)
+ *           or minus the bid (buyer, who borrows it to buy the option):
+ *           x_t = r x_{t-1} - theta_t(y_t - y_{t-1}).  Along any path the
+ *           seller's portfolio can settle an exercise at every level and its
+ *           stock at N+1, and the buyer's can settle the buyer's exercise at
+ *           its stopping level (or its stock at N+1); NaN where hold is.
  *   stop    DEVICE pointer, n_options int32: the buyer's stopping level, -1 if
  *           it never stops (or the status is not OB_OK).
  *   status  DEVICE pointer or NULL, n_options int32 (as for ob_price_ask_bid).
@@ -147,7 +155,7 @@ int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double*
  * ob_price_ask_bid.  Returns OB_ERR_ARG on a NULL pointer (status may be NULL)
  * or stride outside [1, 2^26]. */
 int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* moves, int64_t stride,
-                  double* out, double* hold, int32_t* stop, int32_t* status, void* stream);
+                  double* out, double* hold, double* cash, int32_t* stop, int32_t* status, void* stream);
 
 /* The plain form of the same computation: one warp per option, options taken
  * in index order with a static assignment, no queue and no retry (an option

@@ -65,7 +65,7 @@ def load():
         lib.ob_greeks.restype = ctypes.c_int
         lib.ob_price_ask_bid_hedge.argtypes = [P, i64, P, P, P, P]
         lib.ob_price_ask_bid_hedge.restype = ctypes.c_int
-        lib.ob_hedge_path.argtypes = [P, i64, P, i64, P, P, P, P, P]
+        lib.ob_hedge_path.argtypes = [P, i64, P, i64, P, P, P, P, P, P]
         lib.ob_hedge_path.restype = ctypes.c_int
         lib.ob_price_ask_bid_host.argtypes = [P, i64, P, P]
         lib.ob_price_ask_bid_host.restype = ctypes.c_int
@@ -131,12 +131,13 @@ def ob_price_ask_bid_hedge(params, n, out, status, hedge, stream=None):
                                          _stream(stream)))
 
 
-def ob_hedge_path(params, n, moves, stride, out, hold, stop, status=None, stream=None):
+def ob_hedge_path(params, n, moves, stride, out, hold, cash, stop, status=None, stream=None):
     """The hedge along one path per option: moves[n, stride] int8 (non-zero up), out[n, 2] ask/bid,
     hold[n, stride + 1, 2] the seller's and buyer's holdings after rebalancing at each level,
-    stop[n] the buyer's stopping level (-1: never)."""
+    cash (same shape, or None) their cash after rebalancing, stop[n] the buyer's stopping level
+    (-1: never)."""
     _check(load().ob_hedge_path(_ptr(params), int(n), _ptr(moves), int(stride), _ptr(out), _ptr(hold),
-                                _ptr(stop), _ptr(status), _stream(stream)))
+                                _ptr(cash), _ptr(stop), _ptr(status), _stream(stream)))
 
 
 def ob_price_ask_bid_plain(params, n, out, status=None, stream=None):
@@ -254,7 +255,7 @@ def hedge(table, stream=None):
 
 def hedge_path(table, moves, stream=None):
     """The hedge along the paths moves[n, stride] (int8, non-zero up) of a workloads table:
-    (out[n,2], hold[n,stride+1,2], stop[n], status[n]) tensors."""
+    (out[n,2], hold[n,stride+1,2], cash[n,stride+1,2], stop[n], status[n]) tensors."""
     import torch
     n = int(np.asarray(table).shape[0])
     dev = to_device(table)
@@ -266,10 +267,11 @@ def hedge_path(table, moves, stream=None):
         mv = torch.zeros((n, 1), dtype=torch.int8, device=dev.device)
     out = torch.empty((n, 2), dtype=torch.float64, device=dev.device)
     hold = torch.empty((n, stride + 1, 2), dtype=torch.float64, device=dev.device)
+    cash = torch.empty_like(hold)
     stop = torch.empty(n, dtype=torch.int32, device=dev.device)
     st = torch.empty(n, dtype=torch.int32, device=dev.device)
-    ob_hedge_path(dev, n, mv, stride, out, hold, stop, st, stream)
-    return out, hold, stop, st
+    ob_hedge_path(dev, n, mv, stride, out, hold, cash, stop, st, stream)
+    return out, hold, cash, stop, st
 
 
 def crr(table, stream=None, wide=False):

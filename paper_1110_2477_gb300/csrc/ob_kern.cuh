@@ -380,7 +380,7 @@ cudaError_t launch_greeks_retry(int grid, cudaStream_t s, const obk::Opt* opts, 
 
 // ob_path.cu (the hedge along a path: one 16-warp CTA team per option from a device queue)
 cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* order, int* head,
-                        const int8_t* moves, long long stride, double* out, double* hold, int* stop, int* status,
-                        char* arena, size_t cta_bytes);
+                        const int8_t* moves, long long stride, double* out, double* hold, double* cash, int* stop,
+                        int* status, char* arena, size_t cta_bytes);
 
 }  // namespace obl

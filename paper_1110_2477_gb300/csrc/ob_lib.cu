@@ -801,7 +801,7 @@ int ob_greeks(const ob_option_t* params, int64_t n_options, double* out, double*
 }
 
 int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* moves, int64_t stride,
-                  double* out, double* hold, int32_t* stop, int32_t* status, void* stream) {
+                  double* out, double* hold, double* cash, int32_t* stop, int32_t* status, void* stream) {
   if (n_options < 0 || n_options > (1 << 30)) return OB_ERR_ARG;
   if (n_options == 0) return OB_OK;
   if (!params || !out || !hold || !stop || !moves || stride < 1 || stride > (1 << 26)) return OB_ERR_ARG;
@@ -831,8 +831,8 @@ int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* mo
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
-  e = launch_path(workers, s, opts, n, order, &P->ctl[C_HEAVY_HEAD], moves, (long long)stride, out, hold, stop,
-                  status, P->arena, wbytes);
+  e = launch_path(workers, s, opts, n, order, &P->ctl[C_HEAVY_HEAD], moves, (long long)stride, out, hold, cash,
+                  stop, status, P->arena, wbytes);
   if (e != cudaSuccess) return cuda_fail(e);
   return co.end();
 }

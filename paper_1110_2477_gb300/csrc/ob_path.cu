@@ -47,10 +47,14 @@ __device__ double rebalance_to(const double* Y, const double* V, const double* S
 }
 
 // One option: the induction of TcRun::run with the path's w_t kept, then the rebalancing
-// along the path by lane 0.  moves[t] (t < N): non-zero up, 0 down.  hold: 2 (N+1) doubles.
+// along the path by lane 0.  moves[t] (t < N): non-zero up, 0 down.  hold and cash (may be
+// null): 2 (N+1) doubles.  The cash of a self-financing portfolio is carried in future-value
+// units, where it changes only by the cost of each rebalancing: X_t = X_{t-1} - theta_t
+// lambda_t (y_t - y_{t-1}), X_{-1} = ask lambda_0 (seller) or -bid lambda_0 (buyer); the
+// cash in time-t money is X_t / lambda_t.
 template <class Team>
 __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, char* slice, size_t bytes,
-                        double& ask, double& bid, double* hold, int& stop) {
+                        double& ask, double& bid, double* hold, double* cash, int& stop) {
   int rc = check_option(o, true);
   ask = bid = dnan();
   stop = -1;
@@ -130,10 +134,11 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
     tm.sync();
   }
   const double lam0 = L.lam[0];
-  ask = R.root_value(0) / lam0;
-  bid = -R.root_value(1) / lam0;
+  const double z0s = R.root_value(0), z0b = R.root_value(1);
+  ask = z0s / lam0;
+  bid = -z0b / lam0;
   if (lane == 0) {  // the rebalancing along the path
-    double ys = 0.0, yb = 0.0;
+    double ys = 0.0, yb = 0.0, Xs = z0s, Xb = z0b;
     int jj = 0;
     for (int t = 0; t <= N; ++t) {
       if (t > 0) jj += moves[t - 1] != 0 ? 1 : 0;
@@ -143,10 +148,15 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
       const double sa = Sl * (1.0 + kt), sb = Sl * (1.0 - kt);
       const PathLv a = lv[2 * t], b = lv[2 * t + 1];
       double v;
-      ys = rebalance_to(store + a.off, store + a.off + a.m, store + a.off + 2 * a.m, a.m, a.sL, sa, sb, ys, v);
+      const double y1 =
+          rebalance_to(store + a.off, store + a.off + a.m, store + a.off + 2 * a.m, a.m, a.sL, sa, sb, ys, v);
+      Xs -= (y1 >= ys ? sa : sb) * (y1 - ys);
+      ys = y1;
       hold[2 * t] = ys;
+      if (cash) cash[2 * t] = Xs / L.lam[t];
       if (stop >= 0) {
         hold[2 * t + 1] = dnan();
+        if (cash) cash[2 * t + 1] = dnan();
         continue;
       }
       const double y = rebalance_to(store + b.off, store + b.off + b.m, store + b.off + 2 * b.m, b.m, b.sL, sa,
@@ -162,8 +172,11 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
       if (ue < v) {
         stop = t;
         hold[2 * t + 1] = dnan();
+        if (cash) cash[2 * t + 1] = dnan();
       } else {
+        Xb -= (y >= yb ? sa : sb) * (y - yb);
         hold[2 * t + 1] = yb = y;
+        if (cash) cash[2 * t + 1] = Xb / L.lam[t];
       }
     }
   }
@@ -176,8 +189,8 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
 __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__ opts, int n,
                                                     const int* __restrict__ order, int* head,
                                                     const int8_t* __restrict__ moves, long long stride,
-                                                    double* out, double* hold, int* stop, int* status,
-                                                    char* arena, size_t cta_bytes) {
+                                                    double* out, double* hold, double* cash, int* stop,
+                                                    int* status, char* arena, size_t cta_bytes) {
   __shared__ long long tbuf[obk::BlockTeam<16>::BUF];
   __shared__ int s_next;
   obk::BlockTeam<16> bt{tbuf};
@@ -192,13 +205,14 @@ __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__
     if (i < 0) break;
     const obk::Opt o = opts[i];
     double* h = hold + 2 * (stride + 1) * (long long)i;
+    double* c = cash ? cash + 2 * (stride + 1) * (long long)i : nullptr;
     double ask, bid;
     int st = -1, rc;
     if (o.N > stride) {
       rc = obk::ST_ARG;
       ask = bid = dnan();
     } else {
-      rc = path_one(bt, o, moves + stride * (long long)i, my, cta_bytes, ask, bid, h, st);
+      rc = path_one(bt, o, moves + stride * (long long)i, my, cta_bytes, ask, bid, h, c, st);
     }
     if (threadIdx.x == 0) {
       out[2 * i] = rc ? dnan() : ask;
@@ -207,15 +221,19 @@ __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__
       if (status) status[i] = rc;
     }
     const long long first = rc ? 0 : 2 * ((long long)o.N + 1);
-    for (long long k = first + threadIdx.x; k < 2 * (stride + 1); k += blockDim.x) h[k] = dnan();
+    for (long long k = first + threadIdx.x; k < 2 * (stride + 1); k += blockDim.x) {
+      h[k] = dnan();
+      if (c) c[k] = dnan();
+    }
     __syncthreads();
   }
 }
 
 cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* order, int* head,
-                        const int8_t* moves, long long stride, double* out, double* hold, int* stop, int* status,
-                        char* arena, size_t cta_bytes) {
-  k_tc_path<<<grid, 512, 0, s>>>(opts, n, order, head, moves, stride, out, hold, stop, status, arena, cta_bytes);
+                        const int8_t* moves, long long stride, double* out, double* hold, double* cash, int* stop,
+                        int* status, char* arena, size_t cta_bytes) {
+  k_tc_path<<<grid, 512, 0, s>>>(opts, n, order, head, moves, stride, out, hold, cash, stop, status, arena,
+                                 cta_bytes);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,9 @@
   * prices: bitwise those of ob_price_ask_bid on the same records;
   * holdings: the oracle's within 1e-9 (relative to max(1, |y|)) at every level of the path,
     NaN in the same places (beyond N_i, and from the buyer's stopping level on);
+  * cash: the oracle's within 1e-9 relative to max(|x|, S0); the two carry it in different
+    units (the kernel in future-value units, the oracle in time-t money, growing by r a
+    level), so they round differently over N levels of trades of size up to S |dy|;
   * the buyer's stopping level: the oracle's;
   * paths: random, all up, all down, alternating; rows longer than N_i; N = 1;
   * a batch above the cost-ordering limit (8192 options: taken in index order);
@@ -22,23 +25,32 @@ def _gpu(table, moves):
     import torch
 
     import paper_1110_2477_gb300 as ob
-    out, hold, stop, st = ob.hedge_path(table, moves)
+    out, hold, cash, stop, st = ob.hedge_path(table, moves)
     ref_out, ref_st = ob.price(table)
     torch.cuda.synchronize()
-    return (out.cpu().numpy(), hold.cpu().numpy(), stop.cpu().numpy(), st.cpu().numpy(),
+    return (out.cpu().numpy(), hold.cpu().numpy(), cash.cpu().numpy(), stop.cpu().numpy(), st.cpu().numpy(),
             ref_out.cpu().numpy(), ref_st.cpu().numpy())
 
 
+def _close_cash(g, o, S0):
+    fin = ~np.isnan(o)
+    assert np.array_equal(np.isnan(g), ~fin)
+    scale = np.maximum(np.abs(o), S0)
+    err = np.abs(g - o)[fin] / scale[fin]
+    assert err.max(initial=0.0) <= 1e-9, err.max()
+
+
 def _check(table, moves, nthreads=8):
-    out, hold, stop, st, ref_out, ref_st = _gpu(table, moves)
+    out, hold, cash, stop, st, ref_out, ref_st = _gpu(table, moves)
     assert np.array_equal(st, ref_st)
     assert np.array_equal(out.view(np.int64), ref_out.view(np.int64))
-    oh, ostop, ost = oracle.hedge_path(table, moves, nthreads=nthreads)
+    oh, oc, ostop, ost = oracle.hedge_path(table, moves, nthreads=nthreads)
     assert np.array_equal(st, ost)
     ok = st == 0
     assert np.array_equal(stop[ok], ostop[ok])
     assert np.all(stop[~ok] == -1)
-    assert np.all(np.isnan(hold[~ok]))
+    assert np.all(np.isnan(hold[~ok])) and np.all(np.isnan(cash[~ok]))
+    _close_cash(cash[ok], oc[ok], table["S0"][ok][:, None, None])
     g, o = hold[ok], oh[ok]
     assert np.array_equal(np.isnan(g), np.isnan(o))
     fin = ~np.isnan(o)
@@ -79,12 +91,13 @@ def test_no_costs_holdings_are_the_oracle_crr_deltas():
 def test_short_rows_and_bad_options():
     t = W.concat(W.make(N=50), W.make(N=30), W.make(N=40, sigma=-1.0), W.make(N=40))
     mv = np.random.default_rng(9).integers(0, 2, (len(t), 40)).astype(np.int8)
-    out, hold, stop, st, ref_out, ref_st = _gpu(t, mv)
+    out, hold, cash, stop, st, ref_out, ref_st = _gpu(t, mv)
     assert st[0] == -1 and np.all(np.isnan(out[0])) and np.all(np.isnan(hold[0])) and stop[0] == -1
+    assert np.all(np.isnan(cash[0])) and np.all(np.isnan(cash[2]))
     assert st[2] == -1 and np.all(np.isnan(out[2])) and np.all(np.isnan(hold[2]))
     assert st[1] == 0 and st[3] == 0
     assert np.all(np.isnan(hold[1, 31:]))
-    oh, ostop, ost = oracle.hedge_path(t[[1, 3]], mv[[1, 3]])
+    oh, oc, ostop, ost = oracle.hedge_path(t[[1, 3]], mv[[1, 3]])
     for gi, oi in ((1, 0), (3, 1)):
         assert np.array_equal(out[gi].view(np.int64), ref_out[gi].view(np.int64))
         assert stop[gi] == ostop[oi]
@@ -92,6 +105,7 @@ def test_short_rows_and_bad_options():
         assert np.array_equal(np.isnan(g), np.isnan(o))
         fin = ~np.isnan(o)
         assert np.all(np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1.0, np.abs(o[fin])))
+        _close_cash(cash[gi], oc[oi], t["S0"][gi])
 
 
 def test_batch_above_the_ordering_limit():
@@ -109,7 +123,7 @@ def test_empty_batch():
     out = torch.empty((0, 2), dtype=torch.float64, device="cuda")
     hold = torch.empty((0, 5, 2), dtype=torch.float64, device="cuda")
     stop = torch.empty(0, dtype=torch.int32, device="cuda")
-    ob.ob_hedge_path(p, 0, mv, 4, out, hold, stop)
+    ob.ob_hedge_path(p, 0, mv, 4, out, hold, hold, stop)
     torch.cuda.synchronize()
 
 
@@ -118,3 +132,22 @@ def test_paper_size_sample():
                  W.make(N=1500, payoff=W.SPREAD, K2=110.0, k=0.005))
     mv = np.random.default_rng(23).integers(0, 2, (len(t), 1500)).astype(np.int8)
     _check(t, mv, nthreads=3)
+
+
+def test_cash_is_optional():
+    import torch
+
+    import paper_1110_2477_gb300 as ob
+    t = W.concat(W.make(N=80, k=0.01), W.make(N=60, payoff=W.CALL, k=0.004))
+    mv = np.random.default_rng(12).integers(0, 2, (len(t), 80)).astype(np.int8)
+    dev = ob.to_device(t)
+    m = torch.as_tensor(mv).cuda()
+    out = torch.empty((2, 2), dtype=torch.float64, device="cuda")
+    hold = torch.empty((2, 81, 2), dtype=torch.float64, device="cuda")
+    stop = torch.empty(2, dtype=torch.int32, device="cuda")
+    ob.ob_hedge_path(dev, 2, m, 80, out, hold, None, stop)
+    out2, hold2, cash2, stop2, st2 = ob.hedge_path(t, mv)
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.int64), out2.view(torch.int64))
+    assert torch.equal(torch.nan_to_num(hold, 7.0), torch.nan_to_num(hold2, 7.0))
+    assert torch.equal(stop, stop2)
