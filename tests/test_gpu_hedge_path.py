@@ -10,7 +10,8 @@
   * paths: random, all up, all down, alternating; rows longer than N_i; N = 1;
   * a batch above the cost-ordering limit (8192 options: taken in index order);
   * an option with N_i > stride, and one that fails its checks, carry NaN and their status;
-  * the paper's option sizes (N = 1500) on a sample of paths.
+  * the paper's option sizes (N = 1500) on a sample of paths;
+  * the benchmark's path workload in its launch configuration, sampled.
 """
 import numpy as np
 import pytest
@@ -151,3 +152,21 @@ def test_cash_is_optional():
     assert torch.equal(out.view(torch.int64), out2.view(torch.int64))
     assert torch.equal(torch.nan_to_num(hold, 7.0), torch.nan_to_num(hold2, 7.0))
     assert torch.equal(stop, stop2)
+
+
+def test_path_workload_full_launch_sampled():
+    """The benchmark's path workload in its own launch configuration (1024 puts, N = 1000,
+    one random path each, seed 8), 16 sampled options against the oracle."""
+    t = W.greeks_puts()
+    mv = np.random.default_rng(8).integers(0, 2, (len(t), int(t["N"].max()))).astype(np.int8)
+    out, hold, cash, stop, st, ref_out, ref_st = _gpu(t, mv)
+    assert np.all(st == 0)
+    assert np.array_equal(out.view(np.int64), ref_out.view(np.int64))
+    idx = np.random.default_rng(2).choice(len(t), 16, replace=False)
+    oh, oc, ostop, ost = oracle.hedge_path(t[idx], mv[idx], nthreads=8)
+    assert np.all(ost == 0) and np.array_equal(stop[idx], ostop)
+    g, o = hold[idx], oh
+    assert np.array_equal(np.isnan(g), np.isnan(o))
+    fin = ~np.isnan(o)
+    assert np.all(np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1.0, np.abs(o[fin])))
+    _close_cash(cash[idx], oc, t["S0"][idx][:, None, None])
