@@ -616,7 +616,7 @@ def run_path(args, rank, world, local):
                    "l2": "flushed (256 MiB write) before every timed step"},
         "plain": {"value": n / plain_s, "unit": "options/s", "call": "ob_price_ask_bid"},
         "path_over_plain_time": (job_s / args.steps) / plain_s,
-        "gpu_launches": (2 if n <= 8192 else 1) * args.steps, "step_ms": step_ms, "clocks": clocks,
+        "gpu_launches": (3 if n <= 8192 else 2) * args.steps, "step_ms": step_ms, "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": p_achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
                      "frac": p_achieved / peak["tflops"], "traffic": None,
                      "note": "algorithmic FP64 flops = %d per merged successor breakpoint of the "

@@ -149,9 +149,11 @@ int ob_price_ask_bid_hedge(const ob_option_t* params, int64_t n_options, double*
  *   status  DEVICE pointer or NULL, n_options int32 (as for ob_price_ask_bid).
  * One 16-warp CTA team per option, up to one per SM, taking the options from a
  * device queue (the costliest first for batches up to 8192 options, in index
- * order above), with 128 MiB of scratch each: three quarters for the level
- * arrays, one quarter for w_t of the path's nodes.  No follow-up launch: an option that outgrows either part gets
- * OB_ERR_CAPACITY.  Same pool, serialisation and call ordering as
+ * order above), with 128 MiB of scratch each (OB_PATH_MB): three quarters for
+ * the level arrays, one quarter for w_t of the path's nodes.  An option that
+ * outgrows either part is retried by a second launch of one CTA team with the
+ * whole pool, on the same stream; one that outgrows that too gets
+ * OB_ERR_CAPACITY and NaN.  Same pool, serialisation and call ordering as
  * ob_price_ask_bid.  Returns OB_ERR_ARG on a NULL pointer (status may be NULL)
  * or stride outside [1, 2^26]. */
 int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* moves, int64_t stride,

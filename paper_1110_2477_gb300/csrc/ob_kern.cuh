@@ -379,8 +379,8 @@ cudaError_t launch_greeks_retry(int grid, cudaStream_t s, const obk::Opt* opts, 
                                 const int* in_list, int* head, int* ovf_count, int* ovf_list, int last);
 
 // ob_path.cu (the hedge along a path: one 16-warp CTA team per option from a device queue)
-cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* order, int* head,
-                        const int8_t* moves, long long stride, double* out, double* hold, double* cash, int* stop,
-                        int* status, char* arena, size_t cta_bytes);
+cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* n_dev, const int* order,
+                        int* head, const int8_t* moves, long long stride, double* out, double* hold, double* cash,
+                        int* stop, int* status, char* arena, size_t cta_bytes, int* ovf_count, int* ovf_list);
 
 }  // namespace obl

@@ -223,6 +223,7 @@ struct DevPool {
   int team_warps = 16;  // whole-SM teams: one 512-thread CTA per SM
   int greeks_warps = 16; // warps of a Greeks CTA team (16 or 8)
   int greeks_full = 1;   // records of every level when they fit (OB_GREEKS_FULL=0: checkpoints only)
+  size_t path_bytes = kGreeksSmBytes;  // first-tier scratch per CTA of the path form (OB_PATH_MB)
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* ctl = nullptr;      // 2 ints per tier (queue head, overflow count)
@@ -315,6 +316,7 @@ int pool_get(DevPool** out, int* dev_out = nullptr) {
     if (const char* g = getenv("OB_GRAPH")) P.use_graphs = atoi(g) != 0;
     if (const char* g = getenv("OB_GREEKS_WARPS")) P.greeks_warps = atoi(g) == 8 ? 8 : 16;
     if (const char* g = getenv("OB_GREEKS_FULL")) P.greeks_full = atoi(g) != 0;
+    P.path_bytes = env_size("OB_PATH_MB", kGreeksSmBytes >> 20) << 20;
     P.wide_wait_ns = env_size("OB_WIDE_WAIT_MS", kGroupWaitNs / 1000000ULL) * 1000000ULL;
     if (const char* x = getenv("OB_WIDE_SPLIT_X")) P.wide_split_x = atof(x);
     P.test_skip_calls = (int)env_size("OB_TEST_WIDE_SKIP", 0);
@@ -812,12 +814,12 @@ int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* mo
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_call_mu[dev]);
   const int workers = n < P->sms ? n : P->sms;  // one 16-warp CTA team per SM
-  if ((rc = pool_reserve(P, 1, (size_t)workers * kGreeksSmBytes))) return rc;
+  if ((rc = pool_reserve(P, (size_t)n, (size_t)workers * P->path_bytes))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   CallOrder co{P, s};
   if ((rc = co.begin())) return rc;
   size_t wbytes = P->arena_bytes / (size_t)workers;
-  if (wbytes > kGreeksSmBytes) wbytes = kGreeksSmBytes;
+  if (wbytes > P->path_bytes) wbytes = P->path_bytes;
   wbytes &= ~(size_t)255;
   const obk::Opt* opts = (const obk::Opt*)params;
   cudaError_t e;
@@ -831,8 +833,14 @@ int ob_hedge_path(const ob_option_t* params, int64_t n_options, const int8_t* mo
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     order = P->order;
   }
-  e = launch_path(workers, s, opts, n, order, &P->ctl[C_HEAVY_HEAD], moves, (long long)stride, out, hold, cash,
-                  stop, status, P->arena, wbytes);
+  // first tier: one slice per CTA; the options that outgrow it go to a second launch of one
+  // CTA with the whole pool, where an option that still does not fit gets OB_ERR_CAPACITY
+  int* list0 = P->lists;
+  e = launch_path(workers, s, opts, n, nullptr, order, &P->ctl[C_HEAVY_HEAD], moves, (long long)stride, out, hold,
+                  cash, stop, status, P->arena, wbytes, &P->ctl[C_T0_OVF], list0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = launch_path(1, s, opts, n, &P->ctl[C_T0_OVF], list0, &P->ctl[C_T1_HEAD], moves, (long long)stride, out, hold,
+                  cash, stop, status, P->arena, P->arena_bytes & ~(size_t)255, nullptr, nullptr);
   if (e != cudaSuccess) return cuda_fail(e);
   return co.end();
 }

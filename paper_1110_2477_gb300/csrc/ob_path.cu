@@ -185,20 +185,25 @@ __device__ int path_one(const Team& tm, const obk::Opt& o, const int8_t* moves, 
 }
 
 // One 16-warp CTA team per option, taken from a device queue: position q = atomicAdd(head)
-// of order (the costliest first; index order when order is null).
+// of order (the costliest first; index order when order is null), q < n, or q < *n_dev when
+// n_dev is set (a follow-up launch reads the count its predecessor left).  With ovf_count
+// set, an option that outgrows its slice is appended to ovf_list for the follow-up launch
+// and its results are left to it; without, it gets ST_CAPACITY and NaN.
 __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__ opts, int n,
-                                                    const int* __restrict__ order, int* head,
+                                                    const int* n_dev, const int* order, int* head,
                                                     const int8_t* __restrict__ moves, long long stride,
                                                     double* out, double* hold, double* cash, int* stop,
-                                                    int* status, char* arena, size_t cta_bytes) {
+                                                    int* status, char* arena, size_t cta_bytes,
+                                                    int* ovf_count, int* ovf_list) {
   __shared__ long long tbuf[obk::BlockTeam<16>::BUF];
   __shared__ int s_next;
   obk::BlockTeam<16> bt{tbuf};
   char* my = arena + (size_t)blockIdx.x * cta_bytes;
+  const int count = n_dev ? *n_dev : n;
   for (;;) {
     if (threadIdx.x == 0) {
       const int q = atomicAdd(head, 1);
-      s_next = q < n ? (order ? order[q] : q) : -1;
+      s_next = q < count ? (order ? order[q] : q) : -1;
     }
     __syncthreads();
     const int i = s_next;
@@ -213,6 +218,11 @@ __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__
       ask = bid = dnan();
     } else {
       rc = path_one(bt, o, moves + stride * (long long)i, my, cta_bytes, ask, bid, h, c, st);
+    }
+    if (rc == obk::ST_CAPACITY && ovf_count) {  // to the follow-up launch, with more scratch
+      if (threadIdx.x == 0) ovf_list[atomicAdd(ovf_count, 1)] = i;
+      __syncthreads();
+      continue;
     }
     if (threadIdx.x == 0) {
       out[2 * i] = rc ? dnan() : ask;
@@ -229,11 +239,11 @@ __global__ void __launch_bounds__(512, 1) k_tc_path(const obk::Opt* __restrict__
   }
 }
 
-cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* order, int* head,
-                        const int8_t* moves, long long stride, double* out, double* hold, double* cash, int* stop,
-                        int* status, char* arena, size_t cta_bytes) {
-  k_tc_path<<<grid, 512, 0, s>>>(opts, n, order, head, moves, stride, out, hold, cash, stop, status, arena,
-                                 cta_bytes);
+cudaError_t launch_path(int grid, cudaStream_t s, const obk::Opt* opts, int n, const int* n_dev, const int* order,
+                        int* head, const int8_t* moves, long long stride, double* out, double* hold, double* cash,
+                        int* stop, int* status, char* arena, size_t cta_bytes, int* ovf_count, int* ovf_list) {
+  k_tc_path<<<grid, 512, 0, s>>>(opts, n, n_dev, order, head, moves, stride, out, hold, cash, stop, status, arena,
+                                 cta_bytes, ovf_count, ovf_list);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,9 @@
   * a batch above the cost-ordering limit (8192 options: taken in index order);
   * an option with N_i > stride, and one that fails its checks, carry NaN and their status;
   * the paper's option sizes (N = 1500) on a sample of paths;
-  * the benchmark's path workload in its launch configuration, sampled.
+  * the benchmark's path workload in its launch configuration, sampled;
+  * small first-tier slices (the follow-up launch, same bits) and a pool too small for one
+    option (OB_ERR_CAPACITY for it, the others complete).
 """
 import numpy as np
 import pytest
@@ -170,3 +172,53 @@ def test_path_workload_full_launch_sampled():
     fin = ~np.isnan(o)
     assert np.all(np.abs(g[fin] - o[fin]) <= 1e-9 * np.maximum(1.0, np.abs(o[fin])))
     _close_cash(cash[idx], oc, t["S0"][idx][:, None, None])
+
+
+# ---------------------------------------------------------------- scratch limits (subprocess: the pool is per process)
+_CHILD = r"""
+import sys, json, numpy as np, torch
+sys.path.insert(0, %(root)r)
+import workloads as W, paper_1110_2477_gb300 as ob
+t = W.concat(W.make(K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=1000, payoff=W.SPREAD),
+             W.random_table(40, 78, N_lo=50, N_hi=300))
+mv = np.random.default_rng(4).integers(0, 2, (len(t), 1000)).astype(np.int8)
+out, hold, cash, stop, st = ob.hedge_path(t, mv)
+torch.cuda.synchronize()
+print(json.dumps({"out": out.cpu().numpy().view(np.int64).tolist(),
+                  "hold": hold.cpu().numpy().view(np.int64).tolist(),
+                  "cash": cash.cpu().numpy().view(np.int64).tolist(),
+                  "stop": stop.cpu().numpy().tolist(), "st": st.cpu().numpy().tolist()}))
+"""
+
+
+def _child(env_extra):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, "-c", _CHILD % {"root": root}], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return {k: np.array(v) for k, v in json.loads(r.stdout.strip().splitlines()[-1]).items()}
+
+
+def test_capacity_follow_up_launch_and_exhaustion():
+    """1 MiB first-tier slices send the larger options to the follow-up launch on the whole
+    pool: the same bits as with 128 MiB slices.  A 3 MiB pool is too small for the N = 1000
+    spread: OB_ERR_CAPACITY and NaN for it, the others complete with the same bits."""
+    base = _child({})
+    assert np.all(base["st"] == 0)
+    small = _child({"OB_PATH_MB": "1"})
+    for k in base:
+        assert np.array_equal(small[k], base[k]), k
+    tiny = _child({"OB_POOL_MB": "3"})
+    assert tiny["st"][0] == -3 and tiny["stop"][0] == -1
+    for k in ("out", "hold", "cash"):
+        assert np.all(np.isnan(tiny[k][0].view(np.float64))), k
+    assert set(tiny["st"].tolist()) <= {0, -3}
+    ok = tiny["st"] == 0
+    assert ok.sum() >= 1
+    for k in base:
+        assert np.array_equal(tiny[k][ok], base[k][ok]), k
