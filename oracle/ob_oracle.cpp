@@ -871,7 +871,7 @@ int initial_hedge(const Model<double>& m, double* out) {
 // after rebalancing at t (from the previous holding, 0 before t = 0; to the y' attaining
 // v_t(y) = inf_y' [w_t(y')/r + theta_t(y' - y)]), hold[2t+1] the buyer's; the buyer stops at the
 // first t where u_t(y) < v_t(y) for the holding y it arrives with (*stop = t, NaN from there
-// on; -1 if he never does).  The functions w_t of the path's nodes are kept during the
+// on; -1 if it never does).  The functions w_t of the path's nodes are kept during the
 // induction of price_tc (built the same way).  cash[2t] and cash[2t+1] are the parties' cash
 // after rebalancing at t, in time-t money, of the self-financing portfolios that start at
 // t = 0 with no stock and the ask (seller) or minus the bid (buyer, who borrows it to buy the
