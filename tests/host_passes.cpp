@@ -1,11 +1,13 @@
-// The level passes of paper_1110_2477_gb300/csrc (ob_tc.cuh, ob_adj.cuh) compiled for the
-// host with a one-lane team, for CPU tests of their logic: pricing (TcRun), the split of a
-// level over G teams (TcGroup, run phase by phase) and the adjoint (TcAdj).  Test
+// The level passes of paper_1110_2477_gb300/csrc (ob_tc.cuh, ob_adj.cuh, ob_path.cuh) compiled
+// for the host with a one-lane team, for CPU tests of their logic: pricing (TcRun), the split
+// of a level over G teams (TcGroup, run phase by phase), the adjoint (TcAdj) and the hedge
+// along a path (path_one).  Test
 // infrastructure only; the library itself runs these passes on the GPU.
 #include <cstring>
 #include <vector>
 
 #include "ob_adj.cuh"
+#include "ob_path.cuh"
 
 namespace {
 
@@ -228,4 +230,13 @@ extern "C" int hp_greeks(const obk::Opt* o, double* out, double* grad, int full)
   obk::TcRun<OneLane> R(tm, *o, L);
   obk::TcAdj<OneLane> G(R, A);
   return G.run(out[0], out[1], grad, grad + obk::NPAR, full != 0);
+}
+
+// The hedge along a path (path_one) for one checked option: out = (ask, bid), hold and cash
+// 2 (N+1) doubles each, *stop the buyer's stopping level.  slice_kb: the option's scratch.
+extern "C" int hp_hedge_path(const obk::Opt* o, const int8_t* moves, int slice_kb, double* out, double* hold,
+                             double* cash, int* stop) {
+  const size_t bytes = (size_t)slice_kb << 10;
+  OneLane tm;
+  return obk::path_one(tm, *o, moves, arena(bytes), bytes, out[0], out[1], hold, cash, *stop);
 }

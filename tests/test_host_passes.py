@@ -1,8 +1,9 @@
 """The kernel's level passes compiled for the host with a one-lane team (tests/host_passes.cpp)
 against the oracle: prices at the parity tolerance, the same points whether a level is split
-over 1 or G teams (bitwise), and the adjoint against the oracle's dual-number gradient.  This
-checks the passes' logic (merge with owner handoff, running minima, restriction and exercise
-per piece, the split of a level, the reverse sweep) without a GPU."""
+over 1 or G teams (bitwise), the adjoint against the oracle's dual-number gradient, and the
+hedge along a path against the oracle's.  This checks the passes' logic (merge with owner
+handoff, running minima, restriction and exercise per piece, the split of a level, the
+reverse sweep, the path's w kept per level and the forward rebalancing) without a GPU."""
 import ctypes
 import os
 import subprocess
@@ -174,3 +175,48 @@ def test_host_adjoint_matches_oracle_gradient(payoff):
             assert np.all(np.abs(grad - rgrad[i].reshape(-1)) <= 1e-6 * scale), (i, full, grad, rgrad[i])
             res.append(np.concatenate([out, grad]))
         assert np.array_equal(res[0].view(np.int64), res[1].view(np.int64)), i
+
+
+def test_host_hedge_path_matches_oracle():
+    """path_one on the host (one-lane team) against the oracle's hedge along a path: prices
+    bitwise those of the host pricing run, holdings within 1e-9 of max(1, |y|), cash within
+    1e-9 of max(|x|, S0), the same stopping levels; a slice too small for the path store
+    gives ST_CAPACITY."""
+    t = W.concat(W.random_table(30, 32000, N_lo=1, N_hi=120, k_hi=0.03),
+                 W.make(S0=100, K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=60, payoff=W.SPREAD),
+                 W.make(k=0.0, N=40), W.make(k=0.01, N=1))
+    S = int(t["N"].max())
+    mv = np.random.default_rng(6).integers(0, 2, (len(t), S)).astype(np.int8)
+    oh, oc, ostop, ost = oracle.hedge_path(t, mv, nthreads=8)
+    P = ctypes.c_void_p
+    stops = 0
+    for i in range(len(t)):
+        N = int(t["N"][i])
+        a = _rec(t[i])
+        m = np.ascontiguousarray(mv[i])
+        out = np.zeros(2)
+        hold = np.full(2 * (N + 1), np.nan)
+        cash = np.full(2 * (N + 1), np.nan)
+        stop = ctypes.c_int(-2)
+        rc = _lib().hp_hedge_path(a.ctypes.data_as(P), m.ctypes.data_as(P), 64 << 10, out.ctypes.data_as(P),
+                                  hold.ctypes.data_as(P), cash.ctypes.data_as(P), ctypes.byref(stop))
+        assert rc == ost[i] == 0, (i, rc)
+        prc, pout, _ = _price(t[i])
+        assert prc == 0 and np.array_equal(out.view(np.int64), pout.view(np.int64)), i
+        assert stop.value == ostop[i], (i, stop.value, ostop[i])
+        stops += stop.value >= 0
+        h, c = hold.reshape(N + 1, 2), cash.reshape(N + 1, 2)
+        ho, co = oh[i, :N + 1], oc[i, :N + 1]
+        assert np.array_equal(np.isnan(h), np.isnan(ho)) and np.array_equal(np.isnan(c), np.isnan(co)), i
+        f = ~np.isnan(ho)
+        assert np.all(np.abs(h[f] - ho[f]) <= 1e-9 * np.maximum(1.0, np.abs(ho[f]))), i
+        assert np.all(np.abs(c[f] - co[f]) <= 1e-9 * np.maximum(np.abs(co[f]), t["S0"][i])), i
+    assert stops >= 1
+    # 64 KiB: too small for the N = 60 spread's level arrays and path store together
+    i = len(t) - 3
+    out = np.zeros(2)
+    hold = np.zeros(2 * 61)
+    stop = ctypes.c_int(-2)
+    rc = _lib().hp_hedge_path(_rec(t[i]).ctypes.data_as(P), np.ascontiguousarray(mv[i]).ctypes.data_as(P), 64,
+                              out.ctypes.data_as(P), hold.ctypes.data_as(P), None, ctypes.byref(stop))
+    assert rc == -3
