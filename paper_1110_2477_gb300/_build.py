@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 UNITS = ["ob_lib.cu", "ob_batched16.cu", "ob_batched8.cu", "ob_batched_half.cu", "ob_tiers.cu", "ob_group.cu", "ob_greeks8.cu",
          "ob_greeks.cu", "ob_path.cu"]
 SRC = [os.path.join(CSRC, u) for u in UNITS]
-DEPS = SRC + [os.path.join(CSRC, f) for f in ("ob_kern.cuh", "ob_tc.cuh", "ob_team.cuh", "ob_adj.cuh")] + [
+DEPS = SRC + [os.path.join(CSRC, f) for f in ("ob_kern.cuh", "ob_tc.cuh", "ob_team.cuh", "ob_adj.cuh", "ob_path.cuh")] + [
     os.path.join(ROOT, "include", "ob.h")]
 LIB = os.path.join(HERE, "libob.so")
 OBJ = os.path.join(HERE, "_build")
