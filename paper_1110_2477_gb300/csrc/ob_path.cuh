@@ -107,21 +107,24 @@ OB_HD int path_one(const Team& tm, const Opt& o, const int8_t* moves, char* slic
     if (!R.pass1(t, wtot, utot)) return ST_CAPACITY;
     R.pass2(t, wtot);
     if (!R.pass3(t, wtot, ztot)) return ST_CAPACITY;
-    // keep w of the path's seller node j and buyer node t + 1 + j (w is ordered by node)
+    // keep w of the path's seller node j and buyer node t + 1 + j (w is ordered by node):
+    // the first point of each node and of the next one, four binary searches on the points'
+    // node index, one per lane, into the four slots past the store
     const double* nt1 = L.nt[(t + 1) & 1];
-    for (int p = 0; p < 2; ++p) {
-      const int node = p * (t + 1) + j;
-      int lo = 0, hi = wtot;  // first point of node, then of node + 1
-      if (lane == 0) {
-        int a = 0, b = wtot;
-        while (a < b) { const int mid = (a + b) >> 1; if (L.wN[mid] < node) a = mid + 1; else b = mid; }
-        lo = a;
-        b = wtot;
-        while (a < b) { const int mid = (a + b) >> 1; if (L.wN[mid] < node + 1) a = mid + 1; else b = mid; }
-        hi = a;
+    long long* bound = (long long*)(store + store_cap);
+    for (int k = lane; k < 4; k += Team::W) {
+      const int node = (k >> 1) * (t + 1) + j + (k & 1);
+      int a = 0, b = wtot;
+      while (a < b) {
+        const int mid = (a + b) >> 1;
+        if (L.wN[mid] < node) a = mid + 1;
+        else b = mid;
       }
-      lo = tm.bcast0(lo);
-      hi = tm.bcast0(hi);
+      bound[k] = a;
+    }
+    tm.sync();
+    for (int p = 0; p < 2; ++p) {
+      const int lo = (int)bound[2 * p], hi = (int)bound[2 * p + 1];
       const int m = hi - lo;
       if (m < 1 || used + 3LL * m > store_cap) return ST_CAPACITY;
       for (int i = lane; i < m; i += Team::W) {
