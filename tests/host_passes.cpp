@@ -1,7 +1,7 @@
 // The level passes of paper_1110_2477_gb300/csrc (ob_tc.cuh, ob_adj.cuh, ob_path.cuh) compiled
 // for the host with a one-lane team, for CPU tests of their logic: pricing (TcRun), the split
-// of a level over G teams (TcGroup, run phase by phase), the adjoint (TcAdj) and the hedge
-// along a path (path_one).  Test
+// of a level over G teams (TcGroup, run phase by phase), the adjoint (TcAdj), the hedge at
+// the root (TcRun::root_hedge) and the hedge along a path (path_one).  Test
 // infrastructure only; the library itself runs these passes on the GPU.
 #include <cstring>
 #include <vector>
@@ -47,6 +47,19 @@ char* arena(size_t bytes) {
 }
 
 }  // namespace
+
+// The pricing run plus the hedge at the root (TcRun::root_hedge): hedge[4] as the library
+// returns it (holdings of the seller and the buyer, the two exercise flags).
+extern "C" int hp_price_hedge(const obk::Opt* o, double* out, double* hedge) {
+  const size_t bytes = 256ull << 20;
+  OneLane tm;
+  obk::Lay L;
+  if (!obk::carve(arena(bytes), bytes, o->N, 16, L)) return obk::ST_CAPACITY;
+  obk::TcRun<OneLane> R(tm, *o, L);
+  const int rc = R.run(out[0], out[1]);
+  for (int c = 0; c < 4; ++c) hedge[c] = R.st.hedge[c];
+  return rc;
+}
 
 extern "C" int hp_price(const obk::Opt* o, double* out, long long* pts) {
   const size_t bytes = 256ull << 20;

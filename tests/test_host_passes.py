@@ -220,3 +220,33 @@ def test_host_hedge_path_matches_oracle():
     rc = _lib().hp_hedge_path(_rec(t[i]).ctypes.data_as(P), np.ascontiguousarray(mv[i]).ctypes.data_as(P), 64,
                               out.ctypes.data_as(P), hold.ctypes.data_as(P), None, ctypes.byref(stop))
     assert rc == -3
+
+
+def test_host_root_hedge_matches_oracle():
+    """TcRun::root_hedge on the host (one-lane team) against the oracle's hedge at the root:
+    holdings within 1e-9 of max(1, |y|), or a breakpoint that attains the same minimum to
+    within 1e-12 where two tie; the exercise flags equal wherever u_0(0) and v_0(0) are not
+    within rounding of each other (the oracle's root objective decides)."""
+    t = W.concat(W.random_table(40, 33000, N_lo=1, N_hi=120, k_hi=0.03), W.make(S0=50.0, N=30, k=0.0),
+                 W.make(S0=100, K=95, K2=105, sigma=0.1, T=0.1, k=0.02, N=60, payoff=W.SPREAD))
+    oh, ost = oracle.initial_hedge(t, nthreads=8)
+    P = ctypes.c_void_p
+    for i in range(len(t)):
+        out = np.zeros(2)
+        hg = np.zeros(4)
+        rc = _lib().hp_price_hedge(_rec(t[i]).ctypes.data_as(P), out.ctypes.data_as(P), hg.ctypes.data_as(P))
+        assert rc == ost[i] == 0, (i, rc)
+        for p in (0, 1):
+            yg, yo = hg[p], oh[i, p]
+            if abs(yg - yo) > 1e-9 * max(1.0, abs(yo)):
+                f = oracle.root_objective(t[i:i + 1], p, [yg, yo])
+                assert abs(f[0] - f[1]) <= 1e-12 * max(1.0, abs(f[1])), (i, p, yg, yo, f)
+        assert hg[2] in (0.0, 1.0) and hg[3] in (0.0, 1.0)
+        # a flag may differ only where exercise and the hedge tie: then the price (ask =
+        # max(u, v) for the seller, -bid = min(u, v) for the buyer) equals v to rounding
+        if hg[2] != oh[i, 2]:
+            v = oracle.root_objective(t[i:i + 1], 0, [oh[i, 0]])[0]
+            assert abs(out[0] - v) <= 1e-11 * max(1.0, abs(v)), (i, "seller flag off a tie")
+        if hg[3] != oh[i, 3]:
+            v = oracle.root_objective(t[i:i + 1], 1, [oh[i, 1]])[0]
+            assert abs(-out[1] - v) <= 1e-11 * max(1.0, abs(v)), (i, "buyer flag off a tie")
