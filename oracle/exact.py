@@ -158,3 +158,94 @@ def price_row(row):
     return price(float(row["S0"]), float(row["K"]), float(row["K2"]), float(row["sigma"]),
                  float(row["R"]), float(row["T"]), float(row["k"]), int(row["N"]),
                  int(row["payoff"]))
+
+
+def hedge_path(row, moves):
+    """Exact hedge along one path (Section 3), for the C++ oracle's hedge_path: at each level t
+    of the path each party rebalances from the holding it arrived with (none before t = 0) to
+    the y' that attains min over y' of w_t(y')/r + theta_t(y' - y), the rightmost among equal
+    minima; the candidates are the breakpoints of w_t and y itself.  The cash of the
+    self-financing portfolios that start from the ask and from minus the bid follows
+    x_t = r x_{t-1} - theta_t(y_t - y_{t-1}).  The buyer stops at the first level where
+    exercising with the holding it arrived with costs less: u_t(y) < v_t(y).
+    Returns (ask, bid, hold, cash, stop), hold[t] = (seller, buyer) with None from the stop on."""
+    S0, K, K2 = float(row["S0"]), float(row["K"]), float(row["K2"])
+    sigma, R, T, k = float(row["sigma"]), float(row["R"]), float(row["T"]), float(row["k"])
+    N, payoff = int(row["N"]), int(row["payoff"])
+    dt = T / N
+    u = Q(math.exp(sigma * math.sqrt(dt)))
+    r = Q(math.exp(R * dt))
+    S0q, Kq, K2q, kq = Q(S0), Q(K), Q(K2), Q(k)
+    one = Q(1)
+
+    def stock(t, j):
+        return S0q * (u ** (2 * j - t))
+
+    def pay(S):
+        if payoff == 0:
+            return Kq, Q(-1)
+        if payoff == 1:
+            return -Kq, Q(1)
+        return max(S - Kq, Q(0)) - max(S - K2q, Q(0)), Q(0)
+
+    jt = [0] * (N + 1)
+    for t in range(1, N + 1):
+        jt[t] = jt[t - 1] + (1 if moves[t - 1] else 0)
+    zs, zb = [], []
+    for j in range(N + 2):
+        S = stock(N + 1, j)
+        Sa, Sb = (one + kq) * S, (one - kq) * S
+        zs.append(expense(Q(0), Q(0), Sa, Sb, False))
+        zb.append(expense(Q(0), Q(0), Sa, Sb, True))
+    F = [None] * (N + 1)  # (seller's w_t / r, buyer's) at the path's node of level t
+    for t in range(N, -1, -1):
+        for j in range(t + 1):
+            S = stock(t, j)
+            kt = Q(0) if t == 0 else kq
+            Sa, Sb = (one + kt) * S, (one - kt) * S
+            xi, zeta = pay(S)
+            if j == jt[t]:
+                pair = []
+                for z in (zs, zb):
+                    w = envelope(z[j + 1], z[j], True)
+                    pair.append(PLQ(w.ys, [x / r for x in w.fs], w.sL / r, w.sR / r))
+                F[t] = pair
+            zs[j] = node_step(zs[j + 1], zs[j], r, Sa, Sb, xi, zeta, False)
+            zb[j] = node_step(zb[j + 1], zb[j], r, Sa, Sb, xi, zeta, True)
+    ask, bid = zs[0](Q(0)), -zb[0](Q(0))
+
+    def rebalance(G, Sa, Sb, y0):
+        best = None
+        for c in sorted(set(G.ys) | {y0}):
+            v = G(c) + (Sa if c >= y0 else Sb) * (c - y0)
+            if best is None or v <= best[1]:
+                best = (c, v)
+        return best
+
+    hold, cash = [], []
+    ys, yb, xs, xb = Q(0), Q(0), ask, -bid
+    stop = -1
+    for t in range(N + 1):
+        S = stock(t, jt[t])
+        kt = Q(0) if t == 0 else kq
+        Sa, Sb = (one + kt) * S, (one - kt) * S
+        y, _ = rebalance(F[t][0], Sa, Sb, ys)
+        if t > 0:
+            xs *= r
+        xs -= (Sa if y >= ys else Sb) * (y - ys)
+        ys = y
+        hb = cb = None
+        if stop < 0:
+            y, v = rebalance(F[t][1], Sa, Sb, yb)
+            xi, zeta = pay(S)
+            if expense(xi, zeta, Sa, Sb, True)(yb) < v:
+                stop = t
+            else:
+                if t > 0:
+                    xb *= r
+                xb -= (Sa if y >= yb else Sb) * (y - yb)
+                yb = y
+                hb, cb = yb, xb
+        hold.append((ys, hb))
+        cash.append((xs, cb))
+    return ask, bid, hold, cash, stop

@@ -355,3 +355,43 @@ def test_path_portfolios_are_tight_on_the_binding_path(party):
                 break
             C, y = cash[0, tt, party] * r, hold[0, tt, party]
     assert checked >= 2 * len(t)
+
+
+EXACT_PATH_CASES = [
+    dict(k=0.01, N=8, payoff=W.PUT),
+    dict(k=0.03, N=7, payoff=W.PUT, S0=92.0, R=0.08),
+    dict(k=0.01, N=9, payoff=W.CALL),
+    dict(k=0.02, N=6, payoff=W.CALL, S0=108.0, sigma=0.35),
+    dict(K=95.0, K2=105.0, k=0.01, N=8, payoff=W.SPREAD),
+    dict(K=95.0, K2=105.0, k=0.02, N=7, payoff=W.SPREAD, sigma=0.1, T=0.1),
+]
+
+
+@pytest.mark.parametrize("case", EXACT_PATH_CASES)
+def test_path_hedge_matches_exact_arithmetic(case):
+    """The oracle's hedge along a path against exact rational arithmetic (oracle/exact.py: the
+    induction with an exact slope restriction written from its definition, and the
+    rebalancing by exact comparison of the candidates, the rightmost among exact ties), on 6
+    paths per option with costs: holdings within 1e-9 of max(1, |y|), cash within 1e-9 of
+    max(|x|, S0), NaN exactly where the buyer has stopped, the same stopping level."""
+    from oracle import exact
+    t = W.make(**case)
+    o = t[0]
+    N = int(o["N"])
+    rng = np.random.default_rng(int(1000 * case["k"]) + N)
+    paths = [np.ones(N, np.int8), np.zeros(N, np.int8)] + [rng.integers(0, 2, N).astype(np.int8)
+                                                           for _ in range(4)]
+    for mv in paths:
+        hold, cash, stop, st = oracle.hedge_path(t, mv[None, :])
+        assert st[0] == 0
+        a, b, eh, ec, es = exact.hedge_path(o, mv)
+        assert stop[0] == es, (stop[0], es)
+        for tt in range(N + 1):
+            for p in (0, 1):
+                ye, xe = eh[tt][p], ec[tt][p]
+                y, x = hold[0, tt, p], cash[0, tt, p]
+                if ye is None:
+                    assert np.isnan(y) and np.isnan(x), (tt, p)
+                    continue
+                assert abs(y - float(ye)) <= 1e-9 * max(1.0, abs(float(ye))), (tt, p, y, float(ye))
+                assert abs(x - float(xe)) <= 1e-9 * max(abs(float(xe)), float(o["S0"])), (tt, p, x, float(xe))
