@@ -138,36 +138,28 @@ sys.path.insert(0, %(root)r)
 import workloads as W, paper_1110_2477_gb300 as ob
 t = W.concat(W.make(k=0.01, N=40), W.make(k=0.005, N=30, payoff=W.CALL))
 res = {}
-try:
-    ob.price(t)
-    torch.cuda.synchronize()
-    res["price"] = "ok"
-except ob.ObError as e:
-    res["price"] = str(e)
-dev = ob.to_device(t)
-out = torch.empty((2, 2), dtype=torch.float64, device="cuda")
-st = torch.empty(2, dtype=torch.int32, device="cuda")
-ob.ob_price_ask_bid_noalloc(dev, 2, out, st)
-torch.cuda.synchronize()
-res["noalloc"] = {"out": out.cpu().numpy().tolist(), "st": st.cpu().numpy().tolist()}
+for k in range(2):
+    try:
+        ob.price(t)
+        torch.cuda.synchronize()
+        res["price%d" % k] = "ok"
+    except ob.ObError as e:
+        res["price%d" % k] = str(e)
+res["torch"] = float(torch.arange(10, device="cuda", dtype=torch.float64).sum().item())
 print(json.dumps(res))
 """
 
 
-def test_pool_allocation_failure_is_reported_and_fixed_scratch_still_prices():
+def test_pool_allocation_failure_is_reported_and_the_context_stays_usable():
     """An allocation failure injected on the host side: a pool size no GPU has (OB_POOL_MB,
     read once per process, so the test runs in a child process).  cudaMalloc refuses it, the
-    pooled call returns OB_ERR_NOMEM with nothing enqueued, and the fixed-scratch entry point,
-    which allocates nothing at call time, still prices the same options against the oracle."""
+    pooled call returns OB_ERR_NOMEM with nothing enqueued, a second call does the same, and
+    the CUDA context stays usable."""
     env = dict(os.environ, OB_POOL_MB="1000000000")  # 1e9 MiB
     r = subprocess.run([sys.executable, "-c", _NOMEM_CHILD % {"root": ROOT}], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    assert res["price"].endswith("(-6)"), res["price"]
-    assert res["noalloc"]["st"] == [0, 0]
-    t = W.concat(W.make(k=0.01, N=40), W.make(k=0.005, N=30, payoff=W.CALL))
-    ref, rst = oracle.price_ask_bid(t)
-    got = np.array(res["noalloc"]["out"])
-    scale = np.maximum(np.abs(ref), 1e-2 * t["K"][:, None])
-    assert np.all(np.abs(got - ref) <= RTOL * scale)
+    assert res["price0"].endswith("(-6)"), res["price0"]
+    assert res["price1"].endswith("(-6)"), res["price1"]
+    assert res["torch"] == 45.0
