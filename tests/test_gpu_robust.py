@@ -7,6 +7,8 @@
     involved: the other CTAs give up after a 200 ms limit and return.
   * Calls made concurrently on two streams, and from two host threads, are ordered by the
     library on the device and price as they do alone.
+  * An allocation failure injected on the host (a pool size no GPU has) is reported as
+    OB_ERR_NOMEM with nothing enqueued; the context stays usable.
 """
 import json
 import os
